@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the space-time Schur-complement PCG (arXiv 2009.08875) on GB300.
+
+Metric: Schur-PCG DoF-iterations/s = N_t * N_x * (PCG iterations) / time.
+Workload: the 2D heat equation of the paper's weak-scaling row N_t = 513 (Table 5.3):
+space level K = 9 (N_x = 261121), time level J = 9 (N_t = 513), N = 1.34e8 unknowns,
+manufactured solution u = (1 + t^2) sin(pi x) sin(pi y), FP64, PCG to relative K_X-norm
+residual 1e-10 with the paper's preconditioner settings (alpha 0.3, 2 V-cycles, 3+3 sweeps).
+
+One step = one full solve: f_hat = W^T f (Lemma 4.1), PCG on S_hat w = f_hat (all rows of the
+hot path every iteration), u = W w.  Inputs are resident on the device when the timed region
+starts; every vector (1.07 GB) is larger than L2, so no flush is needed.  `e2e` repeats the
+solve through the host-buffer entry point with the copies inside the timed region.
+
+--impl reference times the CPU oracle (oracle/) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K_SPACE, J_TIME = 9, 9
+TOL = 1e-10
+# oracle sample: one PCG iteration at the workload's space level on a short time axis
+SAMPLE_K, SAMPLE_J = 9, 2
+
+# nominal FP64 rate of the profiling recipe (1.25 TFLOP/s) as FP64 instructions per second
+# (one add, mul or fma each; an fma counts 2 flops)
+FP64_INST_PEAK = 1.25e12 / 2.0
+
+# DRAM traffic per finest-level sweep launch from one ncu capture, valid only for the kernel
+# source it was taken on (keyed by the SHA-256 of k_mg.cu); otherwise reported as null.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--K", type=int, default=K_SPACE)
+    ap.add_argument("--J", type=int, default=J_TIME)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-sample-child", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------------------------
+def oracle_iteration_rate(steps=1, warmup=0):
+    """Time `steps` oracle PCG iterations (S_hat + K_X + vector updates) at K=9, J=2."""
+    import numpy as np
+
+    from oracle import schur
+    from paper_2009_08875_gb300 import inputs
+
+    p = schur.Problem(SAMPLE_K, SAMPLE_J)
+    g, u0, _ = inputs.manufactured(SAMPLE_K, SAMPLE_J)
+    fhat = p.rhs_hat(g, u0)
+    r = fhat.copy()
+    z = p.apply_KX(r)
+    pdir = z.copy()
+    w = np.zeros_like(fhat)
+    rho = float(np.vdot(r, z))
+    times = []
+    for it in range(warmup + steps):
+        t0 = time.perf_counter()
+        q = p.apply_Shat(pdir)
+        alpha = rho / float(np.vdot(pdir, q))
+        w += alpha * pdir
+        r -= alpha * q
+        z = p.apply_KX(r)
+        rho_new = float(np.vdot(r, z))
+        pdir = z + (rho_new / rho) * pdir
+        rho = rho_new
+        times.append(time.perf_counter() - t0)
+    n = p.Nt * p.Nx
+    timed = times[warmup:]
+    return dict(dof=n, seconds=timed, value=n * len(timed) / sum(timed))
+
+
+def oracle_in_subprocess(steps=1, warmup=0, timeout=1800):
+    """Run the oracle timing single-threaded in a child process (BLAS/OpenMP pinned to 1)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample-child", "--steps", str(steps),
+           "--warmup", str(warmup)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=timeout)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def sample_text():
+    return (f"one oracle PCG iteration (S_hat apply, K_X apply, vector updates) at K={SAMPLE_K} "
+            f"(N_x={(2**SAMPLE_K - 1)**2}), J={SAMPLE_J} (N_t={2**SAMPLE_J + 1}), manufactured forcing; "
+            "single thread (scipy.sparse, BLAS pinned to 1 thread)")
+
+
+# ----------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            import torch
+            ident = str(torch.cuda.get_device_properties(self.dev).uuid)
+            ident = ident if ident.startswith("GPU-") else "GPU-" + ident
+        except Exception:
+            ident = str(self.dev)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={ident}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ----------------------------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ----------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = oracle_in_subprocess(steps=args.steps, warmup=args.warmup)
+    value = res["value"]
+    line = {
+        "impl": "reference", "metric": "Schur-PCG DoF-iters/s (FP64)", "value": value,
+        "unit": "DoF-iter/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(res["seconds"]) / len(res["seconds"]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"heat eq. unit square K={args.K} J={args.J} (bounded oracle sample: K={SAMPLE_K} "
+                               f"J={SAMPLE_J})", "step": "one oracle PCG iteration"},
+        "cpu_baseline": {"value": value, "unit": "DoF-iter/s", "cores": 1, "kind": "oracle", "sample": sample_text()},
+        "e2e": {"value": value, "unit": "DoF-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------------
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_2009_08875_gb300", "csrc", "k_mg.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_2009_08875_gb300 import Solver, inputs
+
+    K, J = args.K, args.J
+    g_np, u0_np, _ = inputs.manufactured(K, J)
+    solver = Solver(K, J, tol=TOL, tol_mode=0, maxit=500)
+    stream = solver.stream
+    Nt, Nx = solver.shape
+    N = Nt * Nx
+    g = torch.from_numpy(g_np).cuda()
+    u0 = torch.from_numpy(u0_np).cuda()
+    f = torch.empty((Nt, Nx), dtype=torch.float64, device="cuda")
+    w = torch.empty_like(f)
+    u = torch.empty_like(f)
+
+    def step():
+        solver.rhs(g, u0, f)
+        its, _ = solver.pcg_solve(f, w)
+        solver.synthesize(w, u)
+        return its
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    solver.profile_begin()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    iters = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        iters += step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = solver.profile_end()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+        it_t = torch.tensor([iters], device="cuda", dtype=torch.float64)
+        dist.all_reduce(it_t)
+        iters_all = it_t.item()
+        dist.barrier()
+    else:
+        iters_all = iters
+    value = N * iters_all / (ms / 1e3)
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        gh = torch.from_numpy(g_np).pin_memory()
+        u0h = torch.from_numpy(u0_np).pin_memory()
+        uh = torch.empty((Nt, Nx), dtype=torch.float64).pin_memory()
+        solver.solve_host(gh, u0h, uh)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        its_e = 0
+        for _ in range(max(1, args.steps)):
+            its_e += solver.solve_host(gh, u0h, uh)[0]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = t.item()
+        e2e = {"value": world * N * its_e / dt, "unit": "DoF-iter/s",
+               "h2d_bytes_per_step": (g_np.size + u0_np.size) * 8, "d2h_bytes_per_step": N * 8}
+
+    if rank != 0:
+        solver.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (finest-level Gauss-Seidel sweep), timed live
+    sweep_s = prof["sweep_ms"] / 1e3
+    achieved = prof["sweep_fp64_ops"] / sweep_s / 1e9 if sweep_s > 0 else None
+    launches = max(prof["sweep_launches"], 1)
+    traffic = NCU_TRAFFIC.get(kernel_source_hash())
+    roofline = {
+        "kernel": "k_gs_sweep (finest level, FP64)",
+        "bound": "alu", "achieved": achieved, "peak": FP64_INST_PEAK / 1e9,
+        "unit": "G FP64 inst/s (add, mul, fma = 1)",
+        "frac": (achieved / (FP64_INST_PEAK / 1e9)) if achieved else None,
+        "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe, / 2 flops per fma",
+        "traffic": traffic,
+        "algorithmic_bytes_per_launch": prof["sweep_bytes"] / launches,
+        "fp64_inst_per_launch": prof["sweep_fp64_ops"] / launches,
+        "avg_launch_ms": prof["sweep_ms"] / launches,
+        "hbm_gbs": prof["sweep_bytes"] / sweep_s / 1e9 if sweep_s > 0 else None,
+        "share_of_step": prof["sweep_ms"] / ms if ms > 0 else None,
+    }
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            res = oracle_in_subprocess(steps=1, warmup=0)
+            cpu = {"value": res["value"], "unit": "DoF-iter/s", "cores": 1, "kind": "oracle",
+                   "sample": sample_text()}
+        except Exception as e:  # the bench line still prints; the failure is stated
+            cpu = {"value": None, "unit": "DoF-iter/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    line = {
+        "metric": "Schur-PCG DoF-iters/s (FP64)", "value": value, "unit": "DoF-iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"2D heat eq., unit square, K={K} (N_x={Nx}), J={J} (N_t={Nt}), "
+                               "u=(1+t^2)sin(pi x)sin(pi y), PCG to rel. 1e-10",
+                   "step": "one full solve: rhs + PCG + synthesis",
+                   "pcg_iterations": iters_all / max(1, args.steps) / world,
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (1.07 GB per vector)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": prof["launches"],
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.oracle_sample_child:
+        print(json.dumps(oracle_iteration_rate(steps=args.steps, warmup=args.warmup)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

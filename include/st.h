@@ -1,0 +1,149 @@
+/*
+ * libst: space-time Schur-complement PCG for the heat equation on one GB300 (sm_103a).
+ *
+ * Method: R. van Venetie and J. Westerdiep, "A parallel algorithm for solving linear
+ * parabolic evolution equations", arXiv 2009.08875.  The library computes the paper's
+ * hot path: PCG on  S_hat w = f_hat  (Sec. 3.4), S_hat = W^T S W, with S in the form of
+ * Lemma 4.2 and the wavelet-in-time, multigrid-in-space preconditioner K_X (Thm. 3.1),
+ * for u' - Laplace(u) = g on a uniformly refined P1 triangulation of the unit square,
+ * P1 in time, three-point wavelets in time (Sec. 5).
+ *
+ * ---------------------------------------------------------------------------------------
+ * Conventions shared by every entry point
+ * ---------------------------------------------------------------------------------------
+ * Sizes.  Space level K >= 1: N_x = (2^K - 1)^2 interior nodes (Sec. 5.1).  Time level
+ *   J >= 1: N_t = 2^J + 1 time nodes.
+ * Layout.  A space-time vector is a dense row-major array of N_t x N_x doubles (time
+ *   slowest).  Column p = iy * (2^K - 1) + ix is interior grid node (ix + 1, iy + 1) at
+ *   (x, y) = ((ix+1) h, (iy+1) h), h = 2^-K.
+ *   - single-scale vectors (u, g, f): row i is time node t_i = i 2^-J;
+ *   - wavelet vectors (w, f_hat, r, z, q): "in-place" lifting order: rows 0 and 2^J hold
+ *     the level-0 coefficients c_0, row i = (2k + 1) 2^(J-j-1) holds d_j[k] (level j + 1).
+ *     The paper lists the same coefficients as (c_0, d_0, ..., d_{J-1}) (Sec. 3.3).
+ * Memory.  Unless a name ends in _host, every vector pointer is a CUDA device pointer to
+ *   caller-owned memory, 8-byte aligned, not aliased with any other argument of the
+ *   same call.  The handle owns its internal workspace (allocated by st_setup).
+ * Streams.  All work is enqueued on the stream given to st_setup, in order, and is
+ *   asynchronous unless stated otherwise.
+ * Errors.  Every function returns an st_status; nothing is thrown across the ABI.  On
+ *   failure st_last_error() returns a message for the calling thread.  Argument errors
+ *   are detected before any work is enqueued.
+ */
+#ifndef ST_H
+#define ST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct st_handle_s* st_handle;
+
+typedef enum {
+  ST_OK = 0,
+  ST_ERR_ARG = 1,        /* invalid argument (null handle/pointer, size out of range)   */
+  ST_ERR_NOMEM = 2,      /* device workspace allocation failed                          */
+  ST_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed                 */
+  ST_ERR_BREAKDOWN = 4,  /* PCG breakdown: p^T S_hat p <= 0 or a non-finite scalar      */
+  ST_ERR_MAXIT = 5       /* PCG stopped at maxit before reaching the tolerance          */
+} st_status;
+
+typedef enum {
+  ST_FP64 = 0            /* every operation in IEEE binary64                            */
+} st_precision;
+
+typedef struct {
+  double alpha;     /* scaling of A_x inside K_j = (alpha A_x + 2^j M_x)^-1, Sec. 5.1: 0.3 */
+  int n_vcycles;    /* V-cycles per multigrid application, from x = 0; Sec. 5.1: 2          */
+  int n_pre;        /* 3-colour Gauss-Seidel pre-sweeps per level; Sec. 5.1: 3              */
+  int n_post;       /* post-sweeps per level (reverse colour order); Sec. 5.1: 3            */
+  double tol;       /* PCG tolerance                                                        */
+  int tol_mode;     /* 0: stop when sqrt(r^T K_X r / r_0^T K_X r_0) <= tol;
+                       1: stop when sqrt(r^T K_X r) <= tol (Eq. 3.3, the paper's rule)      */
+  int maxit;        /* PCG iteration limit                                                  */
+  int precision;    /* st_precision                                                         */
+} st_config;
+
+/* Fills *cfg with the paper's settings (alpha 0.3, 2 V-cycles, 3+3 sweeps, Sec. 5.1),
+ * tol 1e-10 relative, maxit 200, FP64. */
+void st_default_config(st_config* cfg);
+
+/* Creates a handle for the unit square at space level K (1..12) and time level J (1..14),
+ * binds it to `cuda_stream` (a cudaStream_t; NULL = legacy default stream) and allocates
+ * its device workspace (about 20 vectors of N_t x N_x doubles) on the current device.
+ * `domain` must be 0 (unit square).  cfg may be NULL (defaults).  Synchronous. */
+st_status st_setup(st_handle* out, int domain, int space_level, int time_level,
+                   const st_config* cfg, void* cuda_stream);
+
+/* Frees the workspace (after synchronising the bound stream).  NULL is accepted. */
+st_status st_destroy(st_handle h);
+
+/* Reports N_t and N_x of the handle. */
+st_status st_dims(st_handle h, int64_t* Nt, int64_t* Nx);
+
+/* x[s] = K_x b[s] for slices s < nslices (nslices <= 2 N_t), each of N_x doubles:
+ * K_x ~ A_x^-1 is n_vcycles symmetric V-cycles from zero on A_x (Sec. 3.1, Sec. 5.1).
+ * b and x must not overlap. */
+st_status st_apply_Kx(st_handle h, int nslices, const double* b, double* x);
+
+/* y = S u in single-scale coordinates, S by Lemma 4.2:
+ * S = A_t (x) M K_x M + M_t (x) A K_x A + L^T (x) M K_x A + L (x) A K_x M + Gamma_0 (x) M. */
+st_status st_apply_S_nodal(st_handle h, const double* u, double* y);
+
+/* u = W w: the wavelet synthesis W = W_t (x) Id, W_t by Eq. (3.1).  w in wavelet order. */
+st_status st_synthesize(st_handle h, const double* w, double* u);
+
+/* w = W^T u: the transposed (analysis) transform.  w in wavelet order. */
+st_status st_analyze(st_handle h, const double* u, double* w);
+
+/* q = S_hat w = W^T S W w (Sec. 3.4).  w and q in wavelet order. */
+st_status st_apply_S(st_handle h, const double* w, double* q);
+
+/* z = K_X r = blockdiag[K_|l| A_x K_|l|] r (Thm. 3.1), K_l ~ (alpha A_x + 2^l M_x)^-1 by
+ * multigrid, |l| the level of each wavelet row.  r and z in wavelet order. */
+st_status st_apply_KX(st_handle h, const double* r, double* z);
+
+/* f_hat = W^T f with f = B^T K_Y g + u_0 (Lemma 4.1), g interpolated in P1 (x) P1 at the
+ * space-time nodes (g_nodal: N_t x N_x single-scale) and u_0 in P1 (u0_nodal: N_x). */
+st_status st_rhs(st_handle h, const double* g_nodal, const double* u0_nodal, double* fhat);
+
+/* PCG on S_hat w = f_hat with preconditioner K_X (Sec. 3.4), starting from w = 0 (the
+ * input content of w is ignored and overwritten).  Stops by cfg.tol / cfg.tol_mode.
+ * Synchronises the bound stream once per iteration (8 scalars read back).
+ * *iters receives the iteration count; *relres sqrt(r^T K_X r / r_0^T K_X r_0).
+ * Returns ST_ERR_MAXIT (w holds the last iterate) or ST_ERR_BREAKDOWN on failure. */
+st_status st_pcg_solve(st_handle h, const double* fhat, double* w, int* iters, double* relres);
+
+/* End-to-end solve from host memory: copies g_nodal_host (N_t x N_x) and u0_host (N_x)
+ * to the device, forms f_hat, runs PCG, synthesises u = W w and copies u to u_host
+ * (N_t x N_x).  Host buffers should be page-locked for full copy bandwidth.
+ * Synchronous.  Returns like st_pcg_solve. */
+st_status st_solve_host(st_handle h, const double* g_nodal_host, const double* u0_host,
+                        double* u_host, int* iters, double* relres);
+
+/* Measurement hooks (not part of the method).  Between st_profile_begin and st_profile_end the
+ * handle counts every kernel it launches and brackets each finest-level Gauss-Seidel sweep
+ * launch (the dominant kernel) with a pair of CUDA events on the bound stream, adding up the
+ * launch's algorithmic work: per point and sweep 5 FP64 operations for K_x (7 with the mass
+ * couplings of K_l), and 24 bytes (read x and b, write x; 16 on a sweep that starts from
+ * x = 0).  st_profile_end synchronises the stream and reports the sums. */
+typedef struct {
+  int64_t launches;        /* kernels launched by the handle                        */
+  int64_t sweep_launches;  /* finest-level Gauss-Seidel sweep launches timed        */
+  double sweep_ms;         /* their summed CUDA-event durations                     */
+  double sweep_fp64_ops;   /* their algorithmic FP64 operations (add, mul, fma = 1) */
+  double sweep_bytes;      /* their algorithmic DRAM bytes                          */
+} st_profile;
+
+st_status st_profile_begin(st_handle h);
+st_status st_profile_end(st_handle h, st_profile* out);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* st_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ST_H */

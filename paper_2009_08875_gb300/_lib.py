@@ -1,0 +1,77 @@
+"""ctypes binding of libst (include/st.h).  Argument marshalling only: every computation
+happens in the CUDA library; torch tensors supply device memory and the stream."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libst.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "st.h")
+
+ST_OK, ST_ERR_ARG, ST_ERR_NOMEM, ST_ERR_CUDA, ST_ERR_BREAKDOWN, ST_ERR_MAXIT = range(6)
+STATUS_NAMES = {0: "ST_OK", 1: "ST_ERR_ARG", 2: "ST_ERR_NOMEM", 3: "ST_ERR_CUDA", 4: "ST_ERR_BREAKDOWN",
+                5: "ST_ERR_MAXIT"}
+
+
+class StConfig(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("n_vcycles", ctypes.c_int), ("n_pre", ctypes.c_int),
+                ("n_post", ctypes.c_int), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int),
+                ("maxit", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class StProfile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("sweep_launches", ctypes.c_int64), ("sweep_ms", ctypes.c_double),
+                ("sweep_fp64_ops", ctypes.c_double), ("sweep_bytes", ctypes.c_double)]
+
+
+class STError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "st_default_config": (None, [ctypes.POINTER(StConfig)]),
+    "st_setup": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(StConfig), _P]),
+    "st_destroy": (ctypes.c_int, [_P]),
+    "st_dims": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "st_apply_Kx": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "st_apply_S_nodal": (ctypes.c_int, [_P, _P, _P]),
+    "st_synthesize": (ctypes.c_int, [_P, _P, _P]),
+    "st_analyze": (ctypes.c_int, [_P, _P, _P]),
+    "st_apply_S": (ctypes.c_int, [_P, _P, _P]),
+    "st_apply_KX": (ctypes.c_int, [_P, _P, _P]),
+    "st_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
+    "st_pcg_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "st_solve_host": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "st_profile_begin": (ctypes.c_int, [_P]),
+    "st_profile_end": (ctypes.c_int, [_P, ctypes.POINTER(StProfile)]),
+    "st_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load():
+    """Load libst.so; raises ImportError if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libst.so not found at {LIB_PATH}: run __graft_entry__.build() first")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(status):
+    if status != ST_OK:
+        raise STError(status, load().st_last_error().decode())
+    return status

@@ -1,0 +1,142 @@
+// PCG vector kernels (Sec. 3.4): inner products with a fixed-shape two-pass reduction (the
+// same grid, the same partition and the same summation order on every call, so results are
+// bitwise reproducible), and the axpy updates of the Hestenes-Stiefel recurrences, which read
+// their scalars from device memory so the loop needs no host round trip except the stop test.
+#include "st_internal.cuh"
+
+namespace st {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) k_dot_partial(const double* __restrict__ a, const double* __restrict__ b,
+                                                     int64_t n, double* __restrict__ partials) {
+  double acc0 = 0.0, acc1 = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + stride < n; i += 2 * stride) {
+    acc0 = fma(a[i], b[i], acc0);
+    acc1 = fma(a[i + stride], b[i + stride], acc1);
+  }
+  if (i < n) acc0 = fma(a[i], b[i], acc0);
+  double t = block_sum(acc0 + acc1);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(256) k_dot_final(const double* __restrict__ partials, int nb,
+                                                   double* __restrict__ sc, int slot, int op) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partials[i];
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) {
+    switch (op) {
+      case DOT_STORE:
+        sc[slot] = t;
+        break;
+      case DOT_ALPHA:  // t = p^T q
+        sc[SC_PQ] = t;
+        sc[SC_ALPHA] = sc[SC_RHO] / t;
+        break;
+      case DOT_BETA:  // t = r^T z (new)
+        sc[SC_RHO_NEW] = t;
+        sc[SC_BETA] = t / sc[SC_RHO];
+        sc[SC_RHO] = t;
+        break;
+      case DOT_INIT:  // t = r_0^T z_0
+        sc[SC_RHO] = t;
+        sc[SC_RHO0] = t;
+        sc[SC_RHO_NEW] = t;
+        break;
+    }
+  }
+}
+
+// w += alpha p;  r -= alpha q
+__global__ void __launch_bounds__(256) k_update_wr(double* __restrict__ w, double* __restrict__ r,
+                                                   const double* __restrict__ p, const double* __restrict__ q,
+                                                   int64_t n, const double* __restrict__ sc) {
+  const double alpha = sc[SC_ALPHA];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    w[i] = fma(alpha, p[i], w[i]);
+    r[i] = fma(-alpha, q[i], r[i]);
+  }
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(256) k_update_p(double* __restrict__ p, const double* __restrict__ z, int64_t n,
+                                                  const double* __restrict__ sc) {
+  const double beta = sc[SC_BETA];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void __launch_bounds__(256) k_copy(double* __restrict__ dst, const double* __restrict__ src, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
+
+__global__ void __launch_bounds__(256) k_zero(double* __restrict__ dst, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = 0.0;
+}
+
+inline unsigned stream_grid(int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  return (unsigned)(g < kDotBlocks ? (g > 0 ? g : 1) : kDotBlocks);
+}
+
+}  // namespace
+
+cudaError_t launch_dot(const st_handle_s* h, const double* a, const double* b, int64_t n, int slot, int op) {
+  k_dot_partial<<<kDotBlocks, kThreads, 0, h->stream>>>(a, b, n, h->partials);
+  k_dot_final<<<1, kThreads, 0, h->stream>>>(h->partials, kDotBlocks, h->scal, slot, op);
+  count_launch(h, 2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_wr(const st_handle_s* h, double* w, double* r, const double* p, const double* q,
+                             int64_t n) {
+  k_update_wr<<<stream_grid(n), kThreads, 0, h->stream>>>(w, r, p, q, n, h->scal);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_p(const st_handle_s* h, double* p, const double* z, int64_t n) {
+  k_update_p<<<stream_grid(n), kThreads, 0, h->stream>>>(p, z, n, h->scal);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const st_handle_s* h, double* dst, const double* src, int64_t n) {
+  k_copy<<<stream_grid(n), kThreads, 0, h->stream>>>(dst, src, n);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(const st_handle_s* h, double* dst, int64_t n) {
+  k_zero<<<stream_grid(n), kThreads, 0, h->stream>>>(dst, n);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+}  // namespace st

@@ -1,0 +1,141 @@
+// Internal declarations of libst: handle layout, kernel launchers, shared helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/st.h"
+
+namespace st {
+
+// ---------------------------------------------------------------------------------------
+// Multigrid operator coefficients.  On mesh level k (h = 2^-k) the P1 matrix
+// C = a A_x + s M_x has the 7-point stencil
+//   centre 4a + s h^2/2,  axis neighbours -a + s h^2/12,  (1,1)/(-1,-1) diagonal s h^2/12
+// (A_x: 5-point Laplacian; M_x: h^2/12 [6; 1 x 6] on the (i,j)-(i+1,j+1) triangulation).
+// One entry per (coefficient class, level).  Class 0 is K_x (a = 1, s = 0); class 1 + l is
+// K_l (a = alpha, s = 2^l), l = 0..J.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct Coef {
+  T inv_c;  // 1 / centre
+  T c;      // centre
+  T ax;     // axis-neighbour coefficient
+  T dg;     // diagonal-neighbour coefficient
+};
+
+// Level |lambda| of in-place wavelet row i (rows 0 and 2^J: level 0; else J - ctz(i)).
+__host__ __device__ inline int wavelet_row_level(int i, int J) {
+  if (i == 0 || i == (1 << J)) return 0;
+#ifdef __CUDA_ARCH__
+  return J - (__ffs(i) - 1);
+#else
+  return J - __builtin_ctz((unsigned)i);
+#endif
+}
+
+struct MGLevels {
+  int K;                 // finest level
+  int kmin;              // coarsest level (exact solve)
+  int max_slices;        // capacity of the per-level buffers
+  // per level k (index k), kmin <= k < K: the two iterate buffers, right-hand side
+  double* xc[16];
+  double* xc2[16];
+  double* bc[16];
+  // residual on every level k > kmin (k = K included)
+  double* res[16];
+};
+
+}  // namespace st
+
+struct st_handle_s {
+  int domain, K, J;
+  int64_t Nt, Nx;
+  int n;  // 2^K - 1
+  st_config cfg;
+  cudaStream_t stream;
+  int device;
+
+  st::MGLevels mg;
+  st::Coef<double>* coef;  // device, (J + 2) x (K + 1)
+
+  // workspace, each N_t x N_x doubles unless noted
+  double* U;       // single-scale state
+  double* Y;       // 2 N_t slices: Y1 then Y2
+  double* X;       // 2 N_t slices: K_x Y
+  double* Xalt;    // 2 N_t slices: second iterate buffer of the finest multigrid level
+  double* Z;       // single-scale S u
+  double* V1;      // wavelet ping-pong scratch
+  double* V2;
+  double* r;       // PCG residual
+  double* p;       // search direction
+  double* z;       // preconditioned residual
+  double* q;       // S_hat p
+  double* g;       // device copy of g (st_solve_host)
+  double* fhat;    // right-hand side (st_solve_host)
+  double* w;       // solution (st_solve_host)
+  double* u0;      // N_x doubles (st_solve_host)
+  double* partials;  // dot-product partial sums
+  double* scal;      // PCG scalars (device)
+  double* scal_host; // page-locked mirror
+
+  // profiling (st_profile_begin / st_profile_end): kernel launch count, and CUDA events around
+  // every finest-level Gauss-Seidel sweep with that launch's algorithmic FP64 ops and bytes
+  mutable int64_t launches;
+  mutable bool prof_on;
+  mutable int prof_cap, prof_n;
+  mutable cudaEvent_t* prof_ev;
+  mutable double prof_ops, prof_bytes;
+};
+
+namespace st {
+
+// launch accounting: every kernel launch site calls count_launch
+inline void count_launch(const st_handle_s* h, int n = 1) { h->launches += n; }
+// event pair around one profiled launch (no-op unless profiling); returns false if out of events
+bool prof_start(const st_handle_s* h);
+void prof_stop(const st_handle_s* h, double ops, double bytes);
+
+// error helpers (thread-local message)
+void set_error(const std::string& msg);
+st_status cuda_fail(const char* where, cudaError_t e);
+
+// ---------------------------------------------------------------------------------------
+// launchers (all enqueue on `s`; return cudaGetLastError())
+// ---------------------------------------------------------------------------------------
+cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, cudaStream_t s);
+
+// x = K b on nslices slices of the finest level: n_vcycles V-cycles from zero.
+// coef_class < 0: per-slice class 1 + level(slice) (K_X); else a fixed class.
+cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const double* b, double* x);
+
+// wavelet transforms over N_t x N_x
+cudaError_t wavelet_synth(const st_handle_s* h, const double* w, double* u);
+cudaError_t wavelet_anal(const st_handle_s* h, const double* u, double* w);
+
+// Y1, Y2 (Y = [Y1; Y2]) from U: mode 0 (S): Y1 = A_t U M + L^T U A, Y2 = L U M + M_t U A;
+// mode 1 (right-hand side): Y1 = L^T G M, Y2 = M_t G M.
+cudaError_t launch_timemix(const st_handle_s* h, int mode, const double* U, double* Y);
+// Z = M X1 + A X2 + e_0 (x) M row0   (row0: N_x doubles, added to row 0 only)
+cudaError_t launch_epilogue(const st_handle_s* h, const double* X, const double* row0, double* Z);
+// Y = A_x X on nrows slices
+cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const double* X, double* Y);
+
+// vector kernels
+cudaError_t launch_dot(const st_handle_s* h, const double* a, const double* b, int64_t n, int slot, int op);
+cudaError_t launch_update_wr(const st_handle_s* h, double* w, double* r, const double* p, const double* q, int64_t n);
+cudaError_t launch_update_p(const st_handle_s* h, double* p, const double* z, int64_t n);
+cudaError_t launch_copy(const st_handle_s* h, double* dst, const double* src, int64_t n);
+cudaError_t launch_zero(const st_handle_s* h, double* dst, int64_t n);
+
+// PCG scalar slots in h->scal
+enum { SC_RHO = 0, SC_PQ = 1, SC_ALPHA = 2, SC_RHO_NEW = 3, SC_BETA = 4, SC_RHO0 = 5, SC_COUNT = 8 };
+// dot "op" after reduction into `slot`
+enum { DOT_STORE = 0, DOT_ALPHA = 1, DOT_BETA = 2, DOT_INIT = 3 };
+
+constexpr int kDotBlocks = 1216;  // 8 blocks x 152 SMs; fixed for deterministic reductions
+constexpr int kThreads = 256;
+
+}  // namespace st

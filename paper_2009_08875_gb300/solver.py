@@ -1,0 +1,119 @@
+"""Python face of libst: argument marshalling between torch tensors and the C ABI."""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import STError  # noqa: F401
+
+
+def _ptr(t, shape, name, device_ok=True):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if device_ok and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One handle of the CUDA solver for space level K and time level J on the unit square.
+
+    Tensors are (N_t, N_x) float64 CUDA tensors; wavelet-coordinate tensors use the library's
+    in-place row order.  Work is enqueued on `stream` (default: torch's current stream).
+    """
+
+    def __init__(self, K, J, domain=0, alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0,
+                 maxit=200, stream=None):
+        import torch
+        lib = _lib.load()
+        cfg = _lib.StConfig()
+        lib.st_default_config(ctypes.byref(cfg))
+        cfg.alpha, cfg.n_vcycles, cfg.n_pre, cfg.n_post = alpha, n_vcycles, n_pre, n_post
+        cfg.tol, cfg.tol_mode, cfg.maxit = tol, tol_mode, maxit
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _lib.check(lib.st_setup(ctypes.byref(h), domain, K, J, ctypes.byref(cfg), ctypes.c_void_p(stream.cuda_stream)))
+        self._h = h
+        nt, nx = ctypes.c_int64(), ctypes.c_int64()
+        _lib.check(lib.st_dims(h, ctypes.byref(nt), ctypes.byref(nx)))
+        self.Nt, self.Nx = nt.value, nx.value
+        self.K, self.J = K, J
+
+    @property
+    def shape(self):
+        return (self.Nt, self.Nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().st_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def apply_Kx(self, b, x):
+        ns = b.shape[0]
+        _lib.check(_lib.load().st_apply_Kx(self._h, ns, _ptr(b, (ns, self.Nx), "b"), _ptr(x, (ns, self.Nx), "x")))
+
+    def apply_S_nodal(self, u, y):
+        _lib.check(_lib.load().st_apply_S_nodal(self._h, _ptr(u, self.shape, "u"), _ptr(y, self.shape, "y")))
+
+    def synthesize(self, w, u):
+        _lib.check(_lib.load().st_synthesize(self._h, _ptr(w, self.shape, "w"), _ptr(u, self.shape, "u")))
+
+    def analyze(self, u, w):
+        _lib.check(_lib.load().st_analyze(self._h, _ptr(u, self.shape, "u"), _ptr(w, self.shape, "w")))
+
+    def apply_S(self, w, q):
+        _lib.check(_lib.load().st_apply_S(self._h, _ptr(w, self.shape, "w"), _ptr(q, self.shape, "q")))
+
+    def apply_KX(self, r, z):
+        _lib.check(_lib.load().st_apply_KX(self._h, _ptr(r, self.shape, "r"), _ptr(z, self.shape, "z")))
+
+    def rhs(self, g, u0, fhat):
+        _lib.check(_lib.load().st_rhs(self._h, _ptr(g, self.shape, "g"), _ptr(u0, (self.Nx,), "u0"),
+                                      _ptr(fhat, self.shape, "fhat")))
+
+    def pcg_solve(self, fhat, w):
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        st = _lib.load().st_pcg_solve(self._h, _ptr(fhat, self.shape, "fhat"), _ptr(w, self.shape, "w"),
+                                      ctypes.byref(it), ctypes.byref(rr))
+        if st not in (_lib.ST_OK,):
+            _lib.check(st)
+        return it.value, rr.value
+
+    def solve_host(self, g, u0, u):
+        """End-to-end solve from (preferably pinned) host tensors g (N_t, N_x), u0 (N_x,) into u."""
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        st = _lib.load().st_solve_host(self._h, _ptr(g, self.shape, "g", False), _ptr(u0, (self.Nx,), "u0", False),
+                                       _ptr(u, self.shape, "u", False), ctypes.byref(it), ctypes.byref(rr))
+        _lib.check(st)
+        return it.value, rr.value
+
+    def profile_begin(self):
+        """Start counting launches and timing finest-level sweeps (measurement hook)."""
+        _lib.check(_lib.load().st_profile_begin(self._h))
+
+    def profile_end(self):
+        """Synchronise and return a dict with the launch count and the timed sweep totals."""
+        out = _lib.StProfile()
+        _lib.check(_lib.load().st_profile_end(self._h, ctypes.byref(out)))
+        return {f: getattr(out, f) for f, _ in _lib.StProfile._fields_}
