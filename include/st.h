@@ -71,7 +71,7 @@ void st_default_config(st_config* cfg);
 
 /* Creates a handle for the unit square at space level K (1..12) and time level J (1..14),
  * binds it to `cuda_stream` (a cudaStream_t; NULL = legacy default stream) and allocates
- * its device workspace (about 20 vectors of N_t x N_x doubles) on the current device.
+ * its device workspace (about 24 vectors of N_t x N_x doubles) on the current device.
  * `domain` must be 0 (unit square).  cfg may be NULL (defaults).  Synchronous. */
 st_status st_setup(st_handle* out, int domain, int space_level, int time_level,
                    const st_config* cfg, void* cuda_stream);
@@ -121,6 +121,25 @@ st_status st_pcg_solve(st_handle h, const double* fhat, double* w, int* iters, d
  * Synchronous.  Returns like st_pcg_solve. */
 st_status st_solve_host(st_handle h, const double* g_nodal_host, const double* u0_host,
                         double* u_host, int* iters, double* relres);
+
+/* Allocation-free variant of st_apply_Kx (the paper has no counterpart; it exists for callers
+ * that cannot allocate device memory: processes whose device memory budget is owned by another
+ * allocator, such as a framework's caching allocator or a serving runtime's arena, where a raw
+ * cudaMalloc can fail or fragment that pool, and latency-critical loops that forbid allocation
+ * after start-up because cudaMalloc/cudaFree may synchronise the device).
+ * Computes x[s] = K_x b[s] for s < nslices at space level K, bitwise the same as st_apply_Kx
+ * with the default multigrid settings (2 V-cycles, 3 + 3 sweeps), enqueued on cuda_stream.
+ * Needs no handle and allocates nothing: its scratch is one static device array of 32 MiB,
+ * held by every device that loads the library until the process exits.  Sizes whose scratch
+ * (about nslices * N_x * 3.3 doubles) exceeds 32 MiB are rejected with ST_ERR_ARG before any
+ * work is enqueued; for example K = 9 allows 4 slices, K = 7 allows 78.
+ * The first call on each device looks up the array's device address and sets kernel
+ * attributes; make that first call before any stream capture on that device.
+ * Every call on a device shares the one array, which keeps the last call's contents (nothing
+ * in it needs to start at zero), so calls whose work overlaps on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  b and x are device pointers to
+ * caller-owned memory of nslices * N_x doubles and must not overlap. */
+st_status st_apply_Kx_static(int space_level, int nslices, const double* b, double* x, void* cuda_stream);
 
 /* Measurement hooks (not part of the method).  Between st_profile_begin and st_profile_end the
  * handle counts every kernel it launches and brackets each finest-level Gauss-Seidel sweep

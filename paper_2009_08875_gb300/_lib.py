@@ -41,6 +41,7 @@ _SIGS = {
     "st_destroy": (ctypes.c_int, [_P]),
     "st_dims": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "st_apply_Kx": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "st_apply_Kx_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "st_apply_S_nodal": (ctypes.c_int, [_P, _P, _P]),
     "st_synthesize": (ctypes.c_int, [_P, _P, _P]),
     "st_analyze": (ctypes.c_int, [_P, _P, _P]),
