@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--J", type=int, default=J_TIME)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--oracle-sample-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -282,6 +283,48 @@ def run_ours(args):
         e2e = {"value": world * N * its_e / dt, "unit": "DoF-iter/s",
                "h2d_bytes_per_step": (g_np.size + u0_np.size) * 8, "d2h_bytes_per_step": N * 8}
 
+    # mixed precision (binary32 inner PCG under binary64 refinement) on the same workload:
+    # same tolerance, solution compared with the FP64 solution of the timed region
+    mixed = None
+    if not args.no_mixed:
+        u64 = u.clone()
+        solver.close()
+        ms_solver = Solver(K, J, tol=TOL, tol_mode=0, maxit=500, precision="mixed")
+
+        def mstep():
+            ms_solver.rhs(g, u0, f)
+            ms_solver.pcg_solve(f, w)
+            ms_solver.synthesize(w, u)
+            return ms_solver.solve_info()
+
+        for _ in range(max(1, args.warmup)):
+            mstep()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        inner = outer = 0
+        m0.record(ms_solver.stream)
+        for _ in range(args.steps):
+            info = mstep()
+            inner += info["iterations"]
+            outer += info["outer_iterations"]
+        m1.record(ms_solver.stream)
+        torch.cuda.synchronize()
+        mms = m0.elapsed_time(m1)
+        if dist:
+            t = torch.tensor([mms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            mms = t.item()
+        err = ((u - u64).abs().max() / u64.abs().max()).item()
+        mixed = {"solves_per_s": world * args.steps / (mms / 1e3), "ms_per_solve": mms / args.steps,
+                 "fp64_solves_per_s": world * args.steps / (ms / 1e3),
+                 "value": world * N * inner / (mms / 1e3), "unit": "DoF-iter/s (binary32 inner iterations)",
+                 "inner_iterations_per_solve": inner / args.steps, "outer_iterations_per_solve": outer / args.steps,
+                 "rel_err_vs_fp64_solution": err, "dtype": "f32 inner / f64 refinement"}
+        solver = ms_solver
+
     if rank != 0:
         solver.close()
         if dist:
@@ -328,6 +371,7 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "mixed": mixed,
         "gpu_launches": prof["launches"],
         "clocks": clk,
     }

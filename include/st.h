@@ -50,7 +50,11 @@ typedef enum {
 } st_status;
 
 typedef enum {
-  ST_FP64 = 0            /* every operation in IEEE binary64                            */
+  ST_FP64 = 0,           /* every operation in IEEE binary64                              */
+  ST_MIXED_FP32 = 1      /* binary64 iterative refinement around a binary32 inner PCG:
+                            the outer residual f_hat - S_hat w uses the binary64 S (with
+                            its binary64 K_x), corrections and sums are binary64; the inner
+                            solve runs S_hat and K_X in binary32 with binary64 inner products */
 } st_precision;
 
 typedef struct {
@@ -63,10 +67,12 @@ typedef struct {
                        1: stop when sqrt(r^T K_X r) <= tol (Eq. 3.3, the paper's rule)      */
   int maxit;        /* PCG iteration limit                                                  */
   int precision;    /* st_precision                                                         */
+  double inner_tol; /* ST_MIXED_FP32: relative K_X-norm reduction of each inner solve        */
+  int inner_maxit;  /* ST_MIXED_FP32: iteration limit of each inner solve                    */
 } st_config;
 
 /* Fills *cfg with the paper's settings (alpha 0.3, 2 V-cycles, 3+3 sweeps, Sec. 5.1),
- * tol 1e-10 relative, maxit 200, FP64. */
+ * tol 1e-10 relative, maxit 200, FP64; inner_tol 1e-5, inner_maxit 60. */
 void st_default_config(st_config* cfg);
 
 /* Creates a handle for the unit square at space level K (1..12) and time level J (1..14),
@@ -112,8 +118,26 @@ st_status st_rhs(st_handle h, const double* g_nodal, const double* u0_nodal, dou
  * input content of w is ignored and overwritten).  Stops by cfg.tol / cfg.tol_mode.
  * Synchronises the bound stream once per iteration (8 scalars read back).
  * *iters receives the iteration count; *relres sqrt(r^T K_X r / r_0^T K_X r_0).
+ * With cfg.precision = ST_MIXED_FP32 the solve is iterative refinement: each outer step
+ * solves S_hat d = r with binary32 PCG to cfg.inner_tol, adds d to w in binary64 and
+ * recomputes r = f_hat - S_hat w in binary64; it stops when the binary64 residual meets
+ * cfg.tol in the K_X norm (K_X applied in binary32).  *iters is then the total number of
+ * inner PCG iterations (outer steps: st_solve_info).
  * Returns ST_ERR_MAXIT (w holds the last iterate) or ST_ERR_BREAKDOWN on failure. */
 st_status st_pcg_solve(st_handle h, const double* fhat, double* w, int* iters, double* relres);
+
+/* Statistics of the last st_pcg_solve / st_solve_host on the handle. */
+typedef struct {
+  int iterations;        /* PCG iterations (binary32 inner iterations for ST_MIXED_FP32) */
+  int outer_iterations;  /* refinement steps (binary64 S_hat applications); 0 for ST_FP64 */
+  double relres;         /* final sqrt(r^T K_X r / r_0^T K_X r_0)                        */
+} st_solve_info;
+st_status st_solve_info_get(st_handle h, st_solve_info* out);
+
+/* The binary32 operators of the ST_MIXED_FP32 inner solve (same definitions as st_apply_S and
+ * st_apply_KX; float device vectors of N_t x N_x in wavelet order).  Valid on any handle. */
+st_status st_apply_S_f32(st_handle h, const float* w, float* q);
+st_status st_apply_KX_f32(st_handle h, const float* r, float* z);
 
 /* End-to-end solve from host memory: copies g_nodal_host (N_t x N_x) and u0_host (N_x)
  * to the device, forms f_hat, runs PCG, synthesises u = W w and copies u to u_host
@@ -131,8 +155,8 @@ st_status st_solve_host(st_handle h, const double* g_nodal_host, const double* u
  * with the default multigrid settings (2 V-cycles, 3 + 3 sweeps), enqueued on cuda_stream.
  * Needs no handle and allocates nothing: its scratch is one static device array of 32 MiB,
  * held by every device that loads the library until the process exits.  Sizes whose scratch
- * (about nslices * N_x * 3.3 doubles) exceeds 32 MiB are rejected with ST_ERR_ARG before any
- * work is enqueued; for example K = 9 allows 4 slices, K = 7 allows 78.
+ * (about nslices * N_x * 3 doubles) exceeds 32 MiB are rejected with ST_ERR_ARG before any
+ * work is enqueued; for example K = 9 allows 5 slices, K = 7 allows 87.
  * The first call on each device looks up the array's device address and sets kernel
  * attributes; make that first call before any stream capture on that device.
  * Every call on a device shares the one array, which keeps the last call's contents (nothing

@@ -17,7 +17,15 @@ STATUS_NAMES = {0: "ST_OK", 1: "ST_ERR_ARG", 2: "ST_ERR_NOMEM", 3: "ST_ERR_CUDA"
 class StConfig(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("n_vcycles", ctypes.c_int), ("n_pre", ctypes.c_int),
                 ("n_post", ctypes.c_int), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int),
-                ("maxit", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("inner_maxit", ctypes.c_int)]
+
+
+class StSolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("relres", ctypes.c_double)]
+
+
+ST_FP64, ST_MIXED_FP32 = 0, 1
 
 
 class StProfile(ctypes.Structure):
@@ -49,6 +57,9 @@ _SIGS = {
     "st_apply_KX": (ctypes.c_int, [_P, _P, _P]),
     "st_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
     "st_pcg_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "st_solve_info_get": (ctypes.c_int, [_P, ctypes.POINTER(StSolveInfo)]),
+    "st_apply_S_f32": (ctypes.c_int, [_P, _P, _P]),
+    "st_apply_KX_f32": (ctypes.c_int, [_P, _P, _P]),
     "st_solve_host": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double)]),
     "st_profile_begin": (ctypes.c_int, [_P]),

@@ -55,10 +55,15 @@ void prof_stop(const st_handle_s* h, double ops, double bytes) {
 
 using namespace st;
 
-#define ST_CHECK_CUDA(call, where)                 \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return cuda_fail(where, e_); \
+// ST_CHECK_CUDA(call, "where"): returns ST_ERR_CUDA with a message if the call failed.  Variadic
+// so that template arguments with commas need no extra parentheses.
+static inline st_status check_cuda_(cudaError_t e, const char* where) {
+  return e == cudaSuccess ? ST_OK : cuda_fail(where, e);
+}
+#define ST_CHECK_CUDA(...)                      \
+  do {                                          \
+    st_status s_ = check_cuda_(__VA_ARGS__);    \
+    if (s_ != ST_OK) return s_;                 \
   } while (0)
 
 #define ST_REQUIRE(cond, msg)   \
@@ -72,7 +77,7 @@ using namespace st;
 namespace {
 
 void free_all(st_handle_s* h) {
-  double** bufs[] = {&h->U, &h->Y, &h->X, &h->Xalt, &h->Z, &h->V1, &h->V2, &h->r, &h->p, &h->z, &h->q,
+  double** bufs[] = {&h->U, &h->Y, &h->X, &h->Xalt, &h->Bs, &h->Z, &h->V1, &h->V2, &h->r, &h->p, &h->z, &h->q,
                      &h->g, &h->fhat, &h->w, &h->u0, &h->partials, &h->scal};
   for (double** b : bufs) {
     if (*b) cudaFree(*b);
@@ -82,11 +87,17 @@ void free_all(st_handle_s* h) {
     if (h->mg.xc[k]) cudaFree(h->mg.xc[k]);
     if (h->mg.xc2[k]) cudaFree(h->mg.xc2[k]);
     if (h->mg.bc[k]) cudaFree(h->mg.bc[k]);
-    if (h->mg.res[k]) cudaFree(h->mg.res[k]);
-    h->mg.xc[k] = h->mg.xc2[k] = h->mg.bc[k] = h->mg.res[k] = nullptr;
+    h->mg.xc[k] = h->mg.xc2[k] = h->mg.bc[k] = nullptr;
   }
   if (h->coef) cudaFree(h->coef);
   h->coef = nullptr;
+  if (h->coef32) cudaFree(h->coef32);
+  h->coef32 = nullptr;
+  float** fb[] = {&h->xi, &h->ri, &h->pi, &h->zi, &h->qi};
+  for (float** b : fb) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
   if (h->scal_host) cudaFreeHost(h->scal_host);
   h->scal_host = nullptr;
   for (int i = 0; i < h->prof_cap; ++i) cudaEventDestroy(h->prof_ev[i]);
@@ -115,34 +126,42 @@ st_status check_handle(st_handle h) {
   return ST_OK;
 }
 
-st_status apply_S_nodal_impl(st_handle h, const double* u, double* y) {
-  ST_CHECK_CUDA(launch_timemix(h, 0, u, h->Y), "timemix");
-  ST_CHECK_CUDA(mg_apply(h, (int)(2 * h->Nt), 0, h->Y, h->X), "K_x multigrid");
-  ST_CHECK_CUDA(launch_epilogue(h, h->X, u, y), "epilogue");
+template <typename T>
+T* ws(double* p) {
+  return reinterpret_cast<T*>(p);
+}
+
+template <typename T>
+st_status apply_S_nodal_impl(st_handle h, const T* u, T* y) {
+  ST_CHECK_CUDA(launch_timemix<T>(h, 0, u, ws<T>(h->Y)), "timemix");
+  ST_CHECK_CUDA(mg_apply<T>(h, (int)(2 * h->Nt), 0, ws<T>(h->Y), ws<T>(h->X)), "K_x multigrid");
+  ST_CHECK_CUDA(launch_epilogue<T>(h, ws<T>(h->X), u, y), "epilogue");
   return ST_OK;
 }
 
-st_status apply_Shat_impl(st_handle h, const double* w, double* q) {
-  ST_CHECK_CUDA(wavelet_synth(h, w, h->U), "wavelet synthesis");
-  st_status s = apply_S_nodal_impl(h, h->U, h->Z);
+template <typename T>
+st_status apply_Shat_impl(st_handle h, const T* w, T* q) {
+  ST_CHECK_CUDA(wavelet_synth<T>(h, w, ws<T>(h->U)), "wavelet synthesis");
+  st_status s = apply_S_nodal_impl<T>(h, ws<T>(h->U), ws<T>(h->Z));
   if (s != ST_OK) return s;
-  ST_CHECK_CUDA(wavelet_anal(h, h->Z, q), "wavelet analysis");
+  ST_CHECK_CUDA(wavelet_anal<T>(h, ws<T>(h->Z), q), "wavelet analysis");
   return ST_OK;
 }
 
-st_status apply_KX_impl(st_handle h, const double* r, double* z) {
+template <typename T>
+st_status apply_KX_impl(st_handle h, const T* r, T* z) {
   const int nt = (int)h->Nt;
-  ST_CHECK_CUDA(mg_apply(h, nt, -1, r, h->X), "K_l multigrid (1)");
-  ST_CHECK_CUDA(launch_apply_A(h, nt, h->X, h->Y), "A_x");
-  ST_CHECK_CUDA(mg_apply(h, nt, -1, h->Y, z), "K_l multigrid (2)");
+  ST_CHECK_CUDA(mg_apply<T>(h, nt, -1, r, ws<T>(h->X)), "K_l multigrid (1)");
+  ST_CHECK_CUDA(launch_apply_A<T>(h, nt, ws<T>(h->X), ws<T>(h->Y)), "A_x");
+  ST_CHECK_CUDA(mg_apply<T>(h, nt, -1, ws<T>(h->Y), z), "K_l multigrid (2)");
   return ST_OK;
 }
 
 st_status rhs_impl(st_handle h, const double* g, const double* u0, double* fhat) {
-  ST_CHECK_CUDA(launch_timemix(h, 1, g, h->Y), "timemix (rhs)");
-  ST_CHECK_CUDA(mg_apply(h, (int)(2 * h->Nt), 0, h->Y, h->X), "K_x multigrid (rhs)");
-  ST_CHECK_CUDA(launch_epilogue(h, h->X, u0, h->Z), "epilogue (rhs)");
-  ST_CHECK_CUDA(wavelet_anal(h, h->Z, fhat), "wavelet analysis (rhs)");
+  ST_CHECK_CUDA(launch_timemix<double>(h, 1, g, h->Y), "timemix (rhs)");
+  ST_CHECK_CUDA(mg_apply<double>(h, (int)(2 * h->Nt), 0, h->Y, h->X), "K_x multigrid (rhs)");
+  ST_CHECK_CUDA(launch_epilogue<double>(h, h->X, u0, h->Z), "epilogue (rhs)");
+  ST_CHECK_CUDA(wavelet_anal<double>(h, h->Z, fhat), "wavelet analysis (rhs)");
   return ST_OK;
 }
 
@@ -153,17 +172,17 @@ st_status read_scalars(st_handle h) {
   return ST_OK;
 }
 
-st_status pcg_impl(st_handle h, const double* fhat, double* w, int* iters, double* relres) {
+st_status pcg64_impl(st_handle h, const double* fhat, double* w, int* iters, double* relres) {
   const int64_t n = h->Nt * h->Nx;
   const st_config& c = h->cfg;
   if (iters) *iters = 0;
   if (relres) *relres = 0.0;
-  ST_CHECK_CUDA(launch_zero(h, w, n), "zero w");
-  ST_CHECK_CUDA(launch_copy(h, h->r, fhat, n), "copy r");
-  st_status s = apply_KX_impl(h, h->r, h->z);
+  ST_CHECK_CUDA(launch_zero<double>(h, w, n), "zero w");
+  ST_CHECK_CUDA(launch_copy<double, double>(h, h->r, fhat, n), "copy r");
+  st_status s = apply_KX_impl<double>(h, h->r, h->z);
   if (s != ST_OK) return s;
-  ST_CHECK_CUDA(launch_dot(h, h->r, h->z, n, SC_RHO, DOT_INIT), "dot r z");
-  ST_CHECK_CUDA(launch_copy(h, h->p, h->z, n), "copy p");
+  ST_CHECK_CUDA(launch_dot<double, double>(h, h->r, h->z, n, SC_RHO, DOT_INIT), "dot r z");
+  ST_CHECK_CUDA(launch_copy<double, double>(h, h->p, h->z, n), "copy p");
   if ((s = read_scalars(h)) != ST_OK) return s;
   const double rho0 = h->scal_host[SC_RHO0];
   if (!std::isfinite(rho0) || rho0 < 0.0) {
@@ -172,11 +191,11 @@ st_status pcg_impl(st_handle h, const double* fhat, double* w, int* iters, doubl
   }
   if (rho0 == 0.0 || (c.tol_mode == 1 && std::sqrt(rho0) <= c.tol)) return ST_OK;
   for (int it = 1; it <= c.maxit; ++it) {
-    if ((s = apply_Shat_impl(h, h->p, h->q)) != ST_OK) return s;
-    ST_CHECK_CUDA(launch_dot(h, h->p, h->q, n, SC_PQ, DOT_ALPHA), "dot p q");
-    ST_CHECK_CUDA(launch_update_wr(h, w, h->r, h->p, h->q, n), "update w r");
-    if ((s = apply_KX_impl(h, h->r, h->z)) != ST_OK) return s;
-    ST_CHECK_CUDA(launch_dot(h, h->r, h->z, n, SC_RHO_NEW, DOT_BETA), "dot r z");
+    if ((s = apply_Shat_impl<double>(h, h->p, h->q)) != ST_OK) return s;
+    ST_CHECK_CUDA(launch_dot<double, double>(h, h->p, h->q, n, SC_PQ, DOT_ALPHA), "dot p q");
+    ST_CHECK_CUDA(launch_update_wr<double>(h, w, h->r, h->p, h->q, n), "update w r");
+    if ((s = apply_KX_impl<double>(h, h->r, h->z)) != ST_OK) return s;
+    ST_CHECK_CUDA(launch_dot<double, double>(h, h->r, h->z, n, SC_RHO_NEW, DOT_BETA), "dot r z");
     if ((s = read_scalars(h)) != ST_OK) return s;
     const double pq = h->scal_host[SC_PQ], rho = h->scal_host[SC_RHO_NEW];
     if (iters) *iters = it;
@@ -188,10 +207,105 @@ st_status pcg_impl(st_handle h, const double* fhat, double* w, int* iters, doubl
     if (relres) *relres = rr;
     const bool done = c.tol_mode == 1 ? std::sqrt(rho) <= c.tol : rr <= c.tol;
     if (done) return ST_OK;
-    ST_CHECK_CUDA(launch_update_p(h, h->p, h->z, n), "update p");
+    ST_CHECK_CUDA(launch_update_p<double>(h, h->p, h->z, n), "update p");
   }
   set_error("PCG reached maxit before the tolerance");
   return ST_ERR_MAXIT;
+}
+
+// Binary32 PCG on S_hat x = ri from x = 0, with zi = K_X ri already formed; stops at a relative
+// K_X-norm reduction of inner_tol or after inner_maxit iterations.  Inner products accumulate in
+// binary64.  Returns the iteration count through *its.
+st_status inner_pcg32(st_handle h, int* its) {
+  const int64_t n = h->Nt * h->Nx;
+  const st_config& c = h->cfg;
+  *its = 0;
+  ST_CHECK_CUDA(launch_zero<float>(h, h->xi, n), "zero inner x");
+  ST_CHECK_CUDA(launch_copy<float, float>(h, h->pi, h->zi, n), "copy inner p");
+  ST_CHECK_CUDA(launch_dot<float, float>(h, h->ri, h->zi, n, SC_RHO, DOT_INIT), "inner dot r z");
+  st_status s;
+  if ((s = read_scalars(h)) != ST_OK) return s;
+  const double rho0 = h->scal_host[SC_RHO0];
+  if (!(rho0 > 0.0) || !std::isfinite(rho0)) return ST_OK;  // nothing to correct (or caught by the outer test)
+  for (int it = 1; it <= c.inner_maxit; ++it) {
+    if ((s = apply_Shat_impl<float>(h, h->pi, h->qi)) != ST_OK) return s;
+    ST_CHECK_CUDA(launch_dot<float, float>(h, h->pi, h->qi, n, SC_PQ, DOT_ALPHA), "inner dot p q");
+    ST_CHECK_CUDA(launch_update_wr<float>(h, h->xi, h->ri, h->pi, h->qi, n), "inner update");
+    if ((s = apply_KX_impl<float>(h, h->ri, h->zi)) != ST_OK) return s;
+    ST_CHECK_CUDA(launch_dot<float, float>(h, h->ri, h->zi, n, SC_RHO_NEW, DOT_BETA), "inner dot r z");
+    if ((s = read_scalars(h)) != ST_OK) return s;
+    *its = it;
+    const double pq = h->scal_host[SC_PQ], rho = h->scal_host[SC_RHO_NEW];
+    if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rho) || rho < 0.0) {
+      set_error("inner PCG breakdown: p^T S_hat p <= 0 or a non-finite scalar");
+      return ST_ERR_BREAKDOWN;
+    }
+    if (std::sqrt(rho / rho0) <= c.inner_tol) break;
+    ST_CHECK_CUDA(launch_update_p<float>(h, h->pi, h->zi, n), "inner update p");
+  }
+  return ST_OK;
+}
+
+// Iterative refinement: w = 0, r = f_hat; repeat { solve S_hat d = r in binary32; w += d;
+// r = f_hat - S_hat w in binary64 } until sqrt(r^T K_X r) meets the tolerance (K_X in binary32,
+// the inner product in binary64).
+st_status pcg_mixed_impl(st_handle h, const double* fhat, double* w, int* iters, double* relres) {
+  const int64_t n = h->Nt * h->Nx;
+  const st_config& c = h->cfg;
+  if (iters) *iters = 0;
+  if (relres) *relres = 0.0;
+  ST_CHECK_CUDA(launch_zero<double>(h, w, n), "zero w");
+  ST_CHECK_CUDA(launch_copy<double, double>(h, h->r, fhat, n), "copy r");
+  ST_CHECK_CUDA(launch_copy<float, double>(h, h->ri, fhat, n), "round r");
+  st_status s = apply_KX_impl<float>(h, h->ri, h->zi);
+  if (s != ST_OK) return s;
+  ST_CHECK_CUDA(launch_dot<double, float>(h, h->r, h->zi, n, SC_OUTER, DOT_STORE), "outer dot");
+  if ((s = read_scalars(h)) != ST_OK) return s;
+  const double rho0 = h->scal_host[SC_OUTER];
+  if (!std::isfinite(rho0) || rho0 < 0.0) {
+    set_error("PCG breakdown: initial r^T K_X r is negative or not finite");
+    return ST_ERR_BREAKDOWN;
+  }
+  if (rho0 == 0.0 || (c.tol_mode == 1 && std::sqrt(rho0) <= c.tol)) return ST_OK;
+  int total = 0;
+  for (int outer = 1; total < c.maxit; ++outer) {
+    int its = 0;
+    if ((s = inner_pcg32(h, &its)) != ST_OK) return s;
+    total += its;
+    if (iters) *iters = total;
+    h->last_outer = outer;
+    ST_CHECK_CUDA(launch_add_correction(h, w, h->xi, n), "w += d");
+    if ((s = apply_Shat_impl<double>(h, w, h->q)) != ST_OK) return s;
+    ST_CHECK_CUDA(launch_residual_split(h, h->r, h->ri, fhat, h->q, n), "outer residual");
+    if ((s = apply_KX_impl<float>(h, h->ri, h->zi)) != ST_OK) return s;
+    ST_CHECK_CUDA(launch_dot<double, float>(h, h->r, h->zi, n, SC_OUTER, DOT_STORE), "outer dot");
+    if ((s = read_scalars(h)) != ST_OK) return s;
+    const double rho = h->scal_host[SC_OUTER];
+    if (!std::isfinite(rho) || rho < 0.0) {
+      set_error("PCG breakdown: outer r^T K_X r is negative or not finite");
+      return ST_ERR_BREAKDOWN;
+    }
+    const double rr = std::sqrt(rho / rho0);
+    if (relres) *relres = rr;
+    const bool done = c.tol_mode == 1 ? std::sqrt(rho) <= c.tol : rr <= c.tol;
+    if (done) return ST_OK;
+    if (its == 0) break;  // the inner solve made no progress
+  }
+  set_error("mixed-precision refinement reached maxit before the tolerance");
+  return ST_ERR_MAXIT;
+}
+
+st_status pcg_impl(st_handle h, const double* fhat, double* w, int* iters, double* relres) {
+  int it = 0;
+  double rr = 0.0;
+  h->last_outer = 0;
+  st_status s = h->cfg.precision == ST_MIXED_FP32 ? pcg_mixed_impl(h, fhat, w, &it, &rr)
+                                                   : pcg64_impl(h, fhat, w, &it, &rr);
+  h->last_iters = it;
+  h->last_relres = rr;
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return s;
 }
 
 }  // namespace
@@ -208,6 +322,8 @@ void st_default_config(st_config* cfg) {
   cfg->tol_mode = 0;
   cfg->maxit = 200;
   cfg->precision = ST_FP64;
+  cfg->inner_tol = 1e-5;
+  cfg->inner_maxit = 60;
 }
 
 const char* st_last_error(void) { return g_last_error.c_str(); }
@@ -228,7 +344,9 @@ st_status st_setup(st_handle* out, int domain, int space_level, int time_level, 
   ST_REQUIRE(c.alpha > 0.0 && std::isfinite(c.alpha), "st_setup: alpha must be positive");
   ST_REQUIRE(c.maxit >= 0 && c.tol >= 0.0 && (c.tol_mode == 0 || c.tol_mode == 1),
              "st_setup: invalid tolerance settings");
-  ST_REQUIRE(c.precision == ST_FP64, "st_setup: unsupported precision");
+  ST_REQUIRE(c.precision == ST_FP64 || c.precision == ST_MIXED_FP32, "st_setup: unsupported precision");
+  ST_REQUIRE(c.inner_tol > 0.0 && c.inner_tol < 1.0 && c.inner_maxit >= 1,
+             "st_setup: inner_tol must be in (0, 1) and inner_maxit >= 1");
 
   st_handle_s* h = new (std::nothrow) st_handle_s();
   if (!h) {
@@ -259,7 +377,7 @@ st_status st_setup(st_handle* out, int domain, int space_level, int time_level, 
     double** p;
     size_t n;
     const char* name;
-  } plan[] = {{&h->U, V, "U"},   {&h->Y, 2 * V, "Y"},  {&h->X, 2 * V, "X"}, {&h->Xalt, 2 * V, "Xalt"},        {&h->Z, V, "Z"},
+  } plan[] = {{&h->U, V, "U"},   {&h->Y, 2 * V, "Y"},  {&h->X, 2 * V, "X"}, {&h->Xalt, 2 * V, "Xalt"}, {&h->Bs, 2 * V, "Bs"},        {&h->Z, V, "Z"},
               {&h->V1, V, "V1"}, {&h->V2, V, "V2"},    {&h->r, V, "r"},            {&h->p, V, "p"},
               {&h->z, V, "z"},   {&h->q, V, "q"},      {&h->g, V, "g"},            {&h->fhat, V, "fhat"},
               {&h->w, V, "w"},   {&h->u0, (size_t)h->Nx, "u0"}, {&h->partials, (size_t)kDotBlocks, "partials"},
@@ -273,7 +391,26 @@ st_status st_setup(st_handle* out, int domain, int space_level, int time_level, 
       if (s == ST_OK) s = alloc(&h->mg.xc2[k], nk, "multigrid x (second buffer)");
       if (s == ST_OK) s = alloc(&h->mg.bc[k], nk, "multigrid b");
     }
-    if (k > h->mg.kmin && s == ST_OK) s = alloc(&h->mg.res[k], nk, "multigrid residual");
+  }
+  // binary32 inner-solve vectors (every handle gets them: st_apply_S_f32 / st_apply_KX_f32 need none,
+  // but a mixed-precision solve does)
+  float** fplan[] = {&h->xi, &h->ri, &h->pi, &h->zi, &h->qi};
+  for (float** fp : fplan) {
+    if (s != ST_OK || c.precision != ST_MIXED_FP32) break;
+    e = cudaMalloc(reinterpret_cast<void**>(fp), V * sizeof(float));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of the binary32 inner-solve vectors failed");
+      s = ST_ERR_NOMEM;
+    }
+  }
+  if (s == ST_OK) {
+    e = cudaMalloc(reinterpret_cast<void**>(&h->coef32), sizeof(Coef<float>) * (h->J + 2) * (h->K + 1));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of the coefficient table failed");
+      s = ST_ERR_NOMEM;
+    }
   }
   if (s == ST_OK) {
     e = cudaMalloc(reinterpret_cast<void**>(&h->coef), sizeof(Coef<double>) * (h->J + 2) * (h->K + 1));
@@ -294,6 +431,7 @@ st_status st_setup(st_handle* out, int domain, int space_level, int time_level, 
   if (s == ST_OK) {
     e = mg_set_attributes();
     if (e == cudaSuccess) e = launch_make_coef(h->coef, h->K, h->J, c.alpha, h->stream);
+    if (e == cudaSuccess) e = launch_make_coef32(h->coef32, h->K, h->J, c.alpha, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->scal, 0, sizeof(double) * SC_COUNT, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = cuda_fail("st_setup", e);
@@ -328,7 +466,7 @@ st_status st_apply_Kx(st_handle h, int nslices, const double* b, double* x) {
   if (s != ST_OK) return s;
   ST_REQUIRE(b && x, "st_apply_Kx: null pointer");
   ST_REQUIRE(nslices >= 1 && nslices <= 2 * h->Nt, "st_apply_Kx: nslices must be in 1..2 N_t");
-  ST_CHECK_CUDA(mg_apply(h, nslices, 0, b, x), "K_x multigrid");
+  ST_CHECK_CUDA(mg_apply<double>(h, nslices, 0, b, x), "K_x multigrid");
   return ST_OK;
 }
 
@@ -336,14 +474,14 @@ st_status st_apply_S_nodal(st_handle h, const double* u, double* y) {
   st_status s = check_handle(h);
   if (s != ST_OK) return s;
   ST_REQUIRE(u && y, "st_apply_S_nodal: null pointer");
-  return apply_S_nodal_impl(h, u, y);
+  return apply_S_nodal_impl<double>(h, u, y);
 }
 
 st_status st_synthesize(st_handle h, const double* w, double* u) {
   st_status s = check_handle(h);
   if (s != ST_OK) return s;
   ST_REQUIRE(w && u, "st_synthesize: null pointer");
-  ST_CHECK_CUDA(wavelet_synth(h, w, u), "wavelet synthesis");
+  ST_CHECK_CUDA(wavelet_synth<double>(h, w, u), "wavelet synthesis");
   return ST_OK;
 }
 
@@ -351,7 +489,7 @@ st_status st_analyze(st_handle h, const double* u, double* w) {
   st_status s = check_handle(h);
   if (s != ST_OK) return s;
   ST_REQUIRE(w && u, "st_analyze: null pointer");
-  ST_CHECK_CUDA(wavelet_anal(h, u, w), "wavelet analysis");
+  ST_CHECK_CUDA(wavelet_anal<double>(h, u, w), "wavelet analysis");
   return ST_OK;
 }
 
@@ -359,14 +497,36 @@ st_status st_apply_S(st_handle h, const double* w, double* q) {
   st_status s = check_handle(h);
   if (s != ST_OK) return s;
   ST_REQUIRE(w && q, "st_apply_S: null pointer");
-  return apply_Shat_impl(h, w, q);
+  return apply_Shat_impl<double>(h, w, q);
+}
+
+st_status st_apply_S_f32(st_handle h, const float* w, float* q) {
+  st_status s = check_handle(h);
+  if (s != ST_OK) return s;
+  ST_REQUIRE(w && q, "st_apply_S_f32: null pointer");
+  return apply_Shat_impl<float>(h, w, q);
+}
+
+st_status st_apply_KX_f32(st_handle h, const float* r, float* z) {
+  st_status s = check_handle(h);
+  if (s != ST_OK) return s;
+  ST_REQUIRE(r && z, "st_apply_KX_f32: null pointer");
+  return apply_KX_impl<float>(h, r, z);
+}
+
+st_status st_solve_info_get(st_handle h, st_solve_info* out) {
+  ST_REQUIRE(h != nullptr && out != nullptr, "st_solve_info_get: null pointer");
+  out->iterations = h->last_iters;
+  out->outer_iterations = h->last_outer;
+  out->relres = h->last_relres;
+  return ST_OK;
 }
 
 st_status st_apply_KX(st_handle h, const double* r, double* z) {
   st_status s = check_handle(h);
   if (s != ST_OK) return s;
   ST_REQUIRE(r && z, "st_apply_KX: null pointer");
-  return apply_KX_impl(h, r, z);
+  return apply_KX_impl<double>(h, r, z);
 }
 
 st_status st_rhs(st_handle h, const double* g, const double* u0, double* fhat) {
@@ -395,7 +555,7 @@ st_status st_solve_host(st_handle h, const double* g_host, const double* u0_host
   if ((s = rhs_impl(h, h->g, h->u0, h->fhat)) != ST_OK) return s;
   st_status ps = pcg_impl(h, h->fhat, h->w, iters, relres);
   if (ps != ST_OK && ps != ST_ERR_MAXIT) return ps;
-  ST_CHECK_CUDA(wavelet_synth(h, h->w, h->g), "wavelet synthesis");
+  ST_CHECK_CUDA(wavelet_synth<double>(h, h->w, h->g), "wavelet synthesis");
   ST_CHECK_CUDA(cudaMemcpyAsync(u_host, h->g, V * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy u");
   ST_CHECK_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
   return ps;

@@ -16,18 +16,26 @@ namespace {
 // ---------------------------------------------------------------------------------------
 // coefficient table: class 0 -> (a, s) = (1, 0); class 1 + l -> (alpha, 2^l), l = 0..J
 // ---------------------------------------------------------------------------------------
-__global__ void k_make_coef(Coef<double>* coef, int K, int J, double alpha) {
+template <typename T>
+__global__ void k_make_coef(Coef<T>* coef, int K, int J, double alpha) {
   int nclass = J + 2;
   for (int e = threadIdx.x; e < nclass * (K + 1); e += blockDim.x) {
     int cls = e / (K + 1), k = e % (K + 1);
     double a = cls == 0 ? 1.0 : alpha;
     double s = cls == 0 ? 0.0 : ldexp(1.0, cls - 1);
     double h2 = ldexp(1.0, -2 * k);
-    Coef<double> c;
-    c.c = 4.0 * a + s * h2 / 2.0;
-    c.ax = -a + s * h2 / 12.0;
-    c.dg = s * h2 / 12.0;
-    c.inv_c = 1.0 / c.c;
+    const double cc = 4.0 * a + s * h2 / 2.0;
+    const double ax = -a + s * h2 / 12.0, dg = s * h2 / 12.0;
+    const double cc_coarse = 4.0 * a + s * (h2 * 4.0) / 2.0;  // level k - 1
+    Coef<T> c;
+    c.c = (T)cc;
+    c.ax = (T)ax;
+    c.dg = (T)dg;
+    c.inv_c = (T)(1.0 / cc);
+    c.axs = (T)(ax / cc);
+    c.dgs = (T)(dg / cc);
+    c.rho = (T)(cc / cc_coarse);
+    c.pad = T(0);
     coef[e] = c;
   }
 }
@@ -37,6 +45,22 @@ __device__ __forceinline__ Coef<T> slice_coef(const Coef<T>* coef, int coef_clas
                                               int level) {
   int cls = coef_class >= 0 ? coef_class : 1 + wavelet_row_level(slice, J);
   return coef[cls * (K + 1) + level];
+}
+
+// ---------------------------------------------------------------------------------------
+// Nested P1 prolongation: the value of P xc at fine grid node (i, j) (1-based grid indices):
+// the coarse value at even-even nodes, the average of the two coarse end points at the
+// midpoints of horizontal, vertical and (1,1)-diagonal coarse edges; coarse boundary values 0.
+// ---------------------------------------------------------------------------------------
+// Branch-free: with (I, J) = (i >> 1, j >> 1) the value is the average of the coarse values at
+// (I, J) and (I + i mod 2, J + j mod 2); at even-even nodes both are the same node and the
+// average is exact.
+template <typename T>
+__device__ __forceinline__ T prolong_value(const T* __restrict__ cs, int nc, int i, int j) {
+  const int I0 = i >> 1, J0 = j >> 1, I1 = I0 + (i & 1), J1 = J0 + (j & 1);
+  const T a = (I0 >= 1 && I0 <= nc && J0 >= 1 && J0 <= nc) ? cs[(J0 - 1) * nc + (I0 - 1)] : T(0);
+  const T b = (I1 >= 1 && I1 <= nc && J1 >= 1 && J1 <= nc) ? cs[(J1 - 1) * nc + (I1 - 1)] : T(0);
+  return T(0.5) * (a + b);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -51,9 +75,11 @@ constexpr int kWR = 96;  // region width = 32 lanes x 3 columns
 
 // The sweep is out of place (x_in -> x_out): a block's halo overlaps its neighbours' interiors,
 // so reading and writing one buffer in the same launch would race.
-template <typename T, int NSW, int HR, bool DIAG>
+// With PROL the launch first adds the prolongated coarse correction P xc to the iterate it loads
+// (the coarse-grid correction of the V-cycle, fused into the first post-smoothing launch).
+template <typename T, int NSW, int HR, bool DIAG, bool PROL>
 __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T* __restrict__ x_in,
-                                                  const T* __restrict__ b, int n,
+                                                  const T* __restrict__ b, const T* __restrict__ xc, int n,
                                                   const Coef<T>* __restrict__ coef, int coef_class, int J,
                                                   int K, int level, int reverse, int zero_init) {
   constexpr int H = 3 * NSW;
@@ -68,6 +94,8 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
   T* xsl = x_out + off;
   const T* xin = x_in + off;
   const T* bsl = b + off;
+  const int nc = (n - 1) / 2;
+  const T* xcs = PROL ? xc + (int64_t)slice * nc * nc : nullptr;
   const int gx0 = blockIdx.x * TX - H;
   const int gy0 = blockIdx.y * TY - H;
   const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, level);
@@ -77,7 +105,13 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
     int gx = gx0 + rx, gy = gy0 + ry;
     bool in = gx >= 0 && gx < n && gy >= 0 && gy < n;
     int64_t gi = (int64_t)gy * n + gx;
-    xs[idx] = (in && !zero_init) ? xin[gi] : T(0);
+    if (PROL) {
+      T v = (in && !zero_init) ? xin[gi] : T(0);
+      if (in) v += prolong_value(xcs, nc, gx + 1, gy + 1);
+      xs[idx] = v;
+    } else {
+      xs[idx] = (in && !zero_init) ? xin[gi] : T(0);
+    }
     bs[idx] = in ? bsl[gi] : T(0);
   }
   __syncthreads();
@@ -90,18 +124,33 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
     const int lo = t + 1;
     const int ry_lo = max(lo, -gy0), ry_hi = min(HR - lo, n - gy0);
     const int rx_lo = max(lo, -gx0), rx_hi = min(kWR - lo, n - gx0);
-    for (int ry = ry_lo + warp; ry < ry_hi; ry += nwarp) {
-      const int gy = gy0 + ry;
-      // colour (gx + gy + 2) mod 3 == colour  <=>  rx == colour - 2 - gy - gx0 (mod 3)
-      int m = (colour - 2 - gy - gx0) % 3;
-      m += (m < 0) ? 3 : 0;
-      const int rx = 3 * lane + m;
-      if (rx >= rx_lo && rx < rx_hi) {
-        const int i = ry * kWR + rx;
-        T s4 = (xs[i - 1] + xs[i + 1]) + (xs[i - kWR] + xs[i + kWR]);
-        T v = bs[i] - cf.ax * s4;
-        if (DIAG) v -= cf.dg * (xs[i + kWR + 1] + xs[i - kWR - 1]);
-        xs[i] = v * cf.inv_c;
+    // each warp updates R rows per pass: all operands are gathered before any result is
+    // stored, so R independent FP64 chains are in flight (points of one colour never couple)
+    constexpr int R = 2;
+    for (int ry0 = ry_lo + warp; ry0 < ry_hi; ry0 += R * nwarp) {
+      T sa[R], sd[R], bv[R];
+      int at[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int ry = ry0 + q * nwarp;
+        const int gy = gy0 + ry;
+        // colour (gx + gy + 2) mod 3 == colour  <=>  rx == colour - 2 - gy - gx0 (mod 3)
+        int m = (colour - 2 - gy - gx0) % 3;
+        m += (m < 0) ? 3 : 0;
+        const int rx = 3 * lane + m;
+        const bool ok = ry < ry_hi && rx >= rx_lo && rx < rx_hi;
+        const int i = ok ? ry * kWR + rx : kWR + 1;  // a harmless interior address when idle
+        at[q] = ok ? i : -1;
+        sa[q] = (xs[i - 1] + xs[i + 1]) + (xs[i - kWR] + xs[i + kWR]);
+        sd[q] = DIAG ? (xs[i + kWR + 1] + xs[i - kWR - 1]) : T(0);
+        bv[q] = bs[i];
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        // scaled system: x = b' - (ax/c) s4 - (dg/c) s2 with b' = b / c
+        T v = bv[q] - cf.axs * sa[q];
+        if (DIAG) v -= cf.dgs * sd[q];
+        if (at[q] >= 0) xs[at[q]] = v;
       }
     }
     __syncthreads();
@@ -114,50 +163,20 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
   }
 }
 
-// r = b - C x on every point of every slice
-template <typename T, bool DIAG>
-__global__ void k_residual(T* __restrict__ r, const T* __restrict__ x, const T* __restrict__ b, int n,
-                           const Coef<T>* __restrict__ coef, int coef_class, int J, int K, int level) {
+// b' = b / c on the finest level (the multigrid's scaled right-hand side)
+template <typename T>
+__global__ void k_scale_rhs(T* __restrict__ bs, const T* __restrict__ b, int n, const Coef<T>* __restrict__ coef,
+                            int coef_class, int J, int K) {
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   const int slice = blockIdx.y;
-  const int64_t off = (int64_t)slice * N;
-  const T* xs = x + off;
-  const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, level);
-  const int iy = p / n, ix = p - iy * n;
-  const T xw = ix > 0 ? xs[p - 1] : T(0);
-  const T xe = ix < n - 1 ? xs[p + 1] : T(0);
-  const T xsth = iy > 0 ? xs[p - n] : T(0);
-  const T xn = iy < n - 1 ? xs[p + n] : T(0);
-  T s4 = (xw + xe) + (xsth + xn);
-  T v = b[off + p] - cf.ax * s4;
-  if (DIAG) {
-    const T xne = (ix < n - 1 && iy < n - 1) ? xs[p + n + 1] : T(0);
-    const T xsw = (ix > 0 && iy > 0) ? xs[p - n - 1] : T(0);
-    v -= cf.dg * (xne + xsw);
-  }
-  r[off + p] = v - cf.c * xs[p];
+  const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, K);
+  const int64_t i = (int64_t)slice * N + p;
+  bs[i] = b[i] * cf.inv_c;
 }
 
-// coarse rhs = P^T r: coarse node (I, J) collects fine node (2I, 2J) with weight 1 and the
-// midpoints of its six coarse edges (axis and (1,1) diagonal directions) with weight 1/2.
-template <typename T>
-__global__ void k_restrict(T* __restrict__ bc, const T* __restrict__ r, int nc) {
-  const int Nc = nc * nc;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= Nc) return;
-  const int nf = 2 * nc + 1;
-  const int slice = blockIdx.y;
-  const T* rs = r + (int64_t)slice * nf * nf;
-  const int cy = q / nc, cx = q - cy * nc;
-  const int p = (2 * cy + 1) * nf + (2 * cx + 1);  // interior index of fine node (2I, 2J)
-  T e = (rs[p - 1] + rs[p + 1]) + (rs[p - nf] + rs[p + nf]) + (rs[p + nf + 1] + rs[p - nf - 1]);
-  bc[(int64_t)slice * Nc + q] = rs[p] + T(0.5) * e;
-}
-
-// x += P xc: nested P1 interpolation (coarse values at even-even fine nodes, averages of the
-// two coarse end points at midpoints of horizontal, vertical and (1,1)-diagonal edges).
+// x += P xc (used when there is no post-smoothing to fuse the correction into)
 template <typename T>
 __global__ void k_prolong_add(T* __restrict__ x, const T* __restrict__ xc, int nf) {
   const int N = nf * nf;
@@ -165,99 +184,201 @@ __global__ void k_prolong_add(T* __restrict__ x, const T* __restrict__ xc, int n
   if (p >= N) return;
   const int nc = (nf - 1) / 2;
   const int slice = blockIdx.y;
-  const T* cs = xc + (int64_t)slice * nc * nc;
   const int iy = p / nf, ix = p - iy * nf;
-  const int i = ix + 1, j = iy + 1;  // fine grid indices
-  // coarse value at coarse grid node (I, J) (zero on the boundary)
-  auto cv = [&](int I, int Jc) -> T {
-    return (I >= 1 && I <= nc && Jc >= 1 && Jc <= nc) ? cs[(Jc - 1) * nc + (I - 1)] : T(0);
-  };
-  T v;
-  if ((i & 1) == 0 && (j & 1) == 0) {
-    v = cv(i >> 1, j >> 1);
-  } else if ((j & 1) == 0) {
-    v = T(0.5) * (cv(i >> 1, j >> 1) + cv((i >> 1) + 1, j >> 1));
-  } else if ((i & 1) == 0) {
-    v = T(0.5) * (cv(i >> 1, j >> 1) + cv(i >> 1, (j >> 1) + 1));
-  } else {
-    v = T(0.5) * (cv(i >> 1, j >> 1) + cv((i >> 1) + 1, (j >> 1) + 1));
+  x[(int64_t)slice * N + p] += prolong_value(xc + (int64_t)slice * nc * nc, nc, ix + 1, iy + 1);
+}
+
+// ---------------------------------------------------------------------------------------
+// Residual and restriction in one pass: the coarse scaled right-hand side D_c^-1 P^T (b - C x)
+// on a tile of CTX x CTY coarse points.  Coarse point (cx, cy) is fine interior point (2cx+1, 2cy+1); its restriction reads
+// the fine residual there and at the midpoints of its six coarse edges, so the block forms the
+// residual on the (2 CTX + 1) x (2 CTY + 1) fine points it covers (neighbouring tiles share one
+// fine row/column) from x staged with a one-point halo.
+// ---------------------------------------------------------------------------------------
+constexpr int kRCX = 32, kRCY = 16;
+constexpr int kRFX = 2 * kRCX + 1, kRFY = 2 * kRCY + 1;  // residual points
+constexpr int kRXX = kRFX + 2, kRXY = kRFY + 2;          // x points (one-point halo)
+
+template <typename T, bool DIAG>
+__global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, const T* __restrict__ x,
+                                                           const T* __restrict__ b, int n,
+                                                           const Coef<T>* __restrict__ coef, int coef_class, int J,
+                                                           int K, int level) {
+  __shared__ T xs[kRXY * kRXX];
+  __shared__ T rs[kRFY * kRFX];
+  const int nc = (n - 1) / 2;
+  const int slice = blockIdx.z;
+  const int64_t off = (int64_t)slice * n * n;
+  const T* xsl = x + off;
+  const T* bsl = b + off;
+  const int cx0 = blockIdx.x * kRCX, cy0 = blockIdx.y * kRCY;
+  const int fx0 = 2 * cx0, fy0 = 2 * cy0;  // first residual point (fine interior index)
+  const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, level);
+  for (int idx = threadIdx.x; idx < kRXY * kRXX; idx += blockDim.x) {
+    const int ry = idx / kRXX, rx = idx - ry * kRXX;
+    const int gx = fx0 - 1 + rx, gy = fy0 - 1 + ry;
+    const bool in = gx >= 0 && gx < n && gy >= 0 && gy < n;
+    xs[idx] = in ? xsl[(int64_t)gy * n + gx] : T(0);
   }
-  x[(int64_t)slice * N + p] += v;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < kRFY * kRFX; idx += blockDim.x) {
+    const int ry = idx / kRFX, rx = idx - ry * kRFX;
+    const int gx = fx0 + rx, gy = fy0 + ry;
+    T r = T(0);
+    if (gx < n && gy < n) {
+      const int i = (ry + 1) * kRXX + (rx + 1);
+      // scaled residual r' = D^-1 (b - C x) = b' - x - (ax/c) s4 - (dg/c) s2
+      T s4 = (xs[i - 1] + xs[i + 1]) + (xs[i - kRXX] + xs[i + kRXX]);
+      T v = bsl[(int64_t)gy * n + gx] - cf.axs * s4;
+      if (DIAG) v -= cf.dgs * (xs[i + kRXX + 1] + xs[i - kRXX - 1]);
+      r = v - xs[i];
+    }
+    rs[idx] = r;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < kRCX * kRCY; idx += blockDim.x) {
+    const int ty = idx / kRCX, tx = idx - ty * kRCX;
+    const int cx = cx0 + tx, cy = cy0 + ty;
+    if (cx >= nc || cy >= nc) continue;
+    const int i = (2 * ty + 1) * kRFX + (2 * tx + 1);
+    T e = (rs[i - 1] + rs[i + 1]) + (rs[i - kRFX] + rs[i + kRFX]) + (rs[i + kRFX + 1] + rs[i - kRFX - 1]);
+    // coarse scaled rhs: D_c^-1 P^T D r' = (c / c_coarse) P^T r'
+    bc[(int64_t)slice * nc * nc + (int64_t)cy * nc + cx] = cf.rho * rs[i] + (T(0.5) * cf.rho) * e;
+  }
 }
 
 // exact solve on level 1 (one unknown per slice)
 template <typename T>
-__global__ void k_coarse1(T* __restrict__ x, const T* __restrict__ b, int nslices, const Coef<T>* __restrict__ coef,
-                          int coef_class, int J, int K) {
+__global__ void k_coarse1(T* __restrict__ x, const T* __restrict__ b, int nslices) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nslices) return;
-  const Coef<T> cf = slice_coef(coef, coef_class, s, J, K, 1);
-  x[s] = b[s] * cf.inv_c;
+  // one unknown: the scaled right-hand side is the solution
+  x[s] = b[s];
 }
 
-constexpr int kHR64 = 64;
 
-template <bool DIAG>
-cudaError_t gs_sweep(const st_handle_s* h, int k, int nslices, int cls, double* x_out, const double* x_in,
-                     const double* b, bool reverse, bool zero_init) {
-  constexpr int NSW = 1, HR = kHR64, H = 3 * NSW;
+template <typename T>
+const Coef<T>* coef_table(const st_handle_s* h);
+template <>
+const Coef<double>* coef_table<double>(const st_handle_s* h) {
+  return h->coef;
+}
+template <>
+const Coef<float>* coef_table<float>(const st_handle_s* h) {
+  return h->coef32;
+}
+
+// Tile shapes (chosen by measurement on GB300): binary64 is bound by the FP64 pipe, so one sweep
+// per launch keeps the halo recomputation small (3-point halo, 90 x 26 interior; 49 KB of shared
+// memory, 4 blocks per SM to hide shared-memory latency); binary32 is bound by memory, so the
+// pre- or post-smoothing sweeps are fused three to a launch (9-point halo, 78 x 46 interior,
+// 4 blocks per SM), reading x and b once and writing x once per three sweeps.
+template <typename T>
+struct SweepShape;
+#ifndef ST_GS_HR64
+#define ST_GS_HR64 32
+#endif
+#ifndef ST_GS_HR32
+#define ST_GS_HR32 64
+#endif
+#ifndef ST_GS_NSW32
+#define ST_GS_NSW32 3
+#endif
+template <>
+struct SweepShape<double> {
+  static constexpr int kFusedNSW = 1, kFusedHR = ST_GS_HR64, kSingleHR = ST_GS_HR64;
+};
+template <>
+struct SweepShape<float> {
+  static constexpr int kFusedNSW = ST_GS_NSW32, kFusedHR = ST_GS_HR32, kSingleHR = 64;
+};
+
+template <typename T, int NSW, int HR, bool DIAG, bool PROL>
+cudaError_t gs_launch(const st_handle_s* h, int k, int nslices, int cls, T* x_out, const T* x_in, const T* b,
+                      const T* xc, bool reverse, bool zero_init) {
+  constexpr int H = 3 * NSW;
   const int n = (1 << k) - 1;
   const int TX = kWR - 2 * H, TY = HR - 2 * H;
   dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, nslices);
-  const size_t smem = 2 * sizeof(double) * HR * kWR;
+  const size_t smem = 2 * sizeof(T) * HR * kWR;
   // profiled: the finest level, which carries three quarters of the sweep work
   const bool prof = (k == h->K) && prof_start(h);
-  k_gs_sweep<double, NSW, HR, DIAG><<<grid, 256, smem, h->stream>>>(x_out, x_in, b, n, h->coef, cls, h->J, h->K,
-                                                                     k, reverse ? 1 : 0, zero_init ? 1 : 0);
+  k_gs_sweep<T, NSW, HR, DIAG, PROL><<<grid, 256, smem, h->stream>>>(x_out, x_in, b, xc, n, coef_table<T>(h), cls,
+                                                                h->J, h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0);
   count_launch(h);
   if (prof) {
-    // per point and sweep: 3 adds + 1 fma + 1 mul (+ 1 add + 1 fma with diagonal couplings);
-    // bytes: read x and b, write x (x is not read on a zero-initialised sweep)
+    // per point and sweep: 3 adds + 1 fma (+ 1 add + 1 fma with diagonal couplings);
+    // bytes: read x and b, write x (x is not read when the launch starts from x = 0)
     const double pts = (double)n * n * nslices;
-    prof_stop(h, pts * NSW * (DIAG ? 7.0 : 5.0), pts * sizeof(double) * (zero_init ? 2.0 : 3.0));
+    prof_stop(h, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(T) * (zero_init ? 2.0 : 3.0));
   }
   return cudaGetLastError();
 }
 
+// nsw consecutive sweeps of one colour order from x_in (+ P xc if xc != nullptr) into x_out
+// (x_in == x_out is not allowed)
+template <typename T, bool DIAG>
+cudaError_t gs_sweeps(const st_handle_s* h, int k, int nslices, int cls, T* x_out, const T* x_in, const T* b,
+                      const T* xc, bool reverse, bool zero_init, int nsw) {
+  constexpr int F = SweepShape<T>::kFusedNSW, FHR = SweepShape<T>::kFusedHR, HR1 = SweepShape<T>::kSingleHR;
+  if (F > 1 && nsw == F) {
+    return xc ? gs_launch<T, F, FHR, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
+              : gs_launch<T, F, FHR, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+  }
+  return xc ? gs_launch<T, 1, HR1, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
+            : gs_launch<T, 1, HR1, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+}
+
 // One V-cycle on level k.  xb[0], xb[1] are the level's two iterate buffers and *cur the one
 // holding the iterate; every sweep moves it to the other buffer.
-template <bool DIAG>
-cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, double* const xb[2], int* cur,
-                   const double* b, bool x_is_zero) {
+template <typename T, bool DIAG>
+cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, T* const xb[2], int* cur, const T* b,
+                   bool x_is_zero) {
   const st::MGLevels& L = h->mg;
   const int n = (1 << k) - 1;
   const int N = n * n;
   cudaError_t e;
   if (k == L.kmin) {
-    k_coarse1<double><<<(nslices + 255) / 256, 256, 0, h->stream>>>(xb[*cur], b, nslices, h->coef, cls, h->J, h->K);
+    k_coarse1<T><<<(nslices + 255) / 256, 256, 0, h->stream>>>(xb[*cur], b, nslices);
     count_launch(h);
     return cudaGetLastError();
   }
-  for (int s = 0; s < h->cfg.n_pre; ++s) {
-    if ((e = gs_sweep<DIAG>(h, k, nslices, cls, xb[*cur ^ 1], xb[*cur], b, false, x_is_zero && s == 0)) != cudaSuccess)
+  for (int s = 0; s < h->cfg.n_pre;) {
+    const int nsw = (h->cfg.n_pre - s >= SweepShape<T>::kFusedNSW) ? SweepShape<T>::kFusedNSW : 1;
+    if ((e = gs_sweeps<T, DIAG>(h, k, nslices, cls, xb[*cur ^ 1], xb[*cur], b, nullptr, false,
+                                x_is_zero && s == 0, nsw)) != cudaSuccess)
       return e;
     *cur ^= 1;
+    s += nsw;
   }
   if (h->cfg.n_pre == 0 && x_is_zero) {
     // nothing smoothed yet: the iterate must hold zeros before the residual is formed
-    if ((e = cudaMemsetAsync(xb[*cur], 0, sizeof(double) * (size_t)N * nslices, h->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(xb[*cur], 0, sizeof(T) * (size_t)N * nslices, h->stream)) != cudaSuccess) return e;
   }
-  double* x = xb[*cur];
-  dim3 g1((N + 255) / 256, nslices);
-  k_residual<double, DIAG><<<g1, 256, 0, h->stream>>>(L.res[k], x, b, n, h->coef, cls, h->J, h->K, k);
+  T* x = xb[*cur];
+  T* bc = reinterpret_cast<T*>(L.bc[k - 1]);
   const int nc = (1 << (k - 1)) - 1;
-  dim3 g2((nc * nc + 255) / 256, nslices);
-  k_restrict<double><<<g2, 256, 0, h->stream>>>(L.bc[k - 1], L.res[k], nc);
+  dim3 gr((nc + kRCX - 1) / kRCX, (nc + kRCY - 1) / kRCY, nslices);
+  k_residual_restrict<T, DIAG><<<gr, 256, 0, h->stream>>>(bc, x, b, n, coef_table<T>(h), cls, h->J, h->K, k);
+  count_launch(h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  double* const xcb[2] = {L.xc[k - 1], L.xc2[k - 1]};
+  T* const xcb[2] = {reinterpret_cast<T*>(L.xc[k - 1]), reinterpret_cast<T*>(L.xc2[k - 1])};
   int ccur = 0;
-  if ((e = vcycle<DIAG>(h, k - 1, nslices, cls, xcb, &ccur, L.bc[k - 1], true)) != cudaSuccess) return e;
-  k_prolong_add<double><<<g1, 256, 0, h->stream>>>(x, xcb[ccur], n);
-  count_launch(h, 3);  // residual, restriction, prolongation
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  for (int s = 0; s < h->cfg.n_post; ++s) {
-    if ((e = gs_sweep<DIAG>(h, k, nslices, cls, xb[*cur ^ 1], xb[*cur], b, true, false)) != cudaSuccess) return e;
+  if ((e = vcycle<T, DIAG>(h, k - 1, nslices, cls, xcb, &ccur, bc, true)) != cudaSuccess) return e;
+  if (h->cfg.n_post == 0) {
+    dim3 g1((N + 255) / 256, nslices);
+    k_prolong_add<T><<<g1, 256, 0, h->stream>>>(x, xcb[ccur], n);
+    count_launch(h);
+    return cudaGetLastError();
+  }
+  for (int s = 0; s < h->cfg.n_post;) {
+    const int nsw = (h->cfg.n_post - s >= SweepShape<T>::kFusedNSW) ? SweepShape<T>::kFusedNSW : 1;
+    // the first post-smoothing launch also applies the coarse-grid correction x += P xc
+    if ((e = gs_sweeps<T, DIAG>(h, k, nslices, cls, xb[*cur ^ 1], xb[*cur], b, s == 0 ? xcb[ccur] : nullptr, true,
+                                false, nsw)) != cudaSuccess)
+      return e;
     *cur ^= 1;
+    s += nsw;
   }
   return cudaSuccess;
 }
@@ -265,35 +386,64 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, double* co
 }  // namespace
 
 cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, cudaStream_t s) {
-  k_make_coef<<<1, 256, 0, s>>>(coef, K, J, alpha);
+  k_make_coef<double><<<1, 256, 0, s>>>(coef, K, J, alpha);
   return cudaGetLastError();
 }
 
-cudaError_t mg_set_attributes() {
-  const int smem = 2 * sizeof(double) * kHR64 * kWR;
-  cudaError_t e = cudaFuncSetAttribute(k_gs_sweep<double, 1, kHR64, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gs_sweep<double, 1, kHR64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem);
+cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, cudaStream_t s) {
+  k_make_coef<float><<<1, 256, 0, s>>>(coef, K, J, alpha);
+  return cudaGetLastError();
 }
 
-cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const double* b, double* x) {
+template <typename T, int NSW, int HR>
+cudaError_t set_smem_attr() {
+  const int smem = 2 * sizeof(T) * HR * kWR;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gs_sweep<T, NSW, HR, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gs_sweep<T, NSW, HR, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gs_sweep<T, NSW, HR, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gs_sweep<T, NSW, HR, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+cudaError_t mg_set_attributes() {
+  cudaError_t e = set_smem_attr<double, SweepShape<double>::kFusedNSW, SweepShape<double>::kFusedHR>();
+  if (e == cudaSuccess) e = set_smem_attr<double, 1, SweepShape<double>::kSingleHR>();
+  if (e == cudaSuccess) e = set_smem_attr<float, SweepShape<float>::kFusedNSW, SweepShape<float>::kFusedHR>();
+  if (e == cudaSuccess) e = set_smem_attr<float, 1, SweepShape<float>::kSingleHR>();
+  return e;
+}
+
+template <typename T>
+cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x) {
   // class 0 (K_x: s = 0) has no diagonal couplings; the K_l classes do
   const bool diag = coef_class != 0;
-  double* const xb[2] = {x, h->Xalt};
+  T* const xb[2] = {x, reinterpret_cast<T*>(h->Xalt)};
   int cur = 0;
-  cudaError_t e = cudaSuccess;
+  T* bs = reinterpret_cast<T*>(h->Bs);
+  const int n = h->n;
+  dim3 gs((n * n + 255) / 256, nslices);
+  k_scale_rhs<T><<<gs, 256, 0, h->stream>>>(bs, b, n, coef_table<T>(h), coef_class, h->J, h->K);
+  count_launch(h);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   for (int c = 0; c < h->cfg.n_vcycles; ++c) {
-    e = diag ? vcycle<true>(h, h->K, nslices, coef_class, xb, &cur, b, c == 0)
-             : vcycle<false>(h, h->K, nslices, coef_class, xb, &cur, b, c == 0);
+    e = diag ? vcycle<T, true>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0)
+             : vcycle<T, false>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0);
     if (e != cudaSuccess) return e;
   }
-  const size_t bytes = sizeof(double) * (size_t)h->Nx * nslices;
+  const size_t bytes = sizeof(T) * (size_t)h->Nx * nslices;
   if (h->cfg.n_vcycles == 0) return cudaMemsetAsync(x, 0, bytes, h->stream);
   // an odd total number of sweeps leaves the iterate in the alternate buffer
-  if (cur == 1) return cudaMemcpyAsync(x, h->Xalt, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (cur == 1) return cudaMemcpyAsync(x, xb[1], bytes, cudaMemcpyDeviceToDevice, h->stream);
   return cudaSuccess;
 }
+
+template cudaError_t mg_apply<double>(const st_handle_s*, int, int, const double*, double*);
+template cudaError_t mg_apply<float>(const st_handle_s*, int, int, const float*, float*);
 
 }  // namespace st

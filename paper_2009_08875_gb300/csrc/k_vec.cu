@@ -28,16 +28,18 @@ __device__ double block_sum(double v) {
   return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(256) k_dot_partial(const double* __restrict__ a, const double* __restrict__ b,
-                                                     int64_t n, double* __restrict__ partials) {
+// inner products always accumulate in binary64, whatever the vectors' storage type
+template <typename Ta, typename Tb>
+__global__ void __launch_bounds__(256) k_dot_partial(const Ta* __restrict__ a, const Tb* __restrict__ b, int64_t n,
+                                                     double* __restrict__ partials) {
   double acc0 = 0.0, acc1 = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (; i + stride < n; i += 2 * stride) {
-    acc0 = fma(a[i], b[i], acc0);
-    acc1 = fma(a[i + stride], b[i + stride], acc1);
+    acc0 = fma((double)a[i], (double)b[i], acc0);
+    acc1 = fma((double)a[i + stride], (double)b[i + stride], acc1);
   }
-  if (i < n) acc0 = fma(a[i], b[i], acc0);
+  if (i < n) acc0 = fma((double)a[i], (double)b[i], acc0);
   double t = block_sum(acc0 + acc1);
   if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
@@ -71,10 +73,10 @@ __global__ void __launch_bounds__(256) k_dot_final(const double* __restrict__ pa
 }
 
 // w += alpha p;  r -= alpha q
-__global__ void __launch_bounds__(256) k_update_wr(double* __restrict__ w, double* __restrict__ r,
-                                                   const double* __restrict__ p, const double* __restrict__ q,
-                                                   int64_t n, const double* __restrict__ sc) {
-  const double alpha = sc[SC_ALPHA];
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_wr(T* __restrict__ w, T* __restrict__ r, const T* __restrict__ p,
+                                                   const T* __restrict__ q, int64_t n, const double* __restrict__ sc) {
+  const T alpha = (T)sc[SC_ALPHA];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
     w[i] = fma(alpha, p[i], w[i]);
@@ -83,21 +85,44 @@ __global__ void __launch_bounds__(256) k_update_wr(double* __restrict__ w, doubl
 }
 
 // p = z + beta p
-__global__ void __launch_bounds__(256) k_update_p(double* __restrict__ p, const double* __restrict__ z, int64_t n,
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_p(T* __restrict__ p, const T* __restrict__ z, int64_t n,
                                                   const double* __restrict__ sc) {
-  const double beta = sc[SC_BETA];
+  const T beta = (T)sc[SC_BETA];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) p[i] = fma(beta, p[i], z[i]);
 }
 
-__global__ void __launch_bounds__(256) k_copy(double* __restrict__ dst, const double* __restrict__ src, int64_t n) {
+// dst = src, converting the storage type (binary64 <-> binary32 rounds to nearest)
+template <typename Td, typename Ts>
+__global__ void __launch_bounds__(256) k_copy(Td* __restrict__ dst, const Ts* __restrict__ src, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = (Td)src[i];
 }
 
-__global__ void __launch_bounds__(256) k_zero(double* __restrict__ dst, int64_t n) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_zero(T* __restrict__ dst, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = T(0);
+}
+
+// w += d (binary64 accumulation of a binary32 correction)
+__global__ void __launch_bounds__(256) k_add_correction(double* __restrict__ w, const float* __restrict__ d,
+                                                        int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) w[i] += (double)d[i];
+}
+
+// r = f - q (binary64) and rs = r rounded to binary32
+__global__ void __launch_bounds__(256) k_residual_split(double* __restrict__ r, float* __restrict__ rs,
+                                                        const double* __restrict__ f, const double* __restrict__ q,
+                                                        int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double v = f[i] - q[i];
+    r[i] = v;
+    rs[i] = (float)v;
+  }
 }
 
 inline unsigned stream_grid(int64_t n) {
@@ -107,36 +132,68 @@ inline unsigned stream_grid(int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_dot(const st_handle_s* h, const double* a, const double* b, int64_t n, int slot, int op) {
-  k_dot_partial<<<kDotBlocks, kThreads, 0, h->stream>>>(a, b, n, h->partials);
+template <typename Ta, typename Tb>
+cudaError_t launch_dot(const st_handle_s* h, const Ta* a, const Tb* b, int64_t n, int slot, int op) {
+  k_dot_partial<Ta, Tb><<<kDotBlocks, kThreads, 0, h->stream>>>(a, b, n, h->partials);
   k_dot_final<<<1, kThreads, 0, h->stream>>>(h->partials, kDotBlocks, h->scal, slot, op);
   count_launch(h, 2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_wr(const st_handle_s* h, double* w, double* r, const double* p, const double* q,
-                             int64_t n) {
-  k_update_wr<<<stream_grid(n), kThreads, 0, h->stream>>>(w, r, p, q, n, h->scal);
+template <typename T>
+cudaError_t launch_update_wr(const st_handle_s* h, T* w, T* r, const T* p, const T* q, int64_t n) {
+  k_update_wr<T><<<stream_grid(n), kThreads, 0, h->stream>>>(w, r, p, q, n, h->scal);
   count_launch(h);
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_p(const st_handle_s* h, double* p, const double* z, int64_t n) {
-  k_update_p<<<stream_grid(n), kThreads, 0, h->stream>>>(p, z, n, h->scal);
+template <typename T>
+cudaError_t launch_update_p(const st_handle_s* h, T* p, const T* z, int64_t n) {
+  k_update_p<T><<<stream_grid(n), kThreads, 0, h->stream>>>(p, z, n, h->scal);
   count_launch(h);
   return cudaGetLastError();
 }
 
-cudaError_t launch_copy(const st_handle_s* h, double* dst, const double* src, int64_t n) {
-  k_copy<<<stream_grid(n), kThreads, 0, h->stream>>>(dst, src, n);
+template <typename Td, typename Ts>
+cudaError_t launch_copy(const st_handle_s* h, Td* dst, const Ts* src, int64_t n) {
+  k_copy<Td, Ts><<<stream_grid(n), kThreads, 0, h->stream>>>(dst, src, n);
   count_launch(h);
   return cudaGetLastError();
 }
 
-cudaError_t launch_zero(const st_handle_s* h, double* dst, int64_t n) {
-  k_zero<<<stream_grid(n), kThreads, 0, h->stream>>>(dst, n);
+template <typename T>
+cudaError_t launch_zero(const st_handle_s* h, T* dst, int64_t n) {
+  k_zero<T><<<stream_grid(n), kThreads, 0, h->stream>>>(dst, n);
   count_launch(h);
   return cudaGetLastError();
 }
+
+cudaError_t launch_add_correction(const st_handle_s* h, double* w, const float* d, int64_t n) {
+  k_add_correction<<<stream_grid(n), kThreads, 0, h->stream>>>(w, d, n);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, const double* f, const double* q,
+                                  int64_t n) {
+  k_residual_split<<<stream_grid(n), kThreads, 0, h->stream>>>(r, rs, f, q, n);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_dot<double, double>(const st_handle_s*, const double*, const double*, int64_t, int, int);
+template cudaError_t launch_dot<float, float>(const st_handle_s*, const float*, const float*, int64_t, int, int);
+template cudaError_t launch_dot<double, float>(const st_handle_s*, const double*, const float*, int64_t, int, int);
+template cudaError_t launch_update_wr<double>(const st_handle_s*, double*, double*, const double*, const double*,
+                                              int64_t);
+template cudaError_t launch_update_wr<float>(const st_handle_s*, float*, float*, const float*, const float*, int64_t);
+template cudaError_t launch_update_p<double>(const st_handle_s*, double*, const double*, int64_t);
+template cudaError_t launch_update_p<float>(const st_handle_s*, float*, const float*, int64_t);
+template cudaError_t launch_copy<double, double>(const st_handle_s*, double*, const double*, int64_t);
+template cudaError_t launch_copy<float, float>(const st_handle_s*, float*, const float*, int64_t);
+template cudaError_t launch_copy<float, double>(const st_handle_s*, float*, const double*, int64_t);
+template cudaError_t launch_copy<double, float>(const st_handle_s*, double*, const float*, int64_t);
+template cudaError_t launch_zero<double>(const st_handle_s*, double*, int64_t);
+template cudaError_t launch_zero<float>(const st_handle_s*, float*, int64_t);
 
 }  // namespace st

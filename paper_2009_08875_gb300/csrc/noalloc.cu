@@ -51,9 +51,8 @@ cudaError_t static_scratch(double** out) {
 
 // Carves the buffers mg_apply needs for h->mg.max_slices slices at space level h->K out of
 // the scratch starting at `base` (nullptr: only measure) and returns the doubles used: the
-// coefficient table (classes 0..2, levels 0..K), the second fine iterate, per coarse level two
-// iterates and a right-hand side, and a residual on every level above the coarsest.  Every
-// piece starts on a 256-byte boundary.
+// coefficient table (classes 0..2, levels 0..K), the second fine iterate, the scaled fine
+// right-hand side, and per coarse level two iterates and a right-hand side.  Every piece starts on a 256-byte boundary.
 size_t carve_scratch(st_handle_s* h, double* base) {
   size_t used = 0;
   auto carve = [&](size_t count) {
@@ -64,6 +63,7 @@ size_t carve_scratch(st_handle_s* h, double* base) {
   const size_t ns = (size_t)h->mg.max_slices;
   h->coef = reinterpret_cast<Coef<double>*>(carve((sizeof(Coef<double>) / sizeof(double)) * 3 * (h->K + 1)));
   h->Xalt = carve((size_t)h->Nx * ns);
+  h->Bs = carve((size_t)h->Nx * ns);
   for (int k = 1; k <= h->K; ++k) {
     const size_t nk = (size_t)((1 << k) - 1) * ((1 << k) - 1) * ns;
     if (k < h->K) {
@@ -71,7 +71,6 @@ size_t carve_scratch(st_handle_s* h, double* base) {
       h->mg.xc2[k] = carve(nk);
       h->mg.bc[k] = carve(nk);
     }
-    if (k > 1) h->mg.res[k] = carve(nk);
   }
   return used;
 }

@@ -17,6 +17,9 @@ namespace st {
 // (A_x: 5-point Laplacian; M_x: h^2/12 [6; 1 x 6] on the (i,j)-(i+1,j+1) triangulation).
 // One entry per (coefficient class, level).  Class 0 is K_x (a = 1, s = 0); class 1 + l is
 // K_l (a = alpha, s = 2^l), l = 0..J.
+// The multigrid works with the Jacobi-scaled system D^-1 C x = D^-1 b (D = the centre
+// coefficient of the level): Gauss-Seidel is invariant under that row scaling, and it saves the
+// division of every update.  The right-hand side of every level is stored scaled.
 // ---------------------------------------------------------------------------------------
 template <typename T>
 struct Coef {
@@ -24,6 +27,10 @@ struct Coef {
   T c;      // centre
   T ax;     // axis-neighbour coefficient
   T dg;     // diagonal-neighbour coefficient
+  T axs;    // ax / c
+  T dgs;    // dg / c
+  T rho;    // c of this level / c of the next coarser level (rescales restricted residuals)
+  T pad;
 };
 
 // Level |lambda| of in-place wavelet row i (rows 0 and 2^J: level 0; else J - ctz(i)).
@@ -44,8 +51,6 @@ struct MGLevels {
   double* xc[16];
   double* xc2[16];
   double* bc[16];
-  // residual on every level k > kmin (k = K included)
-  double* res[16];
 };
 
 }  // namespace st
@@ -59,13 +64,15 @@ struct st_handle_s {
   int device;
 
   st::MGLevels mg;
-  st::Coef<double>* coef;  // device, (J + 2) x (K + 1)
+  st::Coef<double>* coef;   // device, (J + 2) x (K + 1)
+  st::Coef<float>* coef32;  // the same table rounded to binary32 (mixed precision)
 
   // workspace, each N_t x N_x doubles unless noted
   double* U;       // single-scale state
   double* Y;       // 2 N_t slices: Y1 then Y2
   double* X;       // 2 N_t slices: K_x Y
   double* Xalt;    // 2 N_t slices: second iterate buffer of the finest multigrid level
+  double* Bs;      // 2 N_t slices: the finest level's scaled right-hand side D^-1 b
   double* Z;       // single-scale S u
   double* V1;      // wavelet ping-pong scratch
   double* V2;
@@ -77,6 +84,13 @@ struct st_handle_s {
   double* fhat;    // right-hand side (st_solve_host)
   double* w;       // solution (st_solve_host)
   double* u0;      // N_x doubles (st_solve_host)
+  float* xi;         // ST_MIXED_FP32 inner solve: correction, residual, direction,
+  float* ri;         //   preconditioned residual, S_hat direction (binary32, N_t x N_x)
+  float* pi;
+  float* zi;
+  float* qi;
+  int last_iters, last_outer;
+  double last_relres;
   double* partials;  // dot-product partial sums
   double* scal;      // PCG scalars (device)
   double* scal_host; // page-locked mirror
@@ -106,32 +120,50 @@ st_status cuda_fail(const char* where, cudaError_t e);
 // launchers (all enqueue on `s`; return cudaGetLastError())
 // ---------------------------------------------------------------------------------------
 cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, cudaStream_t s);
+cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, cudaStream_t s);
+
+// The operator launchers below are instantiated for T = double and T = float; the float
+// versions reuse the handle's double workspace (half of each buffer).
 
 // x = K b on nslices slices of the finest level: n_vcycles V-cycles from zero.
 // coef_class < 0: per-slice class 1 + level(slice) (K_X); else a fixed class.
-cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const double* b, double* x);
+template <typename T>
+cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x);
 
 // wavelet transforms over N_t x N_x
-cudaError_t wavelet_synth(const st_handle_s* h, const double* w, double* u);
-cudaError_t wavelet_anal(const st_handle_s* h, const double* u, double* w);
+template <typename T>
+cudaError_t wavelet_synth(const st_handle_s* h, const T* w, T* u);
+template <typename T>
+cudaError_t wavelet_anal(const st_handle_s* h, const T* u, T* w);
 
 // Y1, Y2 (Y = [Y1; Y2]) from U: mode 0 (S): Y1 = A_t U M + L^T U A, Y2 = L U M + M_t U A;
 // mode 1 (right-hand side): Y1 = L^T G M, Y2 = M_t G M.
-cudaError_t launch_timemix(const st_handle_s* h, int mode, const double* U, double* Y);
-// Z = M X1 + A X2 + e_0 (x) M row0   (row0: N_x doubles, added to row 0 only)
-cudaError_t launch_epilogue(const st_handle_s* h, const double* X, const double* row0, double* Z);
+template <typename T>
+cudaError_t launch_timemix(const st_handle_s* h, int mode, const T* U, T* Y);
+// Z = M X1 + A X2 + e_0 (x) M row0   (row0: N_x values, added to row 0 only)
+template <typename T>
+cudaError_t launch_epilogue(const st_handle_s* h, const T* X, const T* row0, T* Z);
 // Y = A_x X on nrows slices
-cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const double* X, double* Y);
+template <typename T>
+cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y);
 
-// vector kernels
-cudaError_t launch_dot(const st_handle_s* h, const double* a, const double* b, int64_t n, int slot, int op);
-cudaError_t launch_update_wr(const st_handle_s* h, double* w, double* r, const double* p, const double* q, int64_t n);
-cudaError_t launch_update_p(const st_handle_s* h, double* p, const double* z, int64_t n);
-cudaError_t launch_copy(const st_handle_s* h, double* dst, const double* src, int64_t n);
-cudaError_t launch_zero(const st_handle_s* h, double* dst, int64_t n);
+// vector kernels (dot products accumulate in binary64)
+template <typename Ta, typename Tb>
+cudaError_t launch_dot(const st_handle_s* h, const Ta* a, const Tb* b, int64_t n, int slot, int op);
+template <typename T>
+cudaError_t launch_update_wr(const st_handle_s* h, T* w, T* r, const T* p, const T* q, int64_t n);
+template <typename T>
+cudaError_t launch_update_p(const st_handle_s* h, T* p, const T* z, int64_t n);
+template <typename Td, typename Ts>
+cudaError_t launch_copy(const st_handle_s* h, Td* dst, const Ts* src, int64_t n);
+template <typename T>
+cudaError_t launch_zero(const st_handle_s* h, T* dst, int64_t n);
+cudaError_t launch_add_correction(const st_handle_s* h, double* w, const float* d, int64_t n);
+cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, const double* f, const double* q,
+                                  int64_t n);
 
 // PCG scalar slots in h->scal
-enum { SC_RHO = 0, SC_PQ = 1, SC_ALPHA = 2, SC_RHO_NEW = 3, SC_BETA = 4, SC_RHO0 = 5, SC_COUNT = 8 };
+enum { SC_RHO = 0, SC_PQ = 1, SC_ALPHA = 2, SC_RHO_NEW = 3, SC_BETA = 4, SC_RHO0 = 5, SC_OUTER = 6, SC_COUNT = 8 };
 // dot "op" after reduction into `slot`
 enum { DOT_STORE = 0, DOT_ALPHA = 1, DOT_BETA = 2, DOT_INIT = 3 };
 

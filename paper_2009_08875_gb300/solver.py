@@ -7,12 +7,12 @@ from . import _lib
 from ._lib import STError  # noqa: F401
 
 
-def _ptr(t, shape, name, device_ok=True):
+def _ptr(t, shape, name, device_ok=True, dtype=None):
     import torch
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch tensor")
-    if t.dtype != torch.float64:
-        raise TypeError(f"{name} must be float64")
+    if t.dtype != (dtype or torch.float64):
+        raise TypeError(f"{name} must be {dtype or torch.float64}")
     if device_ok and not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
     if not t.is_contiguous():
@@ -30,13 +30,15 @@ class Solver:
     """
 
     def __init__(self, K, J, domain=0, alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0,
-                 maxit=200, stream=None):
+                 maxit=200, precision="fp64", inner_tol=1e-5, inner_maxit=60, stream=None):
         import torch
         lib = _lib.load()
         cfg = _lib.StConfig()
         lib.st_default_config(ctypes.byref(cfg))
         cfg.alpha, cfg.n_vcycles, cfg.n_pre, cfg.n_post = alpha, n_vcycles, n_pre, n_post
         cfg.tol, cfg.tol_mode, cfg.maxit = tol, tol_mode, maxit
+        cfg.precision = {"fp64": _lib.ST_FP64, "mixed": _lib.ST_MIXED_FP32}[precision]
+        cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -87,6 +89,22 @@ class Solver:
 
     def apply_KX(self, r, z):
         _lib.check(_lib.load().st_apply_KX(self._h, _ptr(r, self.shape, "r"), _ptr(z, self.shape, "z")))
+
+    def apply_S_f32(self, w, q):
+        import torch
+        _lib.check(_lib.load().st_apply_S_f32(self._h, _ptr(w, self.shape, "w", dtype=torch.float32),
+                                              _ptr(q, self.shape, "q", dtype=torch.float32)))
+
+    def apply_KX_f32(self, r, z):
+        import torch
+        _lib.check(_lib.load().st_apply_KX_f32(self._h, _ptr(r, self.shape, "r", dtype=torch.float32),
+                                               _ptr(z, self.shape, "z", dtype=torch.float32)))
+
+    def solve_info(self):
+        """Iterations, refinement steps and final relative residual of the last solve."""
+        out = _lib.StSolveInfo()
+        _lib.check(_lib.load().st_solve_info_get(self._h, ctypes.byref(out)))
+        return {"iterations": out.iterations, "outer_iterations": out.outer_iterations, "relres": out.relres}
 
     def rhs(self, g, u0, fhat):
         _lib.check(_lib.load().st_rhs(self._h, _ptr(g, self.shape, "g"), _ptr(u0, (self.Nx,), "u0"),

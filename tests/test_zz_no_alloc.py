@@ -46,7 +46,7 @@ def test_static_scratch_variant_matches_st_apply_Kx(K, ns):
 def test_sizes_beyond_the_static_maximum_are_rejected():
     lib = _lib.load()
     b = torch.zeros(1, dtype=torch.float64, device="cuda")
-    # K = 9 fits 4 slices in the 32 MiB array, not 5; nothing is launched
-    st = _static_kx(lib, 9, 5, b, b)
+    # K = 9 fits 5 slices in the 32 MiB array, not 6; nothing is launched
+    st = _static_kx(lib, 9, 6, b, b)
     assert st == _lib.ST_ERR_ARG
     assert "static maximum" in lib.st_last_error().decode()
