@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="precision of the main timed solve (profiling aid; the bench line uses fp64)")
     ap.add_argument("--oracle-sample-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -212,7 +214,7 @@ def run_ours(args):
 
     K, J = args.K, args.J
     g_np, u0_np, _ = inputs.manufactured(K, J)
-    solver = Solver(K, J, tol=TOL, tol_mode=0, maxit=500)
+    solver = Solver(K, J, tol=TOL, tol_mode=0, maxit=500, precision=args.precision)
     stream = solver.stream
     Nt, Nx = solver.shape
     N = Nt * Nx
