@@ -13,6 +13,10 @@
  * ---------------------------------------------------------------------------------------
  * Sizes.  Space level K >= 1: N_x = (2^K - 1)^2 interior nodes (Sec. 5.1).  Time level
  *   J >= 1: N_t = 2^J + 1 time nodes.
+ * Domains.  0: the unit square (Sec. 5.1).  1: the L-shape (0,1)^2 minus [1/2,1)^2 (not in the
+ *   paper), K >= 2; it is stored on the same (2^K - 1)^2 grid, and the grid nodes with
+ *   x >= 1/2 and y >= 1/2 (ix >= 2^(K-1) - 1 and iy >= 2^(K-1) - 1) are outside it: inputs must
+ *   hold zeros there and outputs hold zeros there.
  * Layout.  A space-time vector is a dense row-major array of N_t x N_x doubles (time
  *   slowest).  Column p = iy * (2^K - 1) + ix is interior grid node (ix + 1, iy + 1) at
  *   (x, y) = ((ix+1) h, (iy+1) h), h = 2^-K.
@@ -75,10 +79,12 @@ typedef struct {
  * tol 1e-10 relative, maxit 200, FP64; inner_tol 1e-5, inner_maxit 60. */
 void st_default_config(st_config* cfg);
 
-/* Creates a handle for the unit square at space level K (1..12) and time level J (1..14),
- * binds it to `cuda_stream` (a cudaStream_t; NULL = legacy default stream) and allocates
- * its device workspace (about 24 vectors of N_t x N_x doubles) on the current device.
- * `domain` must be 0 (unit square).  cfg may be NULL (defaults).  Synchronous. */
+/* Creates a handle for `domain` (0 unit square, 1 L-shape) at space level K (1..12; 2..12 for
+ * the L-shape) and time level J (1..14), binds it to `cuda_stream` (a cudaStream_t; NULL =
+ * legacy default stream) and allocates its device workspace (about 26 vectors of N_t x N_x
+ * doubles) on the current device.  The multigrid's coarsest level is 1 (one unknown) on the
+ * square and 2 (five unknowns, dense solve) on the L-shape.  cfg may be NULL (defaults).
+ * Synchronous. */
 st_status st_setup(st_handle* out, int domain, int space_level, int time_level,
                    const st_config* cfg, void* cuda_stream);
 

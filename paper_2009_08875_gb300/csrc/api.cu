@@ -332,8 +332,9 @@ st_status st_setup(st_handle* out, int domain, int space_level, int time_level, 
                    void* cuda_stream) {
   ST_REQUIRE(out != nullptr, "st_setup: null output pointer");
   *out = nullptr;
-  ST_REQUIRE(domain == 0, "st_setup: only domain 0 (unit square) is supported");
+  ST_REQUIRE(domain == 0 || domain == 1, "st_setup: domain must be 0 (unit square) or 1 (L-shape)");
   ST_REQUIRE(space_level >= 1 && space_level <= 12, "st_setup: space level must be in 1..12");
+  ST_REQUIRE(domain == 0 || space_level >= 2, "st_setup: the L-shape needs space level >= 2");
   ST_REQUIRE(time_level >= 1 && time_level <= 14, "st_setup: time level must be in 1..14");
   st_config c;
   st_default_config(&c);
@@ -368,7 +369,7 @@ st_status st_setup(st_handle* out, int domain, int space_level, int time_level, 
     return cuda_fail("cudaGetDevice", e);
   }
   h->mg.K = h->K;
-  h->mg.kmin = 1;
+  h->mg.kmin = domain == 1 ? 2 : 1;  // the L-shape has no unknown on level 1
   h->mg.max_slices = (int)(2 * h->Nt);
 
   const size_t V = (size_t)(h->Nt * h->Nx);

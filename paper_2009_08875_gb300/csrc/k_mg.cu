@@ -73,6 +73,47 @@ __device__ __forceinline__ T prolong_value(const T* __restrict__ cs, int nc, int
 // ---------------------------------------------------------------------------------------
 constexpr int kWR = 96;  // region width = 32 lanes x 3 columns
 
+// Exact solve on level 2 (3 x 3 grid, the coarsest level of the L-shape): one thread per slice
+// assembles C = a A + s M on the level's nodes (rows of nodes outside the domain become the
+// identity with zero right-hand side) and solves C x = D b' by Gaussian elimination (C is SPD on
+// the domain nodes, so no pivoting is needed).
+template <typename T>
+__global__ void k_coarse_dense3(T* __restrict__ x, const T* __restrict__ b, int nslices,
+                                const Coef<T>* __restrict__ coef, int coef_class, int J, int K, int lshape) {
+  const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= nslices) return;
+  const Coef<T> cf = slice_coef(coef, coef_class, sl, J, K, 2);
+  T A[9][10];
+  for (int p = 0; p < 9; ++p) {
+    for (int q = 0; q < 10; ++q) A[p][q] = T(0);
+    const int ix = p % 3, iy = p / 3;
+    if (outside_domain(ix, iy, 3, lshape)) {
+      A[p][p] = T(1);
+      continue;
+    }
+    A[p][p] = cf.c;
+    A[p][9] = cf.c * b[(int64_t)sl * 9 + p];
+    const int nb[6][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}, {1, 1}, {-1, -1}};
+    for (int t = 0; t < 6; ++t) {
+      const int jx = ix + nb[t][0], jy = iy + nb[t][1];
+      if (jx < 0 || jx > 2 || jy < 0 || jy > 2 || outside_domain(jx, jy, 3, lshape)) continue;
+      A[p][jy * 3 + jx] = t < 4 ? cf.ax : cf.dg;
+    }
+  }
+  for (int c = 0; c < 9; ++c) {
+    for (int r = c + 1; r < 9; ++r) {
+      const T f = A[r][c] / A[c][c];
+      for (int q = c; q < 10; ++q) A[r][q] -= f * A[c][q];
+    }
+  }
+  for (int r = 8; r >= 0; --r) {
+    T v = A[r][9];
+    for (int q = r + 1; q < 9; ++q) v -= A[r][q] * A[q][9];
+    A[r][9] = v / A[r][r];
+  }
+  for (int p = 0; p < 9; ++p) x[(int64_t)sl * 9 + p] = A[p][9];
+}
+
 // The sweep is out of place (x_in -> x_out): a block's halo overlaps its neighbours' interiors,
 // so reading and writing one buffer in the same launch would race.
 // With PROL the launch first adds the prolongated coarse correction P xc to the iterate it loads
@@ -81,7 +122,7 @@ template <typename T, int NSW, int HR, bool DIAG, bool PROL>
 __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T* __restrict__ x_in,
                                                   const T* __restrict__ b, const T* __restrict__ xc, int n,
                                                   const Coef<T>* __restrict__ coef, int coef_class, int J,
-                                                  int K, int level, int reverse, int zero_init) {
+                                                  int K, int level, int reverse, int zero_init, int lshape) {
   constexpr int H = 3 * NSW;
   constexpr int TX = kWR - 2 * H;
   constexpr int TY = HR - 2 * H;
@@ -103,7 +144,7 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
   for (int idx = threadIdx.x; idx < HR * kWR; idx += blockDim.x) {
     int ry = idx / kWR, rx = idx - ry * kWR;
     int gx = gx0 + rx, gy = gy0 + ry;
-    bool in = gx >= 0 && gx < n && gy >= 0 && gy < n;
+    bool in = gx >= 0 && gx < n && gy >= 0 && gy < n && !outside_domain(gx, gy, n, lshape);
     int64_t gi = (int64_t)gy * n + gx;
     if (PROL) {
       T v = (in && !zero_init) ? xin[gi] : T(0);
@@ -138,7 +179,7 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
         int m = (colour - 2 - gy - gx0) % 3;
         m += (m < 0) ? 3 : 0;
         const int rx = 3 * lane + m;
-        const bool ok = ry < ry_hi && rx >= rx_lo && rx < rx_hi;
+        const bool ok = ry < ry_hi && rx >= rx_lo && rx < rx_hi && !outside_domain(gx0 + rx, gy, n, lshape);
         const int i = ok ? ry * kWR + rx : kWR + 1;  // a harmless interior address when idle
         at[q] = ok ? i : -1;
         sa[q] = (xs[i - 1] + xs[i + 1]) + (xs[i - kWR] + xs[i + kWR]);
@@ -178,13 +219,14 @@ __global__ void k_scale_rhs(T* __restrict__ bs, const T* __restrict__ b, int n, 
 
 // x += P xc (used when there is no post-smoothing to fuse the correction into)
 template <typename T>
-__global__ void k_prolong_add(T* __restrict__ x, const T* __restrict__ xc, int nf) {
+__global__ void k_prolong_add(T* __restrict__ x, const T* __restrict__ xc, int nf, int lshape) {
   const int N = nf * nf;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   const int nc = (nf - 1) / 2;
   const int slice = blockIdx.y;
   const int iy = p / nf, ix = p - iy * nf;
+  if (outside_domain(ix, iy, nf, lshape)) return;
   x[(int64_t)slice * N + p] += prolong_value(xc + (int64_t)slice * nc * nc, nc, ix + 1, iy + 1);
 }
 
@@ -203,7 +245,7 @@ template <typename T, bool DIAG>
 __global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, const T* __restrict__ x,
                                                            const T* __restrict__ b, int n,
                                                            const Coef<T>* __restrict__ coef, int coef_class, int J,
-                                                           int K, int level) {
+                                                           int K, int level, int lshape) {
   __shared__ T xs[kRXY * kRXX];
   __shared__ T rs[kRFY * kRFX];
   const int nc = (n - 1) / 2;
@@ -217,7 +259,7 @@ __global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, c
   for (int idx = threadIdx.x; idx < kRXY * kRXX; idx += blockDim.x) {
     const int ry = idx / kRXX, rx = idx - ry * kRXX;
     const int gx = fx0 - 1 + rx, gy = fy0 - 1 + ry;
-    const bool in = gx >= 0 && gx < n && gy >= 0 && gy < n;
+    const bool in = gx >= 0 && gx < n && gy >= 0 && gy < n && !outside_domain(gx, gy, n, lshape);
     xs[idx] = in ? xsl[(int64_t)gy * n + gx] : T(0);
   }
   __syncthreads();
@@ -225,7 +267,7 @@ __global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, c
     const int ry = idx / kRFX, rx = idx - ry * kRFX;
     const int gx = fx0 + rx, gy = fy0 + ry;
     T r = T(0);
-    if (gx < n && gy < n) {
+    if (gx < n && gy < n && !outside_domain(gx, gy, n, lshape)) {
       const int i = (ry + 1) * kRXX + (rx + 1);
       // scaled residual r' = D^-1 (b - C x) = b' - x - (ax/c) s4 - (dg/c) s2
       T s4 = (xs[i - 1] + xs[i + 1]) + (xs[i - kRXX] + xs[i + kRXX]);
@@ -240,6 +282,10 @@ __global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, c
     const int ty = idx / kRCX, tx = idx - ty * kRCX;
     const int cx = cx0 + tx, cy = cy0 + ty;
     if (cx >= nc || cy >= nc) continue;
+    if (outside_domain(cx, cy, nc, lshape)) {
+      bc[(int64_t)slice * nc * nc + (int64_t)cy * nc + cx] = T(0);
+      continue;
+    }
     const int i = (2 * ty + 1) * kRFX + (2 * tx + 1);
     T e = (rs[i - 1] + rs[i + 1]) + (rs[i - kRFX] + rs[i + kRFX]) + (rs[i + kRFX + 1] + rs[i - kRFX - 1]);
     // coarse scaled rhs: D_c^-1 P^T D r' = (c / c_coarse) P^T r'
@@ -304,7 +350,8 @@ cudaError_t gs_launch(const st_handle_s* h, int k, int nslices, int cls, T* x_ou
   // profiled: the finest level, which carries three quarters of the sweep work
   const bool prof = (k == h->K) && prof_start(h);
   k_gs_sweep<T, NSW, HR, DIAG, PROL><<<grid, 256, smem, h->stream>>>(x_out, x_in, b, xc, n, coef_table<T>(h), cls,
-                                                                h->J, h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0);
+                                                                      h->J, h->K, k, reverse ? 1 : 0,
+                                                                      zero_init ? 1 : 0, h->domain);
   count_launch(h);
   if (prof) {
     // per point and sweep: 3 adds + 1 fma (+ 1 add + 1 fma with diagonal couplings);
@@ -339,7 +386,11 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, T* const x
   const int N = n * n;
   cudaError_t e;
   if (k == L.kmin) {
-    k_coarse1<T><<<(nslices + 255) / 256, 256, 0, h->stream>>>(xb[*cur], b, nslices);
+    if (k == 1)
+      k_coarse1<T><<<(nslices + 255) / 256, 256, 0, h->stream>>>(xb[*cur], b, nslices);
+    else
+      k_coarse_dense3<T><<<(nslices + 127) / 128, 128, 0, h->stream>>>(xb[*cur], b, nslices, coef_table<T>(h), cls,
+                                                                        h->J, h->K, h->domain);
     count_launch(h);
     return cudaGetLastError();
   }
@@ -359,7 +410,8 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, T* const x
   T* bc = reinterpret_cast<T*>(L.bc[k - 1]);
   const int nc = (1 << (k - 1)) - 1;
   dim3 gr((nc + kRCX - 1) / kRCX, (nc + kRCY - 1) / kRCY, nslices);
-  k_residual_restrict<T, DIAG><<<gr, 256, 0, h->stream>>>(bc, x, b, n, coef_table<T>(h), cls, h->J, h->K, k);
+  k_residual_restrict<T, DIAG><<<gr, 256, 0, h->stream>>>(bc, x, b, n, coef_table<T>(h), cls, h->J, h->K, k,
+                                                          h->domain);
   count_launch(h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   T* const xcb[2] = {reinterpret_cast<T*>(L.xc[k - 1]), reinterpret_cast<T*>(L.xc2[k - 1])};
@@ -367,7 +419,7 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, T* const x
   if ((e = vcycle<T, DIAG>(h, k - 1, nslices, cls, xcb, &ccur, bc, true)) != cudaSuccess) return e;
   if (h->cfg.n_post == 0) {
     dim3 g1((N + 255) / 256, nslices);
-    k_prolong_add<T><<<g1, 256, 0, h->stream>>>(x, xcb[ccur], n);
+    k_prolong_add<T><<<g1, 256, 0, h->stream>>>(x, xcb[ccur], n, h->domain);
     count_launch(h);
     return cudaGetLastError();
   }

@@ -88,11 +88,20 @@ __device__ __forceinline__ T tri_dot(const Tri<T>& t, T a, T b, T c) {
 // rows i-1, i, i+1 in registers (the chunk edges recompute one halo row).
 template <typename T>
 __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __restrict__ Y1, T* __restrict__ Y2,
-                                                 int n, int Nt, int chunk, T mh, TimeConsts<T> tk, int mode) {
+                                                 int n, int Nt, int chunk, T mh, TimeConsts<T> tk, int mode,
+                                                 int lshape) {
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   const int iy = p / n, ix = p - iy * n;
+  if (outside_domain(ix, iy, n, lshape)) {  // nodes outside the domain stay zero
+    const int i0 = blockIdx.y * chunk, i1 = min(Nt, i0 + chunk);
+    for (int i = i0; i < i1; ++i) {
+      Y1[(int64_t)i * N + p] = T(0);
+      Y2[(int64_t)i * N + p] = T(0);
+    }
+    return;
+  }
   const int i0 = blockIdx.y * chunk;
   const int i1 = min(Nt, i0 + chunk);
   T um_m = T(0), ua_m = T(0), um_c, ua_c, um_p = T(0), ua_p = T(0);
@@ -135,26 +144,31 @@ __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __r
 // Z_i = M X1_i + A X2_i (+ M row0 on row 0): the Schur epilogue (K_x already applied)
 template <typename T>
 __global__ void __launch_bounds__(256) k_epilogue(const T* __restrict__ X1, const T* __restrict__ X2,
-                                                  const T* __restrict__ row0, T* __restrict__ Z, int n, T mh) {
+                                                  const T* __restrict__ row0, T* __restrict__ Z, int n, T mh,
+                                                  int lshape) {
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   const int i = blockIdx.y;
   const int iy = p / n, ix = p - iy * n;
   const int64_t off = (int64_t)i * N;
+  if (outside_domain(ix, iy, n, lshape)) {
+    Z[off + p] = T(0);
+    return;
+  }
   T z = mass_of(load_nbr(X1 + off, p, ix, iy, n), mh) + stiff_of(load_nbr(X2 + off, p, ix, iy, n));
   if (i == 0 && row0 != nullptr) z += mass_of(load_nbr(row0, p, ix, iy, n), mh);
   Z[off + p] = z;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_apply_A(const T* __restrict__ X, T* __restrict__ Y, int n) {
+__global__ void __launch_bounds__(256) k_apply_A(const T* __restrict__ X, T* __restrict__ Y, int n, int lshape) {
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   const int iy = p / n, ix = p - iy * n;
   const int64_t off = (int64_t)blockIdx.y * N;
-  Y[off + p] = stiff_of(load_nbr(X + off, p, ix, iy, n));
+  Y[off + p] = outside_domain(ix, iy, n, lshape) ? T(0) : stiff_of(load_nbr(X + off, p, ix, iy, n));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -224,7 +238,7 @@ cudaError_t launch_timemix(const st_handle_s* h, int mode, const T* U, T* Y) {
   dim3 grid((N + 255) / 256, (int)((h->Nt + chunk - 1) / chunk));
   const double hx = ldexp(1.0, -h->K);
   k_timemix<T><<<grid, 256, 0, h->stream>>>(U, Y, Y + h->Nt * h->Nx, n, (int)h->Nt, chunk, (T)(hx * hx / 12.0),
-                                            time_consts<T>(h->J), mode);
+                                            time_consts<T>(h->J), mode, h->domain);
   count_launch(h);
   return cudaGetLastError();
 }
@@ -235,7 +249,7 @@ cudaError_t launch_epilogue(const st_handle_s* h, const T* X, const T* row0, T* 
   const int N = n * n;
   dim3 grid((N + 255) / 256, (int)h->Nt);
   const double hx = ldexp(1.0, -h->K);
-  k_epilogue<T><<<grid, 256, 0, h->stream>>>(X, X + h->Nt * h->Nx, row0, Z, n, (T)(hx * hx / 12.0));
+  k_epilogue<T><<<grid, 256, 0, h->stream>>>(X, X + h->Nt * h->Nx, row0, Z, n, (T)(hx * hx / 12.0), h->domain);
   count_launch(h);
   return cudaGetLastError();
 }
@@ -245,7 +259,7 @@ cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y) {
   const int n = h->n;
   const int N = n * n;
   dim3 grid((N + 255) / 256, nrows);
-  k_apply_A<T><<<grid, 256, 0, h->stream>>>(X, Y, n);
+  k_apply_A<T><<<grid, 256, 0, h->stream>>>(X, Y, n, h->domain);
   count_launch(h);
   return cudaGetLastError();
 }

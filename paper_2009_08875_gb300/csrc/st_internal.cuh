@@ -43,6 +43,15 @@ __host__ __device__ inline int wavelet_row_level(int i, int J) {
 #endif
 }
 
+// Domain mask.  On the L-shape (0,1)^2 minus [1/2,1)^2 the grid nodes with x >= 1/2 and y >= 1/2
+// are outside the domain or on its boundary; the library stores the full (2^k - 1)^2 grid and
+// keeps those nodes at zero.  With q = (n - 1) / 2 (the node x = 1/2 has interior index q) a
+// node (ix, iy) of a level with n points per side is outside iff ix >= q and iy >= q.
+__host__ __device__ inline bool outside_domain(int ix, int iy, int n, int lshape) {
+  const int q = (n - 1) >> 1;
+  return lshape && ix >= q && iy >= q;
+}
+
 struct MGLevels {
   int K;                 // finest level
   int kmin;              // coarsest level (exact solve)

@@ -79,3 +79,28 @@ def smooth_forcing(K: int, J: int, seed: int, domain: int = SQUARE, modes: int =
 def random_state(Nt: int, Nx: int, seed: int):
     """Standard-normal (N_t, N_x) array, seeded."""
     return np.random.default_rng(seed).standard_normal((Nt, Nx))
+
+
+def grid_mask(K: int, domain: int = SQUARE):
+    """Boolean mask over the (2^K - 1)^2 storage grid of the library: True at nodes of the domain."""
+    n = 2 ** K - 1
+    ix, iy = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    keep = np.ones((n, n), dtype=bool)
+    if domain == LSHAPE:
+        q = (n - 1) // 2
+        keep = ~((ix >= q) & (iy >= q))
+    return keep.ravel()
+
+
+def to_grid(K: int, domain: int, a):
+    """Place domain-node values (last axis in domain-node order) on the storage grid, zeros outside."""
+    a = np.asarray(a)
+    m = grid_mask(K, domain)
+    out = np.zeros(a.shape[:-1] + (m.size,), dtype=a.dtype)
+    out[..., m] = a
+    return out
+
+
+def from_grid(K: int, domain: int, a):
+    """Values at the domain nodes of a storage-grid array."""
+    return np.asarray(a)[..., grid_mask(K, domain)]
