@@ -24,6 +24,10 @@
  *   - wavelet vectors (w, f_hat, r, z, q): "in-place" lifting order: rows 0 and 2^J hold
  *     the level-0 coefficients c_0, row i = (2k + 1) 2^(J-j-1) holds d_j[k] (level j + 1).
  *     The paper lists the same coefficients as (c_0, d_0, ..., d_{J-1}) (Sec. 3.3).
+ * Batches.  A handle made by st_setup_batch holds B problems of the same domain, K and J; every
+ *   vector then holds B problems back to back (B x N_t x N_x, u0: B x N_x), every operator acts
+ *   on all of them, and each problem has its own PCG scalars and stop test.  A problem gives the
+ *   same bits alone and inside a batch.  st_setup is st_setup_batch with B = 1.
  * Memory.  Unless a name ends in _host, every vector pointer is a CUDA device pointer to
  *   caller-owned memory, 8-byte aligned, not aliased with any other argument of the
  *   same call.  The handle owns its internal workspace (allocated by st_setup).
@@ -55,10 +59,13 @@ typedef enum {
 
 typedef enum {
   ST_FP64 = 0,           /* every operation in IEEE binary64                              */
-  ST_MIXED_FP32 = 1      /* binary64 iterative refinement around a binary32 inner PCG:
+  ST_MIXED_FP32 = 1,     /* binary64 iterative refinement around a binary32 inner PCG:
                             the outer residual f_hat - S_hat w uses the binary64 S (with
                             its binary64 K_x), corrections and sums are binary64; the inner
                             solve runs S_hat and K_X in binary32 with binary64 inner products */
+  ST_MIXED_PRECOND = 2   /* one binary64 PCG (binary64 S_hat, recurrences and inner products)
+                            preconditioned by K_X in binary32, with the flexible (Polak-Ribiere)
+                            beta = r^T (z - z_old) / rho_old */
 } st_precision;
 
 typedef struct {
@@ -88,13 +95,20 @@ void st_default_config(st_config* cfg);
 st_status st_setup(st_handle* out, int domain, int space_level, int time_level,
                    const st_config* cfg, void* cuda_stream);
 
+/* As st_setup for a batch of B independent problems (B >= 1, 2 B N_t <= 65535). */
+st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_level, int batch,
+                         const st_config* cfg, void* cuda_stream);
+
+/* Reports the batch size B of the handle. */
+st_status st_batch_size(st_handle h, int* B);
+
 /* Frees the workspace (after synchronising the bound stream).  NULL is accepted. */
 st_status st_destroy(st_handle h);
 
 /* Reports N_t and N_x of the handle. */
 st_status st_dims(st_handle h, int64_t* Nt, int64_t* Nx);
 
-/* x[s] = K_x b[s] for slices s < nslices (nslices <= 2 N_t), each of N_x doubles:
+/* x[s] = K_x b[s] for slices s < nslices (nslices <= 2 B N_t), each of N_x doubles:
  * K_x ~ A_x^-1 is n_vcycles symmetric V-cycles from zero on A_x (Sec. 3.1, Sec. 5.1).
  * b and x must not overlap. */
 st_status st_apply_Kx(st_handle h, int nslices, const double* b, double* x);
@@ -132,22 +146,25 @@ st_status st_rhs(st_handle h, const double* g_nodal, const double* u0_nodal, dou
  * Returns ST_ERR_MAXIT (w holds the last iterate) or ST_ERR_BREAKDOWN on failure. */
 st_status st_pcg_solve(st_handle h, const double* fhat, double* w, int* iters, double* relres);
 
-/* Statistics of the last st_pcg_solve / st_solve_host on the handle. */
+/* Statistics of the last st_pcg_solve / st_solve_host on the handle (maxima over the batch). */
 typedef struct {
   int iterations;        /* PCG iterations (binary32 inner iterations for ST_MIXED_FP32) */
-  int outer_iterations;  /* refinement steps (binary64 S_hat applications); 0 for ST_FP64 */
+  int outer_iterations;  /* refinement steps (binary64 S_hat applications); 0 otherwise   */
   double relres;         /* final sqrt(r^T K_X r / r_0^T K_X r_0)                        */
 } st_solve_info;
 st_status st_solve_info_get(st_handle h, st_solve_info* out);
+
+/* The same for problem b of the batch; *status (may be NULL) receives its st_status. */
+st_status st_problem_info(st_handle h, int b, st_solve_info* out, int* status);
 
 /* The binary32 operators of the ST_MIXED_FP32 inner solve (same definitions as st_apply_S and
  * st_apply_KX; float device vectors of N_t x N_x in wavelet order).  Valid on any handle. */
 st_status st_apply_S_f32(st_handle h, const float* w, float* q);
 st_status st_apply_KX_f32(st_handle h, const float* r, float* z);
 
-/* End-to-end solve from host memory: copies g_nodal_host (N_t x N_x) and u0_host (N_x)
+/* End-to-end solve from host memory: copies g_nodal_host (B x N_t x N_x) and u0_host (B x N_x)
  * to the device, forms f_hat, runs PCG, synthesises u = W w and copies u to u_host
- * (N_t x N_x).  Host buffers should be page-locked for full copy bandwidth.
+ * (B x N_t x N_x).  Host buffers should be page-locked for full copy bandwidth.
  * Synchronous.  Returns like st_pcg_solve. */
 st_status st_solve_host(st_handle h, const double* g_nodal_host, const double* u0_host,
                         double* u_host, int* iters, double* relres);

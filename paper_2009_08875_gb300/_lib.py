@@ -25,7 +25,7 @@ class StSolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("relres", ctypes.c_double)]
 
 
-ST_FP64, ST_MIXED_FP32 = 0, 1
+ST_FP64, ST_MIXED_FP32, ST_MIXED_PRECOND = 0, 1, 2
 
 
 class StProfile(ctypes.Structure):
@@ -46,6 +46,10 @@ _SIGS = {
     "st_default_config": (None, [ctypes.POINTER(StConfig)]),
     "st_setup": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(StConfig), _P]),
+    "st_setup_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(StConfig), _P]),
+    "st_batch_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "st_problem_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(StSolveInfo), ctypes.POINTER(ctypes.c_int)]),
     "st_destroy": (ctypes.c_int, [_P]),
     "st_dims": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "st_apply_Kx": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),

@@ -93,6 +93,10 @@ __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __r
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
+  const int64_t poff = (int64_t)blockIdx.z * Nt * N;  // problem blockIdx.z of the batch
+  U += poff;
+  Y1 += poff;
+  Y2 += poff;
   const int iy = p / n, ix = p - iy * n;
   if (outside_domain(ix, iy, n, lshape)) {  // nodes outside the domain stay zero
     const int i0 = blockIdx.y * chunk, i1 = min(Nt, i0 + chunk);
@@ -144,12 +148,17 @@ __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __r
 // Z_i = M X1_i + A X2_i (+ M row0 on row 0): the Schur epilogue (K_x already applied)
 template <typename T>
 __global__ void __launch_bounds__(256) k_epilogue(const T* __restrict__ X1, const T* __restrict__ X2,
-                                                  const T* __restrict__ row0, T* __restrict__ Z, int n, T mh,
-                                                  int lshape) {
+                                                  const T* __restrict__ row0, int64_t row0_stride, T* __restrict__ Z,
+                                                  int n, int Nt, T mh, int lshape) {
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   const int i = blockIdx.y;
+  const int64_t poff = (int64_t)blockIdx.z * Nt * N;  // problem blockIdx.z of the batch
+  X1 += poff;
+  X2 += poff;
+  Z += poff;
+  if (row0 != nullptr) row0 += blockIdx.z * row0_stride;
   const int iy = p / n, ix = p - iy * n;
   const int64_t off = (int64_t)i * N;
   if (outside_domain(ix, iy, n, lshape)) {
@@ -186,6 +195,10 @@ __global__ void k_wsynth(const T* __restrict__ C, const T* __restrict__ D, T* __
                          int J, T s) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= Nx) return;
+  const int64_t poff = (int64_t)blockIdx.z * (((int64_t)1 << J) + 1) * Nx;  // problem of the batch
+  C += poff;
+  D += poff;
+  X += poff;
   const int k = blockIdx.y;  // 0 .. 2^j
   const int nw = 1 << j;
   const int sf = 1 << (J - j - 1);  // fine stride in rows
@@ -207,6 +220,10 @@ template <typename T>
 __global__ void k_wanal(const T* __restrict__ Xf, T* C, T* D, int64_t Nx, int j, int J, T s) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= Nx) return;
+  const int64_t poff = (int64_t)blockIdx.z * (((int64_t)1 << J) + 1) * Nx;  // problem of the batch
+  Xf += poff;
+  C += poff;
+  D += poff;
   const int k = blockIdx.y;
   const int nw = 1 << j;
   const int sf = 1 << (J - j - 1);
@@ -231,25 +248,27 @@ TimeConsts<T> time_consts(int J) {
 }  // namespace
 
 template <typename T>
-cudaError_t launch_timemix(const st_handle_s* h, int mode, const T* U, T* Y) {
+cudaError_t launch_timemix(const st_handle_s* h, int nb, int mode, const T* U, T* Y) {
   const int n = h->n;
   const int N = n * n;
   const int chunk = 32;
-  dim3 grid((N + 255) / 256, (int)((h->Nt + chunk - 1) / chunk));
+  dim3 grid((N + 255) / 256, (int)((h->Nt + chunk - 1) / chunk), nb);
   const double hx = ldexp(1.0, -h->K);
-  k_timemix<T><<<grid, 256, 0, h->stream>>>(U, Y, Y + h->Nt * h->Nx, n, (int)h->Nt, chunk, (T)(hx * hx / 12.0),
+  k_timemix<T><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, chunk,
+                                            (T)(hx * hx / 12.0),
                                             time_consts<T>(h->J), mode, h->domain);
   count_launch(h);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_epilogue(const st_handle_s* h, const T* X, const T* row0, T* Z) {
+cudaError_t launch_epilogue(const st_handle_s* h, int nb, const T* X, const T* row0, int64_t row0_stride, T* Z) {
   const int n = h->n;
   const int N = n * n;
-  dim3 grid((N + 255) / 256, (int)h->Nt);
+  dim3 grid((N + 255) / 256, (int)h->Nt, nb);
   const double hx = ldexp(1.0, -h->K);
-  k_epilogue<T><<<grid, 256, 0, h->stream>>>(X, X + h->Nt * h->Nx, row0, Z, n, (T)(hx * hx / 12.0), h->domain);
+  k_epilogue<T><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt,
+                                             (T)(hx * hx / 12.0), h->domain);
   count_launch(h);
   return cudaGetLastError();
 }
@@ -268,7 +287,7 @@ cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y) {
 // w, and writes level j+1 into a buffer that differs from the one it reads; the last stage
 // writes u.  Scratch buffers V1/V2 alternate.
 template <typename T>
-cudaError_t wavelet_synth(const st_handle_s* h, const T* w, T* u) {
+cudaError_t wavelet_synth(const st_handle_s* h, int nb, const T* w, T* u) {
   const int J = h->J;
   const int64_t Nx = h->Nx;
   const unsigned gx = (unsigned)((Nx + 255) / 256);
@@ -277,7 +296,7 @@ cudaError_t wavelet_synth(const st_handle_s* h, const T* w, T* u) {
   const T* src = w;
   for (int j = 0; j < J; ++j) {
     T* dst = (j == J - 1) ? u : (((J - 1 - j) & 1) ? V1 : V2);
-    dim3 grid(gx, (1u << j) + 1);
+    dim3 grid(gx, (1u << j) + 1, nb);
     k_wsynth<T><<<grid, 256, 0, h->stream>>>(src, w, dst, Nx, j, J, (T)sqrt(ldexp(1.0, j + 1)));
     count_launch(h);
     cudaError_t e = cudaGetLastError();
@@ -290,7 +309,7 @@ cudaError_t wavelet_synth(const st_handle_s* h, const T* w, T* u) {
 // w = W^T u = diag(W_{J-1}^T, I) M_{J-1}^T u: stage J-1 first.  c goes to alternating
 // scratch buffers, d straight to w; stage 0 writes c_0 into rows 0 and 2^J of w.
 template <typename T>
-cudaError_t wavelet_anal(const st_handle_s* h, const T* u, T* w) {
+cudaError_t wavelet_anal(const st_handle_s* h, int nb, const T* u, T* w) {
   const int J = h->J;
   const int64_t Nx = h->Nx;
   const unsigned gx = (unsigned)((Nx + 255) / 256);
@@ -299,7 +318,7 @@ cudaError_t wavelet_anal(const st_handle_s* h, const T* u, T* w) {
   const T* src = u;
   for (int j = J - 1; j >= 0; --j) {
     T* cdst = (j == 0) ? w : ((j & 1) ? V1 : V2);
-    dim3 grid(gx, (1u << j) + 1);
+    dim3 grid(gx, (1u << j) + 1, nb);
     k_wanal<T><<<grid, 256, 0, h->stream>>>(src, cdst, w, Nx, j, J, (T)sqrt(ldexp(1.0, j + 1)));
     count_launch(h);
     cudaError_t e = cudaGetLastError();
@@ -309,12 +328,12 @@ cudaError_t wavelet_anal(const st_handle_s* h, const T* u, T* w) {
   return cudaSuccess;
 }
 
-#define ST_INSTANTIATE(T)                                                                 \
-  template cudaError_t launch_timemix<T>(const st_handle_s*, int, const T*, T*);          \
-  template cudaError_t launch_epilogue<T>(const st_handle_s*, const T*, const T*, T*);    \
-  template cudaError_t launch_apply_A<T>(const st_handle_s*, int, const T*, T*);          \
-  template cudaError_t wavelet_synth<T>(const st_handle_s*, const T*, T*);                \
-  template cudaError_t wavelet_anal<T>(const st_handle_s*, const T*, T*);
+#define ST_INSTANTIATE(T)                                                                           \
+  template cudaError_t launch_timemix<T>(const st_handle_s*, int, int, const T*, T*);               \
+  template cudaError_t launch_epilogue<T>(const st_handle_s*, int, const T*, const T*, int64_t, T*); \
+  template cudaError_t launch_apply_A<T>(const st_handle_s*, int, const T*, T*);                    \
+  template cudaError_t wavelet_synth<T>(const st_handle_s*, int, const T*, T*);                     \
+  template cudaError_t wavelet_anal<T>(const st_handle_s*, int, const T*, T*);
 ST_INSTANTIATE(double)
 ST_INSTANTIATE(float)
 #undef ST_INSTANTIATE

@@ -28,10 +28,15 @@ __device__ double block_sum(double v) {
   return t;  // valid in thread 0
 }
 
-// inner products always accumulate in binary64, whatever the vectors' storage type
+// inner products always accumulate in binary64, whatever the vectors' storage type.  Problem
+// blockIdx.y of a batch owns elements [y n, (y + 1) n); its partial sums go to
+// partials[y * gridDim.x + blockIdx.x].  The partition depends only on n, so a problem gives the
+// same bits alone and inside any batch.
 template <typename Ta, typename Tb>
 __global__ void __launch_bounds__(256) k_dot_partial(const Ta* __restrict__ a, const Tb* __restrict__ b, int64_t n,
                                                      double* __restrict__ partials) {
+  a += (int64_t)blockIdx.y * n;
+  b += (int64_t)blockIdx.y * n;
   double acc0 = 0.0, acc1 = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -41,27 +46,39 @@ __global__ void __launch_bounds__(256) k_dot_partial(const Ta* __restrict__ a, c
   }
   if (i < n) acc0 = fma((double)a[i], (double)b[i], acc0);
   double t = block_sum(acc0 + acc1);
-  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
-__global__ void __launch_bounds__(256) k_dot_final(const double* __restrict__ partials, int nb,
-                                                   double* __restrict__ sc, int slot, int op) {
+// one block per problem: sum its partials and update its PCG scalars.  act (may be null) marks
+// the problems still iterating; a finished problem gets alpha = beta = 0, so the updates leave
+// its vectors unchanged while the others go on.
+__global__ void __launch_bounds__(256) k_dot_final(const double* __restrict__ partials, int nb_per,
+                                                   double* __restrict__ scal, const int* __restrict__ act, int slot,
+                                                   int op) {
+  const int prob = blockIdx.x;
   double acc = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partials[i];
+  for (int i = threadIdx.x; i < nb_per; i += blockDim.x) acc += partials[(int64_t)prob * nb_per + i];
   double t = block_sum(acc);
   if (threadIdx.x == 0) {
+    double* sc = scal + (int64_t)prob * SC_COUNT;
+    const bool on = act == nullptr || act[prob] != 0;
     switch (op) {
       case DOT_STORE:
         sc[slot] = t;
         break;
       case DOT_ALPHA:  // t = p^T q
         sc[SC_PQ] = t;
-        sc[SC_ALPHA] = sc[SC_RHO] / t;
+        sc[SC_ALPHA] = on ? sc[SC_RHO] / t : 0.0;
         break;
       case DOT_BETA:  // t = r^T z (new)
         sc[SC_RHO_NEW] = t;
-        sc[SC_BETA] = t / sc[SC_RHO];
-        sc[SC_RHO] = t;
+        sc[SC_BETA] = on ? t / sc[SC_RHO] : 0.0;
+        if (on) sc[SC_RHO] = t;
+        break;
+      case DOT_BETA_FLEX:  // t = r^T z (new); slot SC_RZOLD holds r^T z_old (Polak-Ribiere)
+        sc[SC_RHO_NEW] = t;
+        sc[SC_BETA] = on ? (t - sc[SC_RZOLD]) / sc[SC_RHO] : 0.0;
+        if (on) sc[SC_RHO] = t;
         break;
       case DOT_INIT:  // t = r_0^T z_0
         sc[SC_RHO] = t;
@@ -72,15 +89,16 @@ __global__ void __launch_bounds__(256) k_dot_final(const double* __restrict__ pa
   }
 }
 
-// w += alpha p;  r -= alpha q
+// w += alpha p;  r -= alpha q  (problem blockIdx.y, elements [y n, (y+1) n))
 template <typename T>
 __global__ void __launch_bounds__(256) k_update_wr(T* __restrict__ w, T* __restrict__ r, const T* __restrict__ p,
                                                    const T* __restrict__ q, int64_t n, const double* __restrict__ sc) {
-  const T alpha = (T)sc[SC_ALPHA];
+  const T alpha = (T)sc[(int64_t)blockIdx.y * SC_COUNT + SC_ALPHA];
+  const int64_t off = (int64_t)blockIdx.y * n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    w[i] = fma(alpha, p[i], w[i]);
-    r[i] = fma(-alpha, q[i], r[i]);
+    w[off + i] = fma(alpha, p[off + i], w[off + i]);
+    r[off + i] = fma(-alpha, q[off + i], r[off + i]);
   }
 }
 
@@ -88,9 +106,11 @@ __global__ void __launch_bounds__(256) k_update_wr(T* __restrict__ w, T* __restr
 template <typename T>
 __global__ void __launch_bounds__(256) k_update_p(T* __restrict__ p, const T* __restrict__ z, int64_t n,
                                                   const double* __restrict__ sc) {
-  const T beta = (T)sc[SC_BETA];
+  const T beta = (T)sc[(int64_t)blockIdx.y * SC_COUNT + SC_BETA];
+  const int64_t off = (int64_t)blockIdx.y * n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) p[i] = fma(beta, p[i], z[i]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+    p[off + i] = fma(beta, p[off + i], z[off + i]);
 }
 
 // dst = src, converting the storage type (binary64 <-> binary32 rounds to nearest)
@@ -125,6 +145,19 @@ __global__ void __launch_bounds__(256) k_residual_split(double* __restrict__ r, 
   }
 }
 
+// blocks of the dot-product partition of one problem of n elements (depends on n only)
+inline int dot_blocks(int64_t n) {
+  int64_t g = (n + 8 * kThreads - 1) / (8 * kThreads);
+  return (int)(g < 1 ? 1 : (g > kDotBlocks ? kDotBlocks : g));
+}
+
+// blocks per problem of a batched elementwise update, about kDotBlocks in total
+inline unsigned per_problem_grid(int64_t n, int nb) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  int64_t cap = kDotBlocks / nb > 0 ? kDotBlocks / nb : 1;
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
 inline unsigned stream_grid(int64_t n) {
   int64_t g = (n + kThreads - 1) / kThreads;
   return (unsigned)(g < kDotBlocks ? (g > 0 ? g : 1) : kDotBlocks);
@@ -133,23 +166,24 @@ inline unsigned stream_grid(int64_t n) {
 }  // namespace
 
 template <typename Ta, typename Tb>
-cudaError_t launch_dot(const st_handle_s* h, const Ta* a, const Tb* b, int64_t n, int slot, int op) {
-  k_dot_partial<Ta, Tb><<<kDotBlocks, kThreads, 0, h->stream>>>(a, b, n, h->partials);
-  k_dot_final<<<1, kThreads, 0, h->stream>>>(h->partials, kDotBlocks, h->scal, slot, op);
+cudaError_t launch_dot(const st_handle_s* h, int nb, const Ta* a, const Tb* b, int64_t n, int slot, int op) {
+  const int nblk = dot_blocks(n);
+  k_dot_partial<Ta, Tb><<<dim3(nblk, nb), kThreads, 0, h->stream>>>(a, b, n, h->partials);
+  k_dot_final<<<nb, kThreads, 0, h->stream>>>(h->partials, nblk, h->scal, h->act, slot, op);
   count_launch(h, 2);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_update_wr(const st_handle_s* h, T* w, T* r, const T* p, const T* q, int64_t n) {
-  k_update_wr<T><<<stream_grid(n), kThreads, 0, h->stream>>>(w, r, p, q, n, h->scal);
+cudaError_t launch_update_wr(const st_handle_s* h, int nb, T* w, T* r, const T* p, const T* q, int64_t n) {
+  k_update_wr<T><<<dim3(per_problem_grid(n, nb), nb), kThreads, 0, h->stream>>>(w, r, p, q, n, h->scal);
   count_launch(h);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_update_p(const st_handle_s* h, T* p, const T* z, int64_t n) {
-  k_update_p<T><<<stream_grid(n), kThreads, 0, h->stream>>>(p, z, n, h->scal);
+cudaError_t launch_update_p(const st_handle_s* h, int nb, T* p, const T* z, int64_t n) {
+  k_update_p<T><<<dim3(per_problem_grid(n, nb), nb), kThreads, 0, h->stream>>>(p, z, n, h->scal);
   count_launch(h);
   return cudaGetLastError();
 }
@@ -181,14 +215,17 @@ cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, co
   return cudaGetLastError();
 }
 
-template cudaError_t launch_dot<double, double>(const st_handle_s*, const double*, const double*, int64_t, int, int);
-template cudaError_t launch_dot<float, float>(const st_handle_s*, const float*, const float*, int64_t, int, int);
-template cudaError_t launch_dot<double, float>(const st_handle_s*, const double*, const float*, int64_t, int, int);
-template cudaError_t launch_update_wr<double>(const st_handle_s*, double*, double*, const double*, const double*,
+template cudaError_t launch_dot<double, double>(const st_handle_s*, int, const double*, const double*, int64_t, int,
+                                                int);
+template cudaError_t launch_dot<float, float>(const st_handle_s*, int, const float*, const float*, int64_t, int, int);
+template cudaError_t launch_dot<double, float>(const st_handle_s*, int, const double*, const float*, int64_t, int,
+                                               int);
+template cudaError_t launch_update_wr<double>(const st_handle_s*, int, double*, double*, const double*, const double*,
                                               int64_t);
-template cudaError_t launch_update_wr<float>(const st_handle_s*, float*, float*, const float*, const float*, int64_t);
-template cudaError_t launch_update_p<double>(const st_handle_s*, double*, const double*, int64_t);
-template cudaError_t launch_update_p<float>(const st_handle_s*, float*, const float*, int64_t);
+template cudaError_t launch_update_wr<float>(const st_handle_s*, int, float*, float*, const float*, const float*,
+                                             int64_t);
+template cudaError_t launch_update_p<double>(const st_handle_s*, int, double*, const double*, int64_t);
+template cudaError_t launch_update_p<float>(const st_handle_s*, int, float*, const float*, int64_t);
 template cudaError_t launch_copy<double, double>(const st_handle_s*, double*, const double*, int64_t);
 template cudaError_t launch_copy<float, float>(const st_handle_s*, float*, const float*, int64_t);
 template cudaError_t launch_copy<float, double>(const st_handle_s*, float*, const double*, int64_t);

@@ -100,7 +100,14 @@ struct st_handle_s {
   float* qi;
   int last_iters, last_outer;
   double last_relres;
-  double* partials;  // dot-product partial sums
+  int B;             // problems in the batch (vectors are B x N_t x N_x)
+  int* act;          // device: 1 while problem b iterates (B ints)
+  int* act_host;     // page-locked mirror
+  int* info_iters;   // host, per problem: iterations, refinement steps, status
+  int* info_outer;
+  int* info_status;
+  double* info_relres;
+  double* partials;  // dot-product partial sums (B x kDotBlocks)
   double* scal;      // PCG scalars (device)
   double* scal_host; // page-locked mirror
 
@@ -139,30 +146,35 @@ cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, cu
 template <typename T>
 cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x);
 
+// The time-coupled launchers act on nb problems stored back to back (N_t x N_x each).
 // wavelet transforms over N_t x N_x
 template <typename T>
-cudaError_t wavelet_synth(const st_handle_s* h, const T* w, T* u);
+cudaError_t wavelet_synth(const st_handle_s* h, int nb, const T* w, T* u);
 template <typename T>
-cudaError_t wavelet_anal(const st_handle_s* h, const T* u, T* w);
+cudaError_t wavelet_anal(const st_handle_s* h, int nb, const T* u, T* w);
 
-// Y1, Y2 (Y = [Y1; Y2]) from U: mode 0 (S): Y1 = A_t U M + L^T U A, Y2 = L U M + M_t U A;
+// Y1, Y2 (Y = [Y1 of all nb problems; Y2 of all nb problems]) from U:
+// mode 0 (S): Y1 = A_t U M + L^T U A, Y2 = L U M + M_t U A;
 // mode 1 (right-hand side): Y1 = L^T G M, Y2 = M_t G M.
 template <typename T>
-cudaError_t launch_timemix(const st_handle_s* h, int mode, const T* U, T* Y);
-// Z = M X1 + A X2 + e_0 (x) M row0   (row0: N_x values, added to row 0 only)
+cudaError_t launch_timemix(const st_handle_s* h, int nb, int mode, const T* U, T* Y);
+// Z = M X1 + A X2 + e_0 (x) M row0 per problem (row0 of problem b at row0 + b row0_stride,
+// N_x values added to its row 0)
 template <typename T>
-cudaError_t launch_epilogue(const st_handle_s* h, const T* X, const T* row0, T* Z);
+cudaError_t launch_epilogue(const st_handle_s* h, int nb, const T* X, const T* row0, int64_t row0_stride, T* Z);
 // Y = A_x X on nrows slices
 template <typename T>
 cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y);
 
-// vector kernels (dot products accumulate in binary64)
+// vector kernels (dot products accumulate in binary64).  launch_dot, launch_update_wr and
+// launch_update_p act on nb problems of n elements each, with per-problem scalars
+// h->scal[b * SC_COUNT + slot] and the per-problem active flags h->act.
 template <typename Ta, typename Tb>
-cudaError_t launch_dot(const st_handle_s* h, const Ta* a, const Tb* b, int64_t n, int slot, int op);
+cudaError_t launch_dot(const st_handle_s* h, int nb, const Ta* a, const Tb* b, int64_t n, int slot, int op);
 template <typename T>
-cudaError_t launch_update_wr(const st_handle_s* h, T* w, T* r, const T* p, const T* q, int64_t n);
+cudaError_t launch_update_wr(const st_handle_s* h, int nb, T* w, T* r, const T* p, const T* q, int64_t n);
 template <typename T>
-cudaError_t launch_update_p(const st_handle_s* h, T* p, const T* z, int64_t n);
+cudaError_t launch_update_p(const st_handle_s* h, int nb, T* p, const T* z, int64_t n);
 template <typename Td, typename Ts>
 cudaError_t launch_copy(const st_handle_s* h, Td* dst, const Ts* src, int64_t n);
 template <typename T>
@@ -172,9 +184,19 @@ cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, co
                                   int64_t n);
 
 // PCG scalar slots in h->scal
-enum { SC_RHO = 0, SC_PQ = 1, SC_ALPHA = 2, SC_RHO_NEW = 3, SC_BETA = 4, SC_RHO0 = 5, SC_OUTER = 6, SC_COUNT = 8 };
+enum {
+  SC_RHO = 0,
+  SC_PQ = 1,
+  SC_ALPHA = 2,
+  SC_RHO_NEW = 3,
+  SC_BETA = 4,
+  SC_RHO0 = 5,
+  SC_OUTER = 6,
+  SC_RZOLD = 7,
+  SC_COUNT = 8
+};
 // dot "op" after reduction into `slot`
-enum { DOT_STORE = 0, DOT_ALPHA = 1, DOT_BETA = 2, DOT_INIT = 3 };
+enum { DOT_STORE = 0, DOT_ALPHA = 1, DOT_BETA = 2, DOT_INIT = 3, DOT_BETA_FLEX = 4 };
 
 constexpr int kDotBlocks = 1216;  // 8 blocks x 152 SMs; fixed for deterministic reductions
 constexpr int kThreads = 256;

@@ -30,29 +30,36 @@ class Solver:
     """
 
     def __init__(self, K, J, domain=0, alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0,
-                 maxit=200, precision="fp64", inner_tol=1e-5, inner_maxit=60, stream=None):
+                 maxit=200, precision="fp64", inner_tol=1e-5, inner_maxit=60, batch=1, stream=None):
         import torch
         lib = _lib.load()
         cfg = _lib.StConfig()
         lib.st_default_config(ctypes.byref(cfg))
         cfg.alpha, cfg.n_vcycles, cfg.n_pre, cfg.n_post = alpha, n_vcycles, n_pre, n_post
         cfg.tol, cfg.tol_mode, cfg.maxit = tol, tol_mode, maxit
-        cfg.precision = {"fp64": _lib.ST_FP64, "mixed": _lib.ST_MIXED_FP32}[precision]
+        cfg.precision = {"fp64": _lib.ST_FP64, "mixed": _lib.ST_MIXED_FP32,
+                         "mixed_precond": _lib.ST_MIXED_PRECOND}[precision]
         cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
         h = ctypes.c_void_p()
-        _lib.check(lib.st_setup(ctypes.byref(h), domain, K, J, ctypes.byref(cfg), ctypes.c_void_p(stream.cuda_stream)))
+        _lib.check(lib.st_setup_batch(ctypes.byref(h), domain, K, J, batch, ctypes.byref(cfg),
+                                      ctypes.c_void_p(stream.cuda_stream)))
         self._h = h
         nt, nx = ctypes.c_int64(), ctypes.c_int64()
         _lib.check(lib.st_dims(h, ctypes.byref(nt), ctypes.byref(nx)))
         self.Nt, self.Nx = nt.value, nx.value
-        self.K, self.J = K, J
+        self.K, self.J, self.B = K, J, batch
 
     @property
     def shape(self):
-        return (self.Nt, self.Nx)
+        """Shape of a space-time vector: (N_t, N_x), or (B, N_t, N_x) for a batch."""
+        return (self.Nt, self.Nx) if self.B == 1 else (self.B, self.Nt, self.Nx)
+
+    @property
+    def u0_shape(self):
+        return (self.Nx,) if self.B == 1 else (self.B, self.Nx)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -106,8 +113,15 @@ class Solver:
         _lib.check(_lib.load().st_solve_info_get(self._h, ctypes.byref(out)))
         return {"iterations": out.iterations, "outer_iterations": out.outer_iterations, "relres": out.relres}
 
+    def problem_info(self, b):
+        """Iterations, refinement steps, final relative residual and status of problem b."""
+        out, st = _lib.StSolveInfo(), ctypes.c_int()
+        _lib.check(_lib.load().st_problem_info(self._h, b, ctypes.byref(out), ctypes.byref(st)))
+        return {"iterations": out.iterations, "outer_iterations": out.outer_iterations, "relres": out.relres,
+                "status": st.value}
+
     def rhs(self, g, u0, fhat):
-        _lib.check(_lib.load().st_rhs(self._h, _ptr(g, self.shape, "g"), _ptr(u0, (self.Nx,), "u0"),
+        _lib.check(_lib.load().st_rhs(self._h, _ptr(g, self.shape, "g"), _ptr(u0, self.u0_shape, "u0"),
                                       _ptr(fhat, self.shape, "fhat")))
 
     def pcg_solve(self, fhat, w):
@@ -121,7 +135,7 @@ class Solver:
     def solve_host(self, g, u0, u):
         """End-to-end solve from (preferably pinned) host tensors g (N_t, N_x), u0 (N_x,) into u."""
         it, rr = ctypes.c_int(), ctypes.c_double()
-        st = _lib.load().st_solve_host(self._h, _ptr(g, self.shape, "g", False), _ptr(u0, (self.Nx,), "u0", False),
+        st = _lib.load().st_solve_host(self._h, _ptr(g, self.shape, "g", False), _ptr(u0, self.u0_shape, "u0", False),
                                        _ptr(u, self.shape, "u", False), ctypes.byref(it), ctypes.byref(rr))
         _lib.check(st)
         return it.value, rr.value

@@ -47,7 +47,7 @@ def test_default_config_is_the_papers():
     assert (cfg.alpha, cfg.n_vcycles, cfg.n_pre, cfg.n_post) == (0.3, 2, 3, 3)
 
 
-@pytest.mark.parametrize("domain,K,J", [(1, 3, 3), (0, 0, 3), (0, 13, 3), (0, 3, 0), (0, 3, 15)])
+@pytest.mark.parametrize("domain,K,J", [(2, 3, 3), (1, 1, 3), (0, 0, 3), (0, 13, 3), (0, 3, 0), (0, 3, 15)])
 def test_setup_rejects_bad_sizes_without_gpu(domain, K, J):
     lib = lib_or_skip()
     h = ctypes.c_void_p()
