@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solves measurement")
+    ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="precision of the main timed solve (profiling aid; the bench line uses fp64)")
     ap.add_argument("--oracle-sample-child", action="store_true", help=argparse.SUPPRESS)
@@ -193,6 +195,53 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------------------
+def batch_workload(nprob, seed=0):
+    """256 independent problems: K ~ U{4..7}, J ~ U{4..8}, g a random smooth sum of 8 modes, u0 = 0."""
+    import numpy as np
+
+    from paper_2009_08875_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nprob):
+        K = int(rng.integers(4, 8))
+        J = int(rng.integers(4, 9))
+        g, u0 = inputs.smooth_forcing(K, J, seed=int(rng.integers(1 << 30)))
+        out.append((K, J, g, u0))
+    return out
+
+
+def run_batch_workload(args):
+    """Many uneven solves through st_batch_* (binary64 PCG with the binary32 preconditioner),
+    host buffers in and out, timed end to end (workspace set-up, copies, solves)."""
+    import torch
+
+    from paper_2009_08875_gb300 import Batch
+    probs = batch_workload(args.batch_problems)
+    host = []
+    for K, J, g, u0 in probs:
+        host.append((K, J, torch.from_numpy(g).pin_memory(), torch.from_numpy(u0).pin_memory(),
+                     torch.empty(g.shape, dtype=torch.float64).pin_memory()))
+    res = None
+    for rep in range(2):  # the first run warms up
+        bt = Batch(precision="mixed_precond", tol=TOL, maxit=500)
+        for K, J, g, u0, u in host:
+            bt.add(0, K, J, g, u0, u)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = bt.run()
+        dt = time.perf_counter() - t0
+        its = [bt.info(i)["iterations"] for i in range(len(host))]
+        dofs = sum(g.numel() for _, _, g, _, _ in host)
+        dof_its = sum(g.numel() * it for (_, _, g, _, _), it in zip(host, its))
+        res = {"problems": len(host), "groups": bt.buckets(), "status": st, "seconds": dt,
+               "solves_per_s": len(host) / dt, "dof_total": dofs, "dof_iters_per_s": dof_its / dt,
+               "iterations_mean": sum(its) / len(its), "iterations_max": max(its),
+               "precision": "f64 PCG, f32 preconditioner", "tol": TOL,
+               "timed": "st_batch_run end to end: workspace set-up, host<->device copies, all solves"}
+        bt.close()
+    return res
+
+
 def kernel_source_hash():
     with open(os.path.join(ROOT, "paper_2009_08875_gb300", "csrc", "k_mg.cu"), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()
@@ -327,6 +376,11 @@ def run_ours(args):
                  "rel_err_vs_fp64_solution": err, "dtype": "f32 inner / f64 refinement"}
         solver = ms_solver
 
+    batch = None
+    if not args.no_batch:
+        solver.close()
+        batch = run_batch_workload(args)
+
     if rank != 0:
         solver.close()
         if dist:
@@ -374,6 +428,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "mixed": mixed,
+        "batch": batch,
         "gpu_launches": prof["launches"],
         "clocks": clk,
     }

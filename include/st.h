@@ -80,10 +80,13 @@ typedef struct {
   int precision;    /* st_precision                                                         */
   double inner_tol; /* ST_MIXED_FP32: relative K_X-norm reduction of each inner solve        */
   int inner_maxit;  /* ST_MIXED_FP32: iteration limit of each inner solve                    */
+  int use_graphs;   /* 1: capture each PCG iteration body once as a CUDA graph and replay it
+                       (only on a stream other than the legacy/per-thread default streams
+                       and outside st_profile_begin/end); 0: plain launches               */
 } st_config;
 
 /* Fills *cfg with the paper's settings (alpha 0.3, 2 V-cycles, 3+3 sweeps, Sec. 5.1),
- * tol 1e-10 relative, maxit 200, FP64; inner_tol 1e-5, inner_maxit 60. */
+ * tol 1e-10 relative, maxit 200, FP64; inner_tol 1e-5, inner_maxit 60, use_graphs 1. */
 void st_default_config(st_config* cfg);
 
 /* Creates a handle for `domain` (0 unit square, 1 L-shape) at space level K (1..12; 2..12 for
@@ -187,6 +190,37 @@ st_status st_solve_host(st_handle h, const double* g_nodal_host, const double* u
  * host threads) race and must be serialised by the caller.  b and x are device pointers to
  * caller-owned memory of nslices * N_x doubles and must not overlap. */
 st_status st_apply_Kx_static(int space_level, int nslices, const double* b, double* x, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Batches of problems of any shape (not in the paper: a throughput interface for many
+ * independent solves).  Problems registered with st_batch_add are grouped by (domain, K, J);
+ * each group is solved as one batched handle on a stream of its own, and the groups run
+ * concurrently.  Every problem's result is bitwise what st_setup + st_solve_host would give
+ * for it alone with the same st_config.  Host buffers belong to the caller and must stay
+ * valid until st_batch_run returns; page-locked buffers copy fastest.
+ * --------------------------------------------------------------------------------------- */
+typedef struct st_batch_s* st_batch;
+
+/* Creates an empty batch solved with *cfg (NULL: defaults) on the current device. */
+st_status st_batch_create(st_batch* out, const st_config* cfg);
+
+/* Registers one problem: g_host (N_t x N_x), u0_host (N_x), result u_host (N_t x N_x) in the
+ * layout of st_solve_host.  *id (may be NULL) receives its index (0, 1, ...). */
+st_status st_batch_add(st_batch b, int domain, int space_level, int time_level, const double* g_host,
+                       const double* u0_host, double* u_host, int* id);
+
+/* Solves every registered problem (synchronous).  Workspace is allocated per group for the
+ * duration of the call.  Returns the first failing problem's status (ST_ERR_MAXIT or
+ * ST_ERR_BREAKDOWN) after solving all of them, or ST_OK. */
+st_status st_batch_run(st_batch b);
+
+/* Statistics and status of problem id after st_batch_run. */
+st_status st_batch_problem_info(st_batch b, int id, st_solve_info* out, int* status);
+
+/* Number of groups (batched handles) the last st_batch_run used. */
+st_status st_batch_buckets(st_batch b, int* n);
+
+st_status st_batch_destroy(st_batch b);
 
 /* Measurement hooks (not part of the method).  Between st_profile_begin and st_profile_end the
  * handle counts every kernel it launches and brackets each finest-level Gauss-Seidel sweep

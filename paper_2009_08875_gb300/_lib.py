@@ -18,7 +18,7 @@ class StConfig(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("n_vcycles", ctypes.c_int), ("n_pre", ctypes.c_int),
                 ("n_post", ctypes.c_int), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("inner_maxit", ctypes.c_int)]
+                ("inner_maxit", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
 class StSolveInfo(ctypes.Structure):
@@ -68,6 +68,14 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_double)]),
     "st_profile_begin": (ctypes.c_int, [_P]),
     "st_profile_end": (ctypes.c_int, [_P, ctypes.POINTER(StProfile)]),
+    "st_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(StConfig)]),
+    "st_batch_add": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                    ctypes.POINTER(ctypes.c_int)]),
+    "st_batch_run": (ctypes.c_int, [_P]),
+    "st_batch_problem_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(StSolveInfo),
+                                             ctypes.POINTER(ctypes.c_int)]),
+    "st_batch_buckets": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "st_batch_destroy": (ctypes.c_int, [_P]),
     "st_last_error": (ctypes.c_char_p, []),
 }
 

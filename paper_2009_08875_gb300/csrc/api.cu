@@ -4,6 +4,7 @@
 // the stop tests; all arithmetic runs on the GPU.  A handle holds B >= 1 problems of the same
 // domain, space level and time level, stored back to back; every operator acts on all of them.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -119,6 +120,10 @@ void free_all(st_handle_s* h) {
   std::free(h->info_relres);
   h->info_iters = h->info_outer = h->info_status = nullptr;
   h->info_relres = nullptr;
+  for (int i = 0; i < 3; ++i) {
+    if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
+    h->graph_exec[i] = nullptr;
+  }
   for (int i = 0; i < h->prof_cap; ++i) cudaEventDestroy(h->prof_ev[i]);
   std::free(h->prof_ev);
   h->prof_ev = nullptr;
@@ -155,11 +160,11 @@ T* ws(double* p) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// operators on all B problems of a handle
+// operators on nb problems of a handle (all of them, or a range whose vectors start at problem b0;
+// the workspace is scratch, so any range works)
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-st_status apply_S_nodal_impl(st_handle h, const T* u, T* y) {
-  const int nb = h->B;
+st_status apply_S_nodal_impl(st_handle h, int nb, const T* u, T* y) {
   ST_CHECK_CUDA(launch_timemix<T>(h, nb, 0, u, ws<T>(h->Y)), "timemix");
   ST_CHECK_CUDA(mg_apply<T>(h, (int)(2 * nb * h->Nt), 0, ws<T>(h->Y), ws<T>(h->X)), "K_x multigrid");
   ST_CHECK_CUDA(launch_epilogue<T>(h, nb, ws<T>(h->X), u, h->Nt * h->Nx, y), "epilogue");
@@ -167,28 +172,19 @@ st_status apply_S_nodal_impl(st_handle h, const T* u, T* y) {
 }
 
 template <typename T>
-st_status apply_Shat_impl(st_handle h, const T* w, T* q) {
-  ST_CHECK_CUDA(wavelet_synth<T>(h, h->B, w, ws<T>(h->U)), "wavelet synthesis");
-  ST_CHECK(apply_S_nodal_impl<T>(h, ws<T>(h->U), ws<T>(h->Z)));
-  ST_CHECK_CUDA(wavelet_anal<T>(h, h->B, ws<T>(h->Z), q), "wavelet analysis");
+st_status apply_Shat_impl(st_handle h, int nb, const T* w, T* q) {
+  ST_CHECK_CUDA(wavelet_synth<T>(h, nb, w, ws<T>(h->U)), "wavelet synthesis");
+  ST_CHECK(apply_S_nodal_impl<T>(h, nb, ws<T>(h->U), ws<T>(h->Z)));
+  ST_CHECK_CUDA(wavelet_anal<T>(h, nb, ws<T>(h->Z), q), "wavelet analysis");
   return ST_OK;
 }
 
 template <typename T>
-st_status apply_KX_impl(st_handle h, const T* r, T* z) {
-  const int rows = (int)(h->B * h->Nt);
+st_status apply_KX_impl(st_handle h, int nb, const T* r, T* z) {
+  const int rows = (int)(nb * h->Nt);
   ST_CHECK_CUDA(mg_apply<T>(h, rows, -1, r, ws<T>(h->X)), "K_l multigrid (1)");
   ST_CHECK_CUDA(launch_apply_A<T>(h, rows, ws<T>(h->X), ws<T>(h->Y)), "A_x");
   ST_CHECK_CUDA(mg_apply<T>(h, rows, -1, ws<T>(h->Y), z), "K_l multigrid (2)");
-  return ST_OK;
-}
-
-st_status rhs_impl(st_handle h, const double* g, const double* u0, double* fhat) {
-  const int nb = h->B;
-  ST_CHECK_CUDA(launch_timemix<double>(h, nb, 1, g, h->Y), "timemix (rhs)");
-  ST_CHECK_CUDA(mg_apply<double>(h, (int)(2 * nb * h->Nt), 0, h->Y, h->X), "K_x multigrid (rhs)");
-  ST_CHECK_CUDA(launch_epilogue<double>(h, nb, h->X, u0, h->Nx, h->Z), "epilogue (rhs)");
-  ST_CHECK_CUDA(wavelet_anal<double>(h, nb, h->Z, fhat), "wavelet analysis (rhs)");
   return ST_OK;
 }
 
@@ -210,6 +206,45 @@ st_status push_act(st_handle h) {
 }
 
 inline double sc(st_handle h, int b, int slot) { return h->scal_host[(size_t)b * SC_COUNT + slot]; }
+
+// Runs one PCG iteration body.  With graphs enabled (on a stream other than the legacy and
+// per-thread default streams, outside profiling) the first call captures the body's launches
+// into a CUDA graph that later calls replay; `key` names the caller-owned vectors the body
+// touches, and a different key captures again.
+template <typename F>
+st_status run_body(st_handle h, int slot, const void* key, F body) {
+  const uintptr_t sv = reinterpret_cast<uintptr_t>(h->stream);
+  const bool use = h->cfg.use_graphs && sv > 2 && !h->prof_on;
+  if (!use) return body();
+  if (h->graph_exec[slot] && h->graph_key[slot] != key) {
+    cudaGraphExecDestroy(h->graph_exec[slot]);
+    h->graph_exec[slot] = nullptr;
+  }
+  if (!h->graph_exec[slot]) {
+    const int64_t before = h->launches;
+    ST_CHECK_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin graph capture");
+    st_status s = body();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (s != ST_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail("end graph capture", e);
+    e = cudaGraphInstantiate(&h->graph_exec[slot], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->graph_exec[slot] = nullptr;
+      return cuda_fail("graph instantiate", e);
+    }
+    h->graph_launches[slot] = h->launches - before;
+    h->launches = before;
+    h->graph_key[slot] = key;
+  }
+  ST_CHECK_CUDA(cudaGraphLaunch(h->graph_exec[slot], h->stream), "graph launch");
+  h->launches += h->graph_launches[slot];
+  return ST_OK;
+}
 
 bool any_active(st_handle h) {
   for (int b = 0; b < h->B; ++b)
@@ -294,18 +329,23 @@ st_status pcg64_impl(st_handle h, const double* fhat, double* w) {
   ST_CHECK(push_act(h));
   ST_CHECK_CUDA(launch_zero<double>(h, w, n * nb), "zero w");
   ST_CHECK_CUDA(launch_copy<double, double>(h, h->r, fhat, n * nb), "copy r");
-  ST_CHECK(apply_KX_impl<double>(h, h->r, h->z));
-  ST_CHECK_CUDA(launch_dot<double, double>(h, nb, h->r, h->z, n, SC_RHO, DOT_INIT), "dot r z");
-  ST_CHECK_CUDA(launch_copy<double, double>(h, h->p, h->z, n * nb), "copy p");
+  ST_CHECK(apply_KX_impl<double>(h, h->B, h->r, h->z));
+  ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO, DOT_INIT), "dot r z");
+  ST_CHECK_CUDA(launch_zero<double>(h, h->p, n * nb), "zero p");  // first body: p = z + 0 p
   ST_CHECK(read_scalars(h));
   init_problems(h, t, SC_RHO0);
   ST_CHECK(push_act(h));
+  auto body = [&]() -> st_status {
+    ST_CHECK_CUDA(launch_update_p<double>(h, 0, nb, h->p, h->z, n), "update p");
+    ST_CHECK(apply_Shat_impl<double>(h, h->B, h->p, h->q));
+    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->p, h->q, n, SC_PQ, DOT_ALPHA), "dot p q");
+    ST_CHECK_CUDA(launch_update_wr<double>(h, 0, nb, w, h->r, h->p, h->q, n), "update w r");
+    ST_CHECK(apply_KX_impl<double>(h, h->B, h->r, h->z));
+    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO_NEW, DOT_BETA), "dot r z");
+    return ST_OK;
+  };
   for (int it = 1; it <= c.maxit && any_active(h); ++it) {
-    ST_CHECK(apply_Shat_impl<double>(h, h->p, h->q));
-    ST_CHECK_CUDA(launch_dot<double, double>(h, nb, h->p, h->q, n, SC_PQ, DOT_ALPHA), "dot p q");
-    ST_CHECK_CUDA(launch_update_wr<double>(h, nb, w, h->r, h->p, h->q, n), "update w r");
-    ST_CHECK(apply_KX_impl<double>(h, h->r, h->z));
-    ST_CHECK_CUDA(launch_dot<double, double>(h, nb, h->r, h->z, n, SC_RHO_NEW, DOT_BETA), "dot r z");
+    ST_CHECK(run_body(h, 0, w, body));
     ST_CHECK(read_scalars(h));
     t.changed = false;
     for (int b = 0; b < nb; ++b) {
@@ -313,9 +353,7 @@ st_status pcg64_impl(st_handle h, const double* fhat, double* w) {
       h->info_iters[b] = it;
       test_problem(h, t, b, sc(h, b, SC_RHO_NEW), sc(h, b, SC_PQ), true);
     }
-    if (!any_active(h)) break;
-    if (t.changed) ST_CHECK(push_act(h));
-    ST_CHECK_CUDA(launch_update_p<double>(h, nb, h->p, h->z, n), "update p");
+    if (t.changed && any_active(h)) ST_CHECK(push_act(h));
   }
   return finish(h);
 }
@@ -330,8 +368,8 @@ st_status inner_pcg32(st_handle h, const std::vector<int>& out_act, std::vector<
   const int64_t n = h->Nt * h->Nx;
   const st_config& c = h->cfg;
   ST_CHECK_CUDA(launch_zero<float>(h, h->xi, n * nb), "zero inner x");
-  ST_CHECK_CUDA(launch_copy<float, float>(h, h->pi, h->zi, n * nb), "copy inner p");
-  ST_CHECK_CUDA(launch_dot<float, float>(h, nb, h->ri, h->zi, n, SC_RHO, DOT_INIT), "inner dot r z");
+  ST_CHECK_CUDA(launch_zero<float>(h, h->pi, n * nb), "zero inner p");  // first body: p = z + 0 p
+  ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RHO, DOT_INIT), "inner dot r z");
   ST_CHECK(read_scalars(h));
   std::vector<double> rho0(nb);
   for (int b = 0; b < nb; ++b) {
@@ -340,12 +378,17 @@ st_status inner_pcg32(st_handle h, const std::vector<int>& out_act, std::vector<
     h->act_host[b] = out_act[b] && rho0[b] > 0.0 && std::isfinite(rho0[b]);
   }
   ST_CHECK(push_act(h));
+  auto body = [&]() -> st_status {
+    ST_CHECK_CUDA(launch_update_p<float>(h, 0, nb, h->pi, h->zi, n), "inner update p");
+    ST_CHECK(apply_Shat_impl<float>(h, h->B, h->pi, h->qi));
+    ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->pi, h->qi, n, SC_PQ, DOT_ALPHA), "inner dot p q");
+    ST_CHECK_CUDA(launch_update_wr<float>(h, 0, nb, h->xi, h->ri, h->pi, h->qi, n), "inner update");
+    ST_CHECK(apply_KX_impl<float>(h, h->B, h->ri, h->zi));
+    ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RHO_NEW, DOT_BETA), "inner dot r z");
+    return ST_OK;
+  };
   for (int it = 1; it <= c.inner_maxit && any_active(h); ++it) {
-    ST_CHECK(apply_Shat_impl<float>(h, h->pi, h->qi));
-    ST_CHECK_CUDA(launch_dot<float, float>(h, nb, h->pi, h->qi, n, SC_PQ, DOT_ALPHA), "inner dot p q");
-    ST_CHECK_CUDA(launch_update_wr<float>(h, nb, h->xi, h->ri, h->pi, h->qi, n), "inner update");
-    ST_CHECK(apply_KX_impl<float>(h, h->ri, h->zi));
-    ST_CHECK_CUDA(launch_dot<float, float>(h, nb, h->ri, h->zi, n, SC_RHO_NEW, DOT_BETA), "inner dot r z");
+    ST_CHECK(run_body(h, 1, nullptr, body));
     ST_CHECK(read_scalars(h));
     bool changed = false;
     for (int b = 0; b < nb; ++b) {
@@ -358,9 +401,7 @@ st_status inner_pcg32(st_handle h, const std::vector<int>& out_act, std::vector<
         changed = true;
       }
     }
-    if (!any_active(h)) break;
-    if (changed) ST_CHECK(push_act(h));
-    ST_CHECK_CUDA(launch_update_p<float>(h, nb, h->pi, h->zi, n), "inner update p");
+    if (changed && any_active(h)) ST_CHECK(push_act(h));
   }
   return ST_OK;
 }
@@ -373,8 +414,8 @@ st_status pcg_mixed_impl(st_handle h, const double* fhat, double* w) {
   ST_CHECK_CUDA(launch_zero<double>(h, w, n * nb), "zero w");
   ST_CHECK_CUDA(launch_copy<double, double>(h, h->r, fhat, n * nb), "copy r");
   ST_CHECK_CUDA(launch_copy<float, double>(h, h->ri, fhat, n * nb), "round r");
-  ST_CHECK(apply_KX_impl<float>(h, h->ri, h->zi));
-  ST_CHECK_CUDA(launch_dot<double, float>(h, nb, h->r, h->zi, n, SC_OUTER, DOT_STORE), "outer dot");
+  ST_CHECK(apply_KX_impl<float>(h, h->B, h->ri, h->zi));
+  ST_CHECK_CUDA(launch_dot<double, float>(h, 0, nb, h->r, h->zi, n, SC_OUTER, DOT_STORE), "outer dot");
   ST_CHECK(read_scalars(h));
   init_problems(h, t, SC_OUTER);
   std::vector<int> out_act(h->act_host, h->act_host + nb), its(nb, 0);
@@ -391,10 +432,10 @@ st_status pcg_mixed_impl(st_handle h, const double* fhat, double* w) {
       progress = progress || its[b] > 0;
     }
     ST_CHECK_CUDA(launch_add_correction(h, w, h->xi, n * nb), "w += d");
-    ST_CHECK(apply_Shat_impl<double>(h, w, h->q));
+    ST_CHECK(apply_Shat_impl<double>(h, h->B, w, h->q));
     ST_CHECK_CUDA(launch_residual_split(h, h->r, h->ri, fhat, h->q, n * nb), "outer residual");
-    ST_CHECK(apply_KX_impl<float>(h, h->ri, h->zi));
-    ST_CHECK_CUDA(launch_dot<double, float>(h, nb, h->r, h->zi, n, SC_OUTER, DOT_STORE), "outer dot");
+    ST_CHECK(apply_KX_impl<float>(h, h->B, h->ri, h->zi));
+    ST_CHECK_CUDA(launch_dot<double, float>(h, 0, nb, h->r, h->zi, n, SC_OUTER, DOT_STORE), "outer dot");
     ST_CHECK(read_scalars(h));
     for (int b = 0; b < nb; ++b) {
       if (!out_act[b]) continue;
@@ -420,7 +461,7 @@ st_status pcg_mixed_impl(st_handle h, const double* fhat, double* w) {
 st_status precond32(st_handle h, const double* r, double* z) {
   const int64_t N = h->B * h->Nt * h->Nx;
   ST_CHECK_CUDA(launch_copy<float, double>(h, h->ri, r, N), "round r");
-  ST_CHECK(apply_KX_impl<float>(h, h->ri, h->zi));
+  ST_CHECK(apply_KX_impl<float>(h, h->B, h->ri, h->zi));
   ST_CHECK_CUDA(launch_copy<double, float>(h, z, h->zi, N), "widen z");
   return ST_OK;
 }
@@ -435,18 +476,23 @@ st_status pcg_precond_impl(st_handle h, const double* fhat, double* w) {
   ST_CHECK_CUDA(launch_zero<double>(h, w, n * nb), "zero w");
   ST_CHECK_CUDA(launch_copy<double, double>(h, h->r, fhat, n * nb), "copy r");
   ST_CHECK(precond32(h, h->r, h->z));
-  ST_CHECK_CUDA(launch_dot<double, double>(h, nb, h->r, h->z, n, SC_RHO, DOT_INIT), "dot r z");
-  ST_CHECK_CUDA(launch_copy<double, double>(h, h->p, h->z, n * nb), "copy p");
+  ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO, DOT_INIT), "dot r z");
+  ST_CHECK_CUDA(launch_zero<double>(h, h->p, n * nb), "zero p");  // first body: p = z + 0 p
   ST_CHECK(read_scalars(h));
   init_problems(h, t, SC_RHO0);
   ST_CHECK(push_act(h));
-  for (int it = 1; it <= c.maxit && any_active(h); ++it) {
-    ST_CHECK(apply_Shat_impl<double>(h, h->p, h->q));
-    ST_CHECK_CUDA(launch_dot<double, double>(h, nb, h->p, h->q, n, SC_PQ, DOT_ALPHA), "dot p q");
-    ST_CHECK_CUDA(launch_update_wr<double>(h, nb, w, h->r, h->p, h->q, n), "update w r");
-    ST_CHECK_CUDA(launch_dot<double, double>(h, nb, h->r, h->z, n, SC_RZOLD, DOT_STORE), "dot r z_old");
+  auto body = [&]() -> st_status {
+    ST_CHECK_CUDA(launch_update_p<double>(h, 0, nb, h->p, h->z, n), "update p");
+    ST_CHECK(apply_Shat_impl<double>(h, h->B, h->p, h->q));
+    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->p, h->q, n, SC_PQ, DOT_ALPHA), "dot p q");
+    ST_CHECK_CUDA(launch_update_wr<double>(h, 0, nb, w, h->r, h->p, h->q, n), "update w r");
+    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RZOLD, DOT_STORE), "dot r z_old");
     ST_CHECK(precond32(h, h->r, h->z));
-    ST_CHECK_CUDA(launch_dot<double, double>(h, nb, h->r, h->z, n, SC_RHO_NEW, DOT_BETA_FLEX), "dot r z");
+    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO_NEW, DOT_BETA_FLEX), "dot r z");
+    return ST_OK;
+  };
+  for (int it = 1; it <= c.maxit && any_active(h); ++it) {
+    ST_CHECK(run_body(h, 2, w, body));
     ST_CHECK(read_scalars(h));
     t.changed = false;
     for (int b = 0; b < nb; ++b) {
@@ -454,11 +500,21 @@ st_status pcg_precond_impl(st_handle h, const double* fhat, double* w) {
       h->info_iters[b] = it;
       test_problem(h, t, b, sc(h, b, SC_RHO_NEW), sc(h, b, SC_PQ), true);
     }
-    if (!any_active(h)) break;
-    if (t.changed) ST_CHECK(push_act(h));
-    ST_CHECK_CUDA(launch_update_p<double>(h, nb, h->p, h->z, n), "update p");
+    if (t.changed && any_active(h)) ST_CHECK(push_act(h));
   }
   return finish(h);
+}
+
+}  // namespace
+
+namespace st {
+
+st_status rhs_impl(st_handle h, int nb, const double* g, const double* u0, double* fhat) {
+  ST_CHECK_CUDA(launch_timemix<double>(h, nb, 1, g, h->Y), "timemix (rhs)");
+  ST_CHECK_CUDA(mg_apply<double>(h, (int)(2 * nb * h->Nt), 0, h->Y, h->X), "K_x multigrid (rhs)");
+  ST_CHECK_CUDA(launch_epilogue<double>(h, nb, h->X, u0, h->Nx, h->Z), "epilogue (rhs)");
+  ST_CHECK_CUDA(wavelet_anal<double>(h, nb, h->Z, fhat), "wavelet analysis (rhs)");
+  return ST_OK;
 }
 
 st_status pcg_impl(st_handle h, const double* fhat, double* w, int* iters, double* relres) {
@@ -478,7 +534,7 @@ st_status pcg_impl(st_handle h, const double* fhat, double* w, int* iters, doubl
   return s;
 }
 
-}  // namespace
+}  // namespace st
 
 extern "C" {
 
@@ -494,6 +550,7 @@ void st_default_config(st_config* cfg) {
   cfg->precision = ST_FP64;
   cfg->inner_tol = 1e-5;
   cfg->inner_maxit = 60;
+  cfg->use_graphs = 1;
 }
 
 const char* st_last_error(void) { return g_last_error.c_str(); }
@@ -667,7 +724,7 @@ st_status st_apply_Kx(st_handle h, int nslices, const double* b, double* x) {
 st_status st_apply_S_nodal(st_handle h, const double* u, double* y) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(u && y, "st_apply_S_nodal: null pointer");
-  return apply_S_nodal_impl<double>(h, u, y);
+  return apply_S_nodal_impl<double>(h, h->B, u, y);
 }
 
 st_status st_synthesize(st_handle h, const double* w, double* u) {
@@ -687,31 +744,31 @@ st_status st_analyze(st_handle h, const double* u, double* w) {
 st_status st_apply_S(st_handle h, const double* w, double* q) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(w && q, "st_apply_S: null pointer");
-  return apply_Shat_impl<double>(h, w, q);
+  return apply_Shat_impl<double>(h, h->B, w, q);
 }
 
 st_status st_apply_S_f32(st_handle h, const float* w, float* q) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(w && q, "st_apply_S_f32: null pointer");
-  return apply_Shat_impl<float>(h, w, q);
+  return apply_Shat_impl<float>(h, h->B, w, q);
 }
 
 st_status st_apply_KX_f32(st_handle h, const float* r, float* z) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(r && z, "st_apply_KX_f32: null pointer");
-  return apply_KX_impl<float>(h, r, z);
+  return apply_KX_impl<float>(h, h->B, r, z);
 }
 
 st_status st_apply_KX(st_handle h, const double* r, double* z) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(r && z, "st_apply_KX: null pointer");
-  return apply_KX_impl<double>(h, r, z);
+  return apply_KX_impl<double>(h, h->B, r, z);
 }
 
 st_status st_rhs(st_handle h, const double* g, const double* u0, double* fhat) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(g && u0 && fhat, "st_rhs: null pointer");
-  return rhs_impl(h, g, u0, fhat);
+  return rhs_impl(h, h->B, g, u0, fhat);
 }
 
 st_status st_pcg_solve(st_handle h, const double* fhat, double* w, int* iters, double* relres) {
@@ -747,7 +804,7 @@ st_status st_solve_host(st_handle h, const double* g_host, const double* u0_host
   ST_CHECK_CUDA(cudaMemcpyAsync(h->u0, u0_host, (size_t)(h->B * h->Nx) * sizeof(double), cudaMemcpyHostToDevice,
                                 h->stream),
                 "copy u0");
-  ST_CHECK(rhs_impl(h, h->g, h->u0, h->fhat));
+  ST_CHECK(rhs_impl(h, h->B, h->g, h->u0, h->fhat));
   st_status ps = pcg_impl(h, h->fhat, h->w, iters, relres);
   if (ps != ST_OK && ps != ST_ERR_MAXIT) return ps;
   ST_CHECK_CUDA(wavelet_synth<double>(h, h->B, h->w, h->g), "wavelet synthesis");

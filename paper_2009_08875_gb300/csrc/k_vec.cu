@@ -80,10 +80,11 @@ __global__ void __launch_bounds__(256) k_dot_final(const double* __restrict__ pa
         sc[SC_BETA] = on ? (t - sc[SC_RZOLD]) / sc[SC_RHO] : 0.0;
         if (on) sc[SC_RHO] = t;
         break;
-      case DOT_INIT:  // t = r_0^T z_0
+      case DOT_INIT:  // t = r_0^T z_0; beta = 0 makes the first p = z + beta p (p = 0) equal z
         sc[SC_RHO] = t;
         sc[SC_RHO0] = t;
         sc[SC_RHO_NEW] = t;
+        sc[SC_BETA] = 0.0;
         break;
     }
   }
@@ -166,24 +167,27 @@ inline unsigned stream_grid(int64_t n) {
 }  // namespace
 
 template <typename Ta, typename Tb>
-cudaError_t launch_dot(const st_handle_s* h, int nb, const Ta* a, const Tb* b, int64_t n, int slot, int op) {
+cudaError_t launch_dot(const st_handle_s* h, int b0, int nb, const Ta* a, const Tb* b, int64_t n, int slot, int op) {
   const int nblk = dot_blocks(n);
   k_dot_partial<Ta, Tb><<<dim3(nblk, nb), kThreads, 0, h->stream>>>(a, b, n, h->partials);
-  k_dot_final<<<nb, kThreads, 0, h->stream>>>(h->partials, nblk, h->scal, h->act, slot, op);
+  k_dot_final<<<nb, kThreads, 0, h->stream>>>(h->partials, nblk, h->scal + (int64_t)b0 * SC_COUNT, h->act + b0, slot,
+                                               op);
   count_launch(h, 2);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_update_wr(const st_handle_s* h, int nb, T* w, T* r, const T* p, const T* q, int64_t n) {
-  k_update_wr<T><<<dim3(per_problem_grid(n, nb), nb), kThreads, 0, h->stream>>>(w, r, p, q, n, h->scal);
+cudaError_t launch_update_wr(const st_handle_s* h, int b0, int nb, T* w, T* r, const T* p, const T* q, int64_t n) {
+  k_update_wr<T><<<dim3(per_problem_grid(n, nb), nb), kThreads, 0, h->stream>>>(w, r, p, q, n,
+                                                                                 h->scal + (int64_t)b0 * SC_COUNT);
   count_launch(h);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_update_p(const st_handle_s* h, int nb, T* p, const T* z, int64_t n) {
-  k_update_p<T><<<dim3(per_problem_grid(n, nb), nb), kThreads, 0, h->stream>>>(p, z, n, h->scal);
+cudaError_t launch_update_p(const st_handle_s* h, int b0, int nb, T* p, const T* z, int64_t n) {
+  k_update_p<T><<<dim3(per_problem_grid(n, nb), nb), kThreads, 0, h->stream>>>(p, z, n,
+                                                                                h->scal + (int64_t)b0 * SC_COUNT);
   count_launch(h);
   return cudaGetLastError();
 }
@@ -215,17 +219,18 @@ cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, co
   return cudaGetLastError();
 }
 
-template cudaError_t launch_dot<double, double>(const st_handle_s*, int, const double*, const double*, int64_t, int,
-                                                int);
-template cudaError_t launch_dot<float, float>(const st_handle_s*, int, const float*, const float*, int64_t, int, int);
-template cudaError_t launch_dot<double, float>(const st_handle_s*, int, const double*, const float*, int64_t, int,
-                                               int);
-template cudaError_t launch_update_wr<double>(const st_handle_s*, int, double*, double*, const double*, const double*,
-                                              int64_t);
-template cudaError_t launch_update_wr<float>(const st_handle_s*, int, float*, float*, const float*, const float*,
+template cudaError_t launch_dot<double, double>(const st_handle_s*, int, int, const double*, const double*, int64_t,
+                                                int, int);
+template cudaError_t launch_dot<float, float>(const st_handle_s*, int, int, const float*, const float*, int64_t, int,
+                                              int);
+template cudaError_t launch_dot<double, float>(const st_handle_s*, int, int, const double*, const float*, int64_t,
+                                               int, int);
+template cudaError_t launch_update_wr<double>(const st_handle_s*, int, int, double*, double*, const double*,
+                                              const double*, int64_t);
+template cudaError_t launch_update_wr<float>(const st_handle_s*, int, int, float*, float*, const float*, const float*,
                                              int64_t);
-template cudaError_t launch_update_p<double>(const st_handle_s*, int, double*, const double*, int64_t);
-template cudaError_t launch_update_p<float>(const st_handle_s*, int, float*, const float*, int64_t);
+template cudaError_t launch_update_p<double>(const st_handle_s*, int, int, double*, const double*, int64_t);
+template cudaError_t launch_update_p<float>(const st_handle_s*, int, int, float*, const float*, int64_t);
 template cudaError_t launch_copy<double, double>(const st_handle_s*, double*, const double*, int64_t);
 template cudaError_t launch_copy<float, float>(const st_handle_s*, float*, const float*, int64_t);
 template cudaError_t launch_copy<float, double>(const st_handle_s*, float*, const double*, int64_t);

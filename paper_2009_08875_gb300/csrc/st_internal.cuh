@@ -101,6 +101,11 @@ struct st_handle_s {
   int last_iters, last_outer;
   double last_relres;
   int B;             // problems in the batch (vectors are B x N_t x N_x)
+  // CUDA graphs of the PCG iteration bodies (0: binary64 PCG, 1: binary32 inner PCG,
+  // 2: binary64 PCG with binary32 preconditioner), re-captured when `graph_key` changes
+  cudaGraphExec_t graph_exec[3];
+  int64_t graph_launches[3];
+  const void* graph_key[3];
   int* act;          // device: 1 while problem b iterates (B ints)
   int* act_host;     // page-locked mirror
   int* info_iters;   // host, per problem: iterations, refinement steps, status
@@ -167,14 +172,15 @@ template <typename T>
 cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y);
 
 // vector kernels (dot products accumulate in binary64).  launch_dot, launch_update_wr and
-// launch_update_p act on nb problems of n elements each, with per-problem scalars
-// h->scal[b * SC_COUNT + slot] and the per-problem active flags h->act.
+// launch_update_p act on problems b0 .. b0 + nb - 1 (the vectors passed start at problem b0)
+// of n elements each, with per-problem scalars h->scal[b * SC_COUNT + slot] and the
+// per-problem active flags h->act[b].
 template <typename Ta, typename Tb>
-cudaError_t launch_dot(const st_handle_s* h, int nb, const Ta* a, const Tb* b, int64_t n, int slot, int op);
+cudaError_t launch_dot(const st_handle_s* h, int b0, int nb, const Ta* a, const Tb* b, int64_t n, int slot, int op);
 template <typename T>
-cudaError_t launch_update_wr(const st_handle_s* h, int nb, T* w, T* r, const T* p, const T* q, int64_t n);
+cudaError_t launch_update_wr(const st_handle_s* h, int b0, int nb, T* w, T* r, const T* p, const T* q, int64_t n);
 template <typename T>
-cudaError_t launch_update_p(const st_handle_s* h, int nb, T* p, const T* z, int64_t n);
+cudaError_t launch_update_p(const st_handle_s* h, int b0, int nb, T* p, const T* z, int64_t n);
 template <typename Td, typename Ts>
 cudaError_t launch_copy(const st_handle_s* h, Td* dst, const Ts* src, int64_t n);
 template <typename T>
@@ -182,6 +188,11 @@ cudaError_t launch_zero(const st_handle_s* h, T* dst, int64_t n);
 cudaError_t launch_add_correction(const st_handle_s* h, double* w, const float* d, int64_t n);
 cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, const double* f, const double* q,
                                   int64_t n);
+
+// whole-handle pipelines (api.cu): right-hand side of nb problems, and the PCG solve of all
+// problems of the handle in its configured precision
+st_status rhs_impl(st_handle_s* h, int nb, const double* g, const double* u0, double* fhat);
+st_status pcg_impl(st_handle_s* h, const double* fhat, double* w, int* iters, double* relres);
 
 // PCG scalar slots in h->scal
 enum {

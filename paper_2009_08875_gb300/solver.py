@@ -30,7 +30,8 @@ class Solver:
     """
 
     def __init__(self, K, J, domain=0, alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0,
-                 maxit=200, precision="fp64", inner_tol=1e-5, inner_maxit=60, batch=1, stream=None):
+                 maxit=200, precision="fp64", inner_tol=1e-5, inner_maxit=60, batch=1, use_graphs=True,
+                 stream=None):
         import torch
         lib = _lib.load()
         cfg = _lib.StConfig()
@@ -40,6 +41,7 @@ class Solver:
         cfg.precision = {"fp64": _lib.ST_FP64, "mixed": _lib.ST_MIXED_FP32,
                          "mixed_precond": _lib.ST_MIXED_PRECOND}[precision]
         cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
+        cfg.use_graphs = 1 if use_graphs else 0
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -149,3 +151,67 @@ class Solver:
         out = _lib.StProfile()
         _lib.check(_lib.load().st_profile_end(self._h, ctypes.byref(out)))
         return {f: getattr(out, f) for f, _ in _lib.StProfile._fields_}
+
+
+def _config(alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0, maxit=200, precision="fp64",
+            inner_tol=1e-5, inner_maxit=60, use_graphs=True):
+    lib = _lib.load()
+    cfg = _lib.StConfig()
+    lib.st_default_config(ctypes.byref(cfg))
+    cfg.alpha, cfg.n_vcycles, cfg.n_pre, cfg.n_post = alpha, n_vcycles, n_pre, n_post
+    cfg.tol, cfg.tol_mode, cfg.maxit = tol, tol_mode, maxit
+    cfg.precision = {"fp64": _lib.ST_FP64, "mixed": _lib.ST_MIXED_FP32,
+                     "mixed_precond": _lib.ST_MIXED_PRECOND}[precision]
+    cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
+    cfg.use_graphs = 1 if use_graphs else 0
+    return cfg
+
+
+class Batch:
+    """Many solves of any shape in one call (st_batch_*).  Inputs and outputs are host tensors
+    (float64, contiguous; page-locked ones copy fastest) kept alive until run() returns."""
+
+    def __init__(self, **cfg):
+        self._cfg = _config(**cfg)
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().st_batch_create(ctypes.byref(h), ctypes.byref(self._cfg)))
+        self._h = h
+        self._keep = []
+
+    def add(self, domain, K, J, g, u0, u):
+        n = 2 ** K - 1
+        Nt, Nx = 2 ** J + 1, n * n
+        ids = ctypes.c_int()
+        _lib.check(_lib.load().st_batch_add(self._h, domain, K, J, _ptr(g, (Nt, Nx), "g", False),
+                                            _ptr(u0, (Nx,), "u0", False), _ptr(u, (Nt, Nx), "u", False),
+                                            ctypes.byref(ids)))
+        self._keep.append((g, u0, u))
+        return ids.value
+
+    def run(self):
+        st = _lib.load().st_batch_run(self._h)
+        if st not in (_lib.ST_OK, _lib.ST_ERR_MAXIT, _lib.ST_ERR_BREAKDOWN):
+            _lib.check(st)
+        return st
+
+    def info(self, i):
+        out, st = _lib.StSolveInfo(), ctypes.c_int()
+        _lib.check(_lib.load().st_batch_problem_info(self._h, i, ctypes.byref(out), ctypes.byref(st)))
+        return {"iterations": out.iterations, "outer_iterations": out.outer_iterations, "relres": out.relres,
+                "status": st.value}
+
+    def buckets(self):
+        n = ctypes.c_int()
+        _lib.check(_lib.load().st_batch_buckets(self._h, ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().st_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -91,3 +91,28 @@ def test_batched_operators_equal_single():
                 op_1(x[b].contiguous(), y1)
                 torch.cuda.synchronize()
                 assert torch.equal(yb[b], y1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_precond"])
+def test_multi_shape_runner_equals_alone(precision):
+    from paper_2009_08875_gb300 import Batch
+    rng = np.random.default_rng(7)
+    shapes = [(0, 4, 3), (0, 5, 4), (1, 4, 3), (0, 4, 3), (0, 5, 4), (1, 5, 3), (0, 4, 3)]
+    bt = Batch(precision=precision, tol=1e-10)
+    probs = []
+    for i, (dom, K, J) in enumerate(shapes):
+        g, u0 = inputs.smooth_forcing(K, J, seed=int(rng.integers(1 << 30)), domain=dom)
+        g = torch.from_numpy(inputs.to_grid(K, dom, g)).pin_memory()
+        u0 = torch.from_numpy(inputs.to_grid(K, dom, inputs.manufactured(K, J, dom)[1])).pin_memory()
+        u = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
+        assert bt.add(dom, K, J, g, u0, u) == i
+        probs.append((dom, K, J, g, u0, u))
+    assert bt.run() == 0
+    assert bt.buckets() == 4
+    for i, (dom, K, J, g, u0, u) in enumerate(probs):
+        with Solver(K, J, domain=dom, precision=precision, tol=1e-10) as s:
+            ua = torch.zeros_like(u)
+            its, _ = s.solve_host(g, u0, ua)
+        assert torch.equal(u, ua), i
+        assert bt.info(i)["iterations"] == its
+    bt.close()
