@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solves measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=0.25, help="seconds of Poisson arrivals replayed")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate (requests/s)")
     ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="precision of the main timed solve (profiling aid; the bench line uses fp64)")
@@ -242,6 +245,71 @@ def run_batch_workload(args):
     return res
 
 
+def run_serve_workload(args, seed=0):
+    """Seeded Poisson arrivals of solves: domain square / L-shape with probability 1/2 each,
+    K and J independent with P(4 + k) proportional to 2^-k (k = 0..5), forcing a random smooth
+    sum of 8 modes, u0 = 0.  Served by st_server_* (binary64 PCG, binary32 preconditioner,
+    continuous batching); latency = submission to result in host memory."""
+    import numpy as np
+    import torch
+
+    from paper_2009_08875_gb300 import Server, inputs
+    rng = np.random.default_rng(seed)
+    pk = 2.0 ** -np.arange(6)
+    pk /= pk.sum()
+    t, arrivals = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / args.serve_rate)
+        if t > args.serve_seconds:
+            break
+        dom = int(rng.integers(0, 2))
+        arrivals.append((t, dom, 4 + int(rng.choice(6, p=pk)), 4 + int(rng.choice(6, p=pk))))
+    # one forcing per shape (the requests' data repeat; outputs of one shape share a buffer,
+    # so this measures timing only: correctness of served results is covered by the tests)
+    data = {}
+    for _, dom, K, J in arrivals:
+        if (dom, K, J) not in data:
+            g, u0 = inputs.smooth_forcing(K, J, seed=K * 16 + J, domain=dom)
+            g = torch.from_numpy(inputs.to_grid(K, dom, g)).pin_memory()
+            u0 = torch.from_numpy(inputs.to_grid(K, dom, u0)).pin_memory()
+            data[(dom, K, J)] = (g, u0, torch.empty(g.shape, dtype=torch.float64).pin_memory())
+    srv = Server(slots_per_group=16, memory_budget_gb=160.0, tol=TOL, maxit=500)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = []
+    for ta, dom, K, J in arrivals:
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        g, u0, u = data[(dom, K, J)]
+        tickets.append((srv.submit(dom, K, J, g, u0, u), dom, K, J))
+    lat, its, failed, pending = [], [], 0, list(tickets)
+    while pending:
+        rest = []
+        for tk in pending:
+            st = srv.poll(tk[0])
+            if st["state"] == Server.DONE:
+                lat.append(st["latency_s"])
+                its.append(st["iterations"])
+            elif st["state"] == Server.FAILED:
+                failed += 1
+            else:
+                rest.append(tk)
+        pending = rest
+        time.sleep(0.001)
+    makespan = time.perf_counter() - t0
+    srv.stop()
+    dof = sum(data[(d, K, J)][0].numel() for _, d, K, J in tickets)
+    lat_ms = np.array(lat) * 1e3
+    return {"offered_rate_per_s": args.serve_rate, "arrival_window_s": args.serve_seconds, "requests": len(tickets),
+            "failed": failed, "makespan_s": makespan, "served_per_s": len(lat) / makespan,
+            "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat) else None,
+            "iterations_mean": float(np.mean(its)) if its else None, "dof_total": dof,
+            "precision": "f64 PCG, f32 preconditioner", "tol": TOL,
+            "note": "offered load exceeds capacity: latency includes queueing behind the backlog"}
+
+
 def kernel_source_hash():
     with open(os.path.join(ROOT, "paper_2009_08875_gb300", "csrc", "k_mg.cu"), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()
@@ -380,6 +448,10 @@ def run_ours(args):
     if not args.no_batch:
         solver.close()
         batch = run_batch_workload(args)
+    serve = None
+    if not args.no_serve:
+        solver.close()
+        serve = run_serve_workload(args)
 
     if rank != 0:
         solver.close()
@@ -429,6 +501,7 @@ def run_ours(args):
         "e2e": e2e,
         "mixed": mixed,
         "batch": batch,
+        "serve": serve,
         "gpu_launches": prof["launches"],
         "clocks": clk,
     }

@@ -222,6 +222,35 @@ st_status st_batch_buckets(st_batch b, int* n);
 
 st_status st_batch_destroy(st_batch b);
 
+/* ---------------------------------------------------------------------------------------
+ * Continuous-batching server (not in the paper).  One worker thread serves queued solves:
+ * problems of one shape share a group (a batched handle with a fixed number of slots, its CG
+ * state resident on the GPU); each round it admits queued requests into free slots (creating
+ * a group when the device-memory budget allows, releasing idle groups of other shapes to make
+ * room), advances every group by one PCG iteration, and returns finished problems to their
+ * callers.  Requests thus join and leave at iteration boundaries while others run, and each
+ * result is computed exactly as if the problem were solved alone.  Precision: ST_FP64 or
+ * ST_MIXED_PRECOND.  Host buffers must stay valid until the request is done.
+ * --------------------------------------------------------------------------------------- */
+typedef struct st_server_s* st_server;
+
+/* Starts the worker on the current device.  slots_per_group: slots of a group (fewer for
+ * large shapes: at most 2 slots N_t <= 65535 and a quarter of the budget per group);
+ * memory_budget_gb: device memory the groups may hold in total. */
+st_status st_server_start(st_server* out, const st_config* cfg, int slots_per_group, double memory_budget_gb);
+
+/* Queues one solve (layout of st_solve_host; u_host receives u = W w).  *ticket identifies it. */
+st_status st_server_submit(st_server s, int domain, int space_level, int time_level, const double* g_host,
+                           const double* u0_host, double* u_host, int64_t* ticket);
+
+/* State of a request: *state 0 queued, 1 running, 2 done, 3 failed (info->relres and
+ * iterations describe the solve; a request that cannot fit in the budget fails).
+ * *latency_s (may be NULL): seconds from submission to completion, or -1 if not finished. */
+st_status st_server_poll(st_server s, int64_t ticket, int* state, st_solve_info* info, double* latency_s);
+
+/* Serves every submitted request, stops the worker and frees all device memory. */
+st_status st_server_stop(st_server s);
+
 /* Measurement hooks (not part of the method).  Between st_profile_begin and st_profile_end the
  * handle counts every kernel it launches and brackets each finest-level Gauss-Seidel sweep
  * launch (the dominant kernel) with a pair of CUDA events on the bound stream, adding up the

@@ -76,6 +76,12 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_int)]),
     "st_batch_buckets": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "st_batch_destroy": (ctypes.c_int, [_P]),
+    "st_server_start": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(StConfig), ctypes.c_int, ctypes.c_double]),
+    "st_server_submit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "st_server_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(StSolveInfo),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "st_server_stop": (ctypes.c_int, [_P]),
     "st_last_error": (ctypes.c_char_p, []),
 }
 

@@ -318,6 +318,43 @@ st_status finish(st_handle h) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// PCG iteration bodies on all B problems: p = z + beta p, q = S_hat p, alpha, w and r updates,
+// z = K_X r, rho and beta (problems whose active flag is clear keep their vectors)
+// ---------------------------------------------------------------------------------------------
+st_status body64(st_handle h, double* w) {
+  const int nb = h->B;
+  const int64_t n = h->Nt * h->Nx;
+  ST_CHECK_CUDA(launch_update_p<double>(h, 0, nb, h->p, h->z, n), "update p");
+  ST_CHECK(apply_Shat_impl<double>(h, nb, h->p, h->q));
+  ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->p, h->q, n, SC_PQ, DOT_ALPHA), "dot p q");
+  ST_CHECK_CUDA(launch_update_wr<double>(h, 0, nb, w, h->r, h->p, h->q, n), "update w r");
+  ST_CHECK(apply_KX_impl<double>(h, nb, h->r, h->z));
+  ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO_NEW, DOT_BETA), "dot r z");
+  return ST_OK;
+}
+
+st_status precond32(st_handle h, int nb, const double* r, double* z, float* ri, float* zi) {
+  const int64_t N = nb * h->Nt * h->Nx;
+  ST_CHECK_CUDA(launch_copy<float, double>(h, ri, r, N), "round r");
+  ST_CHECK(apply_KX_impl<float>(h, nb, ri, zi));
+  ST_CHECK_CUDA(launch_copy<double, float>(h, z, zi, N), "widen z");
+  return ST_OK;
+}
+
+st_status body_precond(st_handle h, double* w) {
+  const int nb = h->B;
+  const int64_t n = h->Nt * h->Nx;
+  ST_CHECK_CUDA(launch_update_p<double>(h, 0, nb, h->p, h->z, n), "update p");
+  ST_CHECK(apply_Shat_impl<double>(h, nb, h->p, h->q));
+  ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->p, h->q, n, SC_PQ, DOT_ALPHA), "dot p q");
+  ST_CHECK_CUDA(launch_update_wr<double>(h, 0, nb, w, h->r, h->p, h->q, n), "update w r");
+  ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RZOLD, DOT_STORE), "dot r z_old");
+  ST_CHECK(precond32(h, nb, h->r, h->z, h->ri, h->zi));
+  ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO_NEW, DOT_BETA_FLEX), "dot r z");
+  return ST_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
 // FP64 PCG (Sec. 3.4), all B problems in lock step, each with its own scalars and stop test
 // ---------------------------------------------------------------------------------------------
 st_status pcg64_impl(st_handle h, const double* fhat, double* w) {
@@ -335,15 +372,7 @@ st_status pcg64_impl(st_handle h, const double* fhat, double* w) {
   ST_CHECK(read_scalars(h));
   init_problems(h, t, SC_RHO0);
   ST_CHECK(push_act(h));
-  auto body = [&]() -> st_status {
-    ST_CHECK_CUDA(launch_update_p<double>(h, 0, nb, h->p, h->z, n), "update p");
-    ST_CHECK(apply_Shat_impl<double>(h, h->B, h->p, h->q));
-    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->p, h->q, n, SC_PQ, DOT_ALPHA), "dot p q");
-    ST_CHECK_CUDA(launch_update_wr<double>(h, 0, nb, w, h->r, h->p, h->q, n), "update w r");
-    ST_CHECK(apply_KX_impl<double>(h, h->B, h->r, h->z));
-    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO_NEW, DOT_BETA), "dot r z");
-    return ST_OK;
-  };
+  auto body = [&]() -> st_status { return body64(h, w); };
   for (int it = 1; it <= c.maxit && any_active(h); ++it) {
     ST_CHECK(run_body(h, 0, w, body));
     ST_CHECK(read_scalars(h));
@@ -458,14 +487,6 @@ st_status pcg_mixed_impl(st_handle h, const double* fhat, double* w) {
 // binary32 K_X as preconditioner; beta = r^T (z - z_old) / rho_old (Polak-Ribiere), which keeps
 // the method convergent for a preconditioner that is only approximately linear
 // ---------------------------------------------------------------------------------------------
-st_status precond32(st_handle h, const double* r, double* z) {
-  const int64_t N = h->B * h->Nt * h->Nx;
-  ST_CHECK_CUDA(launch_copy<float, double>(h, h->ri, r, N), "round r");
-  ST_CHECK(apply_KX_impl<float>(h, h->B, h->ri, h->zi));
-  ST_CHECK_CUDA(launch_copy<double, float>(h, z, h->zi, N), "widen z");
-  return ST_OK;
-}
-
 st_status pcg_precond_impl(st_handle h, const double* fhat, double* w) {
   const int nb = h->B;
   const int64_t n = h->Nt * h->Nx;
@@ -475,22 +496,13 @@ st_status pcg_precond_impl(st_handle h, const double* fhat, double* w) {
   ST_CHECK(push_act(h));
   ST_CHECK_CUDA(launch_zero<double>(h, w, n * nb), "zero w");
   ST_CHECK_CUDA(launch_copy<double, double>(h, h->r, fhat, n * nb), "copy r");
-  ST_CHECK(precond32(h, h->r, h->z));
+  ST_CHECK(precond32(h, nb, h->r, h->z, h->ri, h->zi));
   ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO, DOT_INIT), "dot r z");
   ST_CHECK_CUDA(launch_zero<double>(h, h->p, n * nb), "zero p");  // first body: p = z + 0 p
   ST_CHECK(read_scalars(h));
   init_problems(h, t, SC_RHO0);
   ST_CHECK(push_act(h));
-  auto body = [&]() -> st_status {
-    ST_CHECK_CUDA(launch_update_p<double>(h, 0, nb, h->p, h->z, n), "update p");
-    ST_CHECK(apply_Shat_impl<double>(h, h->B, h->p, h->q));
-    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->p, h->q, n, SC_PQ, DOT_ALPHA), "dot p q");
-    ST_CHECK_CUDA(launch_update_wr<double>(h, 0, nb, w, h->r, h->p, h->q, n), "update w r");
-    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RZOLD, DOT_STORE), "dot r z_old");
-    ST_CHECK(precond32(h, h->r, h->z));
-    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO_NEW, DOT_BETA_FLEX), "dot r z");
-    return ST_OK;
-  };
+  auto body = [&]() -> st_status { return body_precond(h, w); };
   for (int it = 1; it <= c.maxit && any_active(h); ++it) {
     ST_CHECK(run_body(h, 2, w, body));
     ST_CHECK(read_scalars(h));
@@ -533,6 +545,50 @@ st_status pcg_impl(st_handle h, const double* fhat, double* w, int* iters, doubl
   if (relres) *relres = h->last_relres;
   return s;
 }
+
+// ---------------------------------------------------------------------------------------------
+// slot-level operations for continuous batching (server.cu): problem b of a batched handle
+// joins, all problems advance one iteration, a finished problem leaves
+// ---------------------------------------------------------------------------------------------
+// Starts problem b from the inputs already in its slots of h->g and h->u0: f_hat, w = 0,
+// r = f_hat, z = K_X r, p = 0, rho = rho0 = r^T z, beta = 0 (so the next body sets p = z).
+st_status slot_start(st_handle_s* h, int b) {
+  const int64_t V = h->Nt * h->Nx;
+  ST_CHECK(rhs_impl(h, 1, h->g + b * V, h->u0 + b * h->Nx, h->fhat + b * V));
+  ST_CHECK_CUDA(launch_zero<double>(h, h->w + b * V, V), "zero w");
+  ST_CHECK_CUDA(launch_zero<double>(h, h->p + b * V, V), "zero p");
+  ST_CHECK_CUDA(launch_copy<double, double>(h, h->r + b * V, h->fhat + b * V, V), "copy r");
+  if (h->cfg.precision == ST_MIXED_PRECOND)
+    ST_CHECK(precond32(h, 1, h->r + b * V, h->z + b * V, h->ri + b * V, h->zi + b * V));
+  else
+    ST_CHECK(apply_KX_impl<double>(h, 1, h->r + b * V, h->z + b * V));
+  ST_CHECK_CUDA(launch_dot<double, double>(h, b, 1, h->r + b * V, h->z + b * V, V, SC_RHO, DOT_INIT), "dot r z");
+  return ST_OK;
+}
+
+// One iteration body for every problem of the handle (graph-captured), then the scalar
+// readback enqueued on the handle's stream (not waited for).
+st_status step_enqueue(st_handle_s* h) {
+  if (h->cfg.precision == ST_MIXED_PRECOND)
+    ST_CHECK(run_body(h, 2, h->w, [&]() { return body_precond(h, h->w); }));
+  else
+    ST_CHECK(run_body(h, 0, h->w, [&]() { return body64(h, h->w); }));
+  ST_CHECK_CUDA(cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * SC_COUNT * h->B, cudaMemcpyDeviceToHost,
+                                h->stream),
+                "scalar readback");
+  return ST_OK;
+}
+
+// u = W w of problem b copied to u_host (enqueued, not waited for).
+st_status slot_result(st_handle_s* h, int b, double* u_host) {
+  const int64_t V = h->Nt * h->Nx;
+  ST_CHECK_CUDA(wavelet_synth<double>(h, 1, h->w + b * V, h->U + b * V), "wavelet synthesis");
+  ST_CHECK_CUDA(cudaMemcpyAsync(u_host, h->U + b * V, sizeof(double) * V, cudaMemcpyDeviceToHost, h->stream),
+                "copy result");
+  return ST_OK;
+}
+
+st_status push_active(st_handle_s* h) { return push_act(h); }
 
 }  // namespace st
 

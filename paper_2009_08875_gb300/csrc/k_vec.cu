@@ -66,18 +66,18 @@ __global__ void __launch_bounds__(256) k_dot_final(const double* __restrict__ pa
       case DOT_STORE:
         sc[slot] = t;
         break;
-      case DOT_ALPHA:  // t = p^T q
+      case DOT_ALPHA:  // t = p^T q (a zero problem, r = p = 0, takes no step)
         sc[SC_PQ] = t;
-        sc[SC_ALPHA] = on ? sc[SC_RHO] / t : 0.0;
+        sc[SC_ALPHA] = (on && t != 0.0) ? sc[SC_RHO] / t : 0.0;
         break;
       case DOT_BETA:  // t = r^T z (new)
         sc[SC_RHO_NEW] = t;
-        sc[SC_BETA] = on ? t / sc[SC_RHO] : 0.0;
+        sc[SC_BETA] = (on && sc[SC_RHO] != 0.0) ? t / sc[SC_RHO] : 0.0;
         if (on) sc[SC_RHO] = t;
         break;
       case DOT_BETA_FLEX:  // t = r^T z (new); slot SC_RZOLD holds r^T z_old (Polak-Ribiere)
         sc[SC_RHO_NEW] = t;
-        sc[SC_BETA] = on ? (t - sc[SC_RZOLD]) / sc[SC_RHO] : 0.0;
+        sc[SC_BETA] = (on && sc[SC_RHO] != 0.0) ? (t - sc[SC_RZOLD]) / sc[SC_RHO] : 0.0;
         if (on) sc[SC_RHO] = t;
         break;
       case DOT_INIT:  // t = r_0^T z_0; beta = 0 makes the first p = z + beta p (p = 0) equal z

@@ -193,6 +193,11 @@ cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, co
 // problems of the handle in its configured precision
 st_status rhs_impl(st_handle_s* h, int nb, const double* g, const double* u0, double* fhat);
 st_status pcg_impl(st_handle_s* h, const double* fhat, double* w, int* iters, double* relres);
+// continuous batching on a handle's slots (ST_FP64 or ST_MIXED_PRECOND): see api.cu
+st_status slot_start(st_handle_s* h, int b);
+st_status step_enqueue(st_handle_s* h);
+st_status slot_result(st_handle_s* h, int b, double* u_host);
+st_status push_active(st_handle_s* h);
 
 // PCG scalar slots in h->scal
 enum {

@@ -215,3 +215,48 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching solve server (st_server_*).  submit() takes host tensors that must stay
+    alive until poll() reports the request done; stop() serves everything and shuts down."""
+
+    QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
+
+    def __init__(self, slots_per_group=16, memory_budget_gb=100.0, **cfg):
+        cfg.setdefault("precision", "mixed_precond")
+        self._cfg = _config(**cfg)
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().st_server_start(ctypes.byref(h), ctypes.byref(self._cfg), slots_per_group,
+                                               memory_budget_gb))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, domain, K, J, g, u0, u):
+        n = 2 ** K - 1
+        Nt, Nx = 2 ** J + 1, n * n
+        t = ctypes.c_int64()
+        _lib.check(_lib.load().st_server_submit(self._h, domain, K, J, _ptr(g, (Nt, Nx), "g", False),
+                                                _ptr(u0, (Nx,), "u0", False), _ptr(u, (Nt, Nx), "u", False),
+                                                ctypes.byref(t)))
+        self._keep[t.value] = (g, u0, u)
+        return t.value
+
+    def poll(self, ticket):
+        st, info, lat = ctypes.c_int(), _lib.StSolveInfo(), ctypes.c_double()
+        _lib.check(_lib.load().st_server_poll(self._h, ticket, ctypes.byref(st), ctypes.byref(info),
+                                              ctypes.byref(lat)))
+        if st.value >= self.DONE:
+            self._keep.pop(ticket, None)
+        return {"state": st.value, "iterations": info.iterations, "relres": info.relres, "latency_s": lat.value}
+
+    def stop(self):
+        if getattr(self, "_h", None):
+            h, self._h = self._h, None
+            _lib.check(_lib.load().st_server_stop(h))
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
