@@ -251,6 +251,21 @@ st_status st_server_poll(st_server s, int64_t ticket, int* state, st_solve_info*
 /* Serves every submitted request, stops the worker and frees all device memory. */
 st_status st_server_stop(st_server s);
 
+/* Autotuner (not in the paper).  Two Gauss-Seidel kernels compute identical sweeps: shared-
+ * memory tiles (the default) and a register wavefront.  For every multigrid level above the
+ * coarsest, for binary64 and binary32 and for K_x (no mass couplings, 2 B N_t slices) and K_l
+ * (mass couplings, B N_t slices), this times one pre-smoothing launch of each on the handle's
+ * workspace and keeps the faster for later calls on this handle.  Synchronous.
+ * times_ms (may be NULL) receives 8 x 16 floats: times_ms[8 k + i] for level k and i = 0..7 in
+ * the order (binary64 K_x: tiles, wavefront; binary64 K_l: tiles, wavefront; binary32 K_x:
+ * tiles, wavefront; binary32 K_l: tiles, wavefront). */
+st_status st_autotune(st_handle h, float* times_ms);
+
+/* Forces one Gauss-Seidel kernel on every level of this handle: kind 0 shared-memory tiles (the
+ * state after set-up), 1 register wavefront.  Both give bitwise the same sweeps.  Returns
+ * ST_ERR_ARG for any other kind. */
+st_status st_set_smoother(st_handle h, int kind);
+
 /* Measurement hooks (not part of the method).  Between st_profile_begin and st_profile_end the
  * handle counts every kernel it launches and brackets each finest-level Gauss-Seidel sweep
  * launch (the dominant kernel) with a pair of CUDA events on the bound stream, adding up the

@@ -66,6 +66,8 @@ _SIGS = {
     "st_apply_KX_f32": (ctypes.c_int, [_P, _P, _P]),
     "st_solve_host": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double)]),
+    "st_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "st_set_smoother": (ctypes.c_int, [_P, ctypes.c_int]),
     "st_profile_begin": (ctypes.c_int, [_P]),
     "st_profile_end": (ctypes.c_int, [_P, ctypes.POINTER(StProfile)]),
     "st_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(StConfig)]),

@@ -321,8 +321,7 @@ st_status finish(st_handle h) {
 // PCG iteration bodies on all B problems: p = z + beta p, q = S_hat p, alpha, w and r updates,
 // z = K_X r, rho and beta (problems whose active flag is clear keep their vectors)
 // ---------------------------------------------------------------------------------------------
-st_status body64(st_handle h, double* w) {
-  const int nb = h->B;
+st_status body64(st_handle h, double* w, int nb) {
   const int64_t n = h->Nt * h->Nx;
   ST_CHECK_CUDA(launch_update_p<double>(h, 0, nb, h->p, h->z, n), "update p");
   ST_CHECK(apply_Shat_impl<double>(h, nb, h->p, h->q));
@@ -341,8 +340,7 @@ st_status precond32(st_handle h, int nb, const double* r, double* z, float* ri, 
   return ST_OK;
 }
 
-st_status body_precond(st_handle h, double* w) {
-  const int nb = h->B;
+st_status body_precond(st_handle h, double* w, int nb) {
   const int64_t n = h->Nt * h->Nx;
   ST_CHECK_CUDA(launch_update_p<double>(h, 0, nb, h->p, h->z, n), "update p");
   ST_CHECK(apply_Shat_impl<double>(h, nb, h->p, h->q));
@@ -372,7 +370,7 @@ st_status pcg64_impl(st_handle h, const double* fhat, double* w) {
   ST_CHECK(read_scalars(h));
   init_problems(h, t, SC_RHO0);
   ST_CHECK(push_act(h));
-  auto body = [&]() -> st_status { return body64(h, w); };
+  auto body = [&]() -> st_status { return body64(h, w, nb); };
   for (int it = 1; it <= c.maxit && any_active(h); ++it) {
     ST_CHECK(run_body(h, 0, w, body));
     ST_CHECK(read_scalars(h));
@@ -502,7 +500,7 @@ st_status pcg_precond_impl(st_handle h, const double* fhat, double* w) {
   ST_CHECK(read_scalars(h));
   init_problems(h, t, SC_RHO0);
   ST_CHECK(push_act(h));
-  auto body = [&]() -> st_status { return body_precond(h, w); };
+  auto body = [&]() -> st_status { return body_precond(h, w, nb); };
   for (int it = 1; it <= c.maxit && any_active(h); ++it) {
     ST_CHECK(run_body(h, 2, w, body));
     ST_CHECK(read_scalars(h));
@@ -566,14 +564,16 @@ st_status slot_start(st_handle_s* h, int b) {
   return ST_OK;
 }
 
-// One iteration body for every problem of the handle (graph-captured), then the scalar
-// readback enqueued on the handle's stream (not waited for).
-st_status step_enqueue(st_handle_s* h) {
+// One iteration body for problems 0 .. nb - 1 of the handle (graph-captured; a different nb
+// captures again), then the scalar readback enqueued on the handle's stream (not waited for).
+st_status step_enqueue(st_handle_s* h, int nb) {
+  // the graph key combines the vector it writes and the problem count
+  const void* key = reinterpret_cast<const char*>(h->w) + nb;
   if (h->cfg.precision == ST_MIXED_PRECOND)
-    ST_CHECK(run_body(h, 2, h->w, [&]() { return body_precond(h, h->w); }));
+    ST_CHECK(run_body(h, 2, key, [&]() { return body_precond(h, h->w, nb); }));
   else
-    ST_CHECK(run_body(h, 0, h->w, [&]() { return body64(h, h->w); }));
-  ST_CHECK_CUDA(cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * SC_COUNT * h->B, cudaMemcpyDeviceToHost,
+    ST_CHECK(run_body(h, 0, key, [&]() { return body64(h, h->w, nb); }));
+  ST_CHECK_CUDA(cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double) * SC_COUNT * nb, cudaMemcpyDeviceToHost,
                                 h->stream),
                 "scalar readback");
   return ST_OK;
@@ -867,6 +867,32 @@ st_status st_solve_host(st_handle h, const double* g_host, const double* u0_host
   ST_CHECK_CUDA(cudaMemcpyAsync(u_host, h->g, V * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy u");
   ST_CHECK_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
   return ps;
+}
+
+st_status st_autotune(st_handle h, float* times_ms) {
+  ST_CHECK(check_handle(h));
+  float table[8 * 16] = {0};
+  ST_CHECK_CUDA(mg_autotune(h, table), "autotune");
+  for (int i = 0; i < 3; ++i) {  // graphs captured with the old choices are stale
+    if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
+    h->graph_exec[i] = nullptr;
+  }
+  if (times_ms) std::memcpy(times_ms, table, sizeof(table));
+  return ST_OK;
+}
+
+st_status st_set_smoother(st_handle h, int kind) {
+  ST_CHECK(check_handle(h));
+  if (kind != 0 && kind != 1) {
+    set_error("st_set_smoother: kind must be 0 (tiles) or 1 (wavefront)");
+    return ST_ERR_ARG;
+  }
+  std::memset(h->gs_kind, kind, sizeof(h->gs_kind));
+  for (int i = 0; i < 3; ++i) {
+    if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
+    h->graph_exec[i] = nullptr;
+  }
+  return ST_OK;
 }
 
 st_status st_profile_begin(st_handle h) {

@@ -205,6 +205,131 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Gauss-Seidel as a register wavefront.  One warp owns a strip of 96 columns (3 per lane) of one
+// slice and walks its rows from bottom to top.  The S = 3 * NSW colour steps of NSW sweeps form
+// a pipeline along the rows: at time tau, step s (colour c_s) updates row tau - s, for
+// s = 0, 1, ..., S - 1 in that order.  Row j then sees row j + 1 after step s - 1 (done earlier
+// in the same time step) and row j - 1 after step s, which differs from "after step s - 1" only
+// at colour c_s, and same-colour points of adjacent rows are not coupled (the 7-point pattern
+// couples (i, j) with (i, j - 1) and (i - 1, j - 1), whose colours differ).  So the result is
+// that of sequential colour-by-colour sweeps.  The rows tau - S .. tau + 1 of x (and tau - S + 1
+// .. tau of b) live in registers, horizontal neighbours come from the adjacent lane by shuffles,
+// and only the strip's horizontal halo (S columns each side) is recomputed; row tau - S + 1 is
+// complete at time tau and is stored.  For parallelism a strip is also cut into segments of SEG
+// rows, each walked by its own warp over SEG + 2 S rows: errors from the segment's missing
+// neighbours travel one row per colour step, so after S steps the middle SEG rows are exact.
+// ---------------------------------------------------------------------------------------
+template <typename T, int S, bool DIAG, bool PROL>
+__global__ void __launch_bounds__(128) k_gs_wave(T* __restrict__ x_out, const T* __restrict__ x_in,
+                                                 const T* __restrict__ b, const T* __restrict__ xc, int n,
+                                                 const Coef<T>* __restrict__ coef, int coef_class, int J, int K,
+                                                 int level, int reverse, int zero_init, int lshape, int nstrips,
+                                                 int nseg, int seg, int nslices) {
+  constexpr int W = S + 2;          // ring of x rows: row ybase + r lives in slot r mod W
+  constexpr int TXW = kWR - 2 * S;  // output columns of a strip
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (gw >= nstrips * nseg * nslices) return;  // whole warps only
+  const int slice = gw / (nstrips * nseg);
+  const int rest = gw - slice * nstrips * nseg;
+  const int sg = rest / nstrips, strip = rest - sg * nstrips;
+  const int r0 = sg * seg;        // first output row of the segment
+  const int ybase = r0 - S;       // row of time step 0
+  const int gx0 = strip * TXW - S;      // global column of the strip's column 0
+  const int64_t off = (int64_t)slice * n * n;
+  const T* xin = x_in + off;
+  const T* bsl = b + off;
+  T* xo = x_out + off;
+  const int nc = (n - 1) / 2;
+  const T* xcs = PROL ? xc + (int64_t)slice * nc * nc : nullptr;
+  const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, level);
+  const int cbase = gx0 + 3 * lane;  // global column of this lane's element 0
+
+  T xw[W][3], bw[W][3];
+#pragma unroll
+  for (int r = 0; r < W; ++r)
+#pragma unroll
+    for (int e = 0; e < 3; ++e) xw[r][e] = bw[r][e] = T(0);
+
+  auto load_row = [&](int r, T (&xr)[3], T (&br)[3]) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int gx = cbase + e;
+      const bool in = r >= 0 && r < n && gx >= 0 && gx < n && !outside_domain(gx, r, n, lshape);
+      const int64_t gi = (int64_t)r * n + gx;
+      T v = (in && !zero_init) ? xin[gi] : T(0);
+      if (PROL && in) v += prolong_value(xcs, nc, gx + 1, r + 1);
+      xr[e] = v;
+      br[e] = in ? bsl[gi] : T(0);
+    }
+  };
+
+  // one colour step on row j: xc = row j, xn = row j + 1, xs = row j - 1, bc = b of row j
+  auto update_row = [&](T (&xcr)[3], const T (&xn)[3], const T (&xs)[3], const T (&bc)[3], int j, int s,
+                        int colour) {
+    int m = (colour - 2 - j - gx0) % 3;  // the lane's element of this colour in row j
+    m += (m < 0) ? 3 : 0;
+    const int cl = 3 * lane + m;
+    const int gx = cbase + m;
+    const bool ok = cl >= s + 1 && cl < kWR - s - 1 && gx >= 0 && gx < n && !outside_domain(gx, j, n, lshape);
+    // neighbours west, east, south, north, north-east, south-west (uniform branch on m)
+    const T up_c2 = __shfl_up_sync(0xffffffffu, xcr[2], 1);
+    const T dn_c0 = __shfl_down_sync(0xffffffffu, xcr[0], 1);
+    T up_s2 = T(0), dn_n0 = T(0);
+    if (DIAG) {
+      up_s2 = __shfl_up_sync(0xffffffffu, xs[2], 1);
+      dn_n0 = __shfl_down_sync(0xffffffffu, xn[0], 1);
+    }
+    if (m == 0) {
+      T v = bc[0] - cf.axs * ((up_c2 + xcr[1]) + (xs[0] + xn[0]));
+      if (DIAG) v -= cf.dgs * (xn[1] + up_s2);
+      if (ok) xcr[0] = v;
+    } else if (m == 1) {
+      T v = bc[1] - cf.axs * ((xcr[0] + xcr[2]) + (xs[1] + xn[1]));
+      if (DIAG) v -= cf.dgs * (xn[2] + xs[0]);
+      if (ok) xcr[1] = v;
+    } else {
+      T v = bc[2] - cf.axs * ((xcr[1] + dn_c0) + (xs[2] + xn[2]));
+      if (DIAG) v -= cf.dgs * (dn_n0 + xs[1]);
+      if (ok) xcr[2] = v;
+    }
+  };
+
+  load_row(ybase, xw[0], bw[0]);
+  const int L = seg + 2 * S;      // rows walked
+  const int tau_end = L + S - 1;  // the last row completes at tau = L + S - 2
+  const int r1 = min(r0 + seg, n);
+  for (int tau0 = 0; tau0 < tau_end; tau0 += W) {
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const int tau = tau0 + u;
+      if (tau < tau_end) {
+        load_row(ybase + tau + 1, xw[(u + 1) % W], bw[(u + 1) % W]);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const int j = ybase + tau - s;
+          if (tau - s >= 0 && tau - s < L && j >= 0 && j < n) {
+            const int tc = s % 3;
+            update_row(xw[(u - s + 4 * W) % W], xw[(u - s + 1 + 4 * W) % W], xw[(u - s - 1 + 4 * W) % W],
+                       bw[(u - s + 4 * W) % W], j, s, reverse ? 2 - tc : tc);
+          }
+        }
+        const int ro = ybase + tau - S + 1;
+        if (ro >= r0 && ro < r1) {
+          const T(&xr)[3] = xw[(u - S + 1 + 4 * W) % W];
+#pragma unroll
+          for (int e = 0; e < 3; ++e) {
+            const int cl = 3 * lane + e;
+            const int gx = cbase + e;
+            if (cl >= S && cl < kWR - S && gx < n) xo[(int64_t)ro * n + gx] = xr[e];
+          }
+        }
+      }
+    }
+  }
+}
+
 // b' = b / c on the finest level (the multigrid's scaled right-hand side)
 template <typename T>
 __global__ void k_scale_rhs(T* __restrict__ bs, const T* __restrict__ b, int n, const Coef<T>* __restrict__ coef,
@@ -328,6 +453,9 @@ struct SweepShape;
 #ifndef ST_GS_HR32
 #define ST_GS_HR32 64
 #endif
+#ifndef ST_GS_SEG
+#define ST_GS_SEG 64
+#endif
 #ifndef ST_GS_NSW32
 #define ST_GS_NSW32 3
 #endif
@@ -363,12 +491,50 @@ cudaError_t gs_launch(const st_handle_s* h, int k, int nslices, int cls, T* x_ou
   return cudaGetLastError();
 }
 
+template <typename T, int NSW, bool DIAG, bool PROL>
+cudaError_t wave_launch(const st_handle_s* h, int k, int nslices, int cls, T* x_out, const T* x_in, const T* b,
+                        const T* xc, bool reverse, bool zero_init) {
+  constexpr int S = 3 * NSW;
+  const int n = (1 << k) - 1;
+  const int TXW = kWR - 2 * S;
+  const int nstrips = (n + TXW - 1) / TXW;
+  const int seg = ST_GS_SEG;
+  const int nseg = (n + seg - 1) / seg;
+  const int64_t warps = (int64_t)nstrips * nseg * nslices;
+  const unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
+  const bool prof = (k == h->K) && prof_start(h);
+  k_gs_wave<T, S, DIAG, PROL><<<blocks, 128, 0, h->stream>>>(x_out, x_in, b, xc, n, coef_table<T>(h), cls, h->J,
+                                                              h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0,
+                                                              h->domain, nstrips, nseg, seg, nslices);
+  count_launch(h);
+  if (prof) {
+    const double pts = (double)n * n * nslices;
+    prof_stop(h, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(T) * (zero_init ? 2.0 : 3.0));
+  }
+  return cudaGetLastError();
+}
+
 // nsw consecutive sweeps of one colour order from x_in (+ P xc if xc != nullptr) into x_out
 // (x_in == x_out is not allowed)
+// Which Gauss-Seidel kernel a launch uses: the handle's autotuned choice per element type,
+// coupling pattern and level (0: shared-memory tiles, the default; 1: register wavefront).
+template <typename T>
+int gs_kind(const st_handle_s* h, bool diag, int k) {
+  return h->gs_kind[sizeof(T) == 4 ? 1 : 0][diag ? 1 : 0][k];
+}
+
 template <typename T, bool DIAG>
 cudaError_t gs_sweeps(const st_handle_s* h, int k, int nslices, int cls, T* x_out, const T* x_in, const T* b,
                       const T* xc, bool reverse, bool zero_init, int nsw) {
-  constexpr int F = SweepShape<T>::kFusedNSW, FHR = SweepShape<T>::kFusedHR, HR1 = SweepShape<T>::kSingleHR;
+  constexpr int F = SweepShape<T>::kFusedNSW;
+  if (gs_kind<T>(h, DIAG, k) == 1) {
+    if (F > 1 && nsw == F)
+      return xc ? wave_launch<T, F, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
+                : wave_launch<T, F, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+    return xc ? wave_launch<T, 1, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
+              : wave_launch<T, 1, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+  }
+  constexpr int FHR = SweepShape<T>::kFusedHR, HR1 = SweepShape<T>::kSingleHR;
   if (F > 1 && nsw == F) {
     return xc ? gs_launch<T, F, FHR, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
               : gs_launch<T, F, FHR, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
@@ -494,6 +660,61 @@ cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T*
   // an odd total number of sweeps leaves the iterate in the alternate buffer
   if (cur == 1) return cudaMemcpyAsync(x, xb[1], bytes, cudaMemcpyDeviceToDevice, h->stream);
   return cudaSuccess;
+}
+
+// Times both Gauss-Seidel kernels on every level of the handle's shapes (the pre-smoothing
+// launch of a V-cycle: K_x on 2 B N_t slices, K_l on B N_t slices) and keeps the faster per
+// element type, coupling pattern and level.  Uses the workspace as scratch.
+template <typename T, bool DIAG>
+cudaError_t autotune_one(st_handle_s* h, int k, float* ms_tile, float* ms_wave) {
+  const int nslices = (int)((DIAG ? 1 : 2) * h->B * h->Nt);
+  const int cls = DIAG ? -1 : 0;
+  T* xo = reinterpret_cast<T*>(h->X);
+  const T* xi = reinterpret_cast<const T*>(h->Xalt);
+  const T* b = reinterpret_cast<const T*>(h->Bs);
+  const int nsw = SweepShape<T>::kFusedNSW;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best[2] = {0.f, 0.f};
+  cudaError_t err = cudaSuccess;
+  for (int kind = 0; kind < 2 && err == cudaSuccess; ++kind) {
+    h->gs_kind[sizeof(T) == 4 ? 1 : 0][DIAG ? 1 : 0][k] = (unsigned char)kind;
+    float t = 1e30f;
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      err = gs_sweeps<T, DIAG>(h, k, nslices, cls, xo, xi, b, nullptr, false, false, nsw);
+      cudaEventRecord(e1, h->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) t = ms < t ? ms : t;  // the first run warms up
+    }
+    best[kind] = t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->gs_kind[sizeof(T) == 4 ? 1 : 0][DIAG ? 1 : 0][k] = best[1] < best[0] ? 1 : 0;
+  *ms_tile = best[0];
+  *ms_wave = best[1];
+  return err;
+}
+
+cudaError_t mg_autotune(st_handle_s* h, float* table) {
+  const size_t bytes = sizeof(double) * 2 * (size_t)h->B * h->Nt * h->Nx;
+  cudaError_t e = cudaMemsetAsync(h->Xalt, 0, bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Bs, 0, bytes, h->stream);
+  const bool saved = h->prof_on;
+  h->prof_on = false;
+  for (int k = h->mg.kmin + 1; k <= h->K && e == cudaSuccess; ++k) {
+    float* row = table + 8 * k;
+    if (e == cudaSuccess) e = autotune_one<double, false>(h, k, row + 0, row + 1);
+    if (e == cudaSuccess) e = autotune_one<double, true>(h, k, row + 2, row + 3);
+    if (e == cudaSuccess) e = autotune_one<float, false>(h, k, row + 4, row + 5);
+    if (e == cudaSuccess) e = autotune_one<float, true>(h, k, row + 6, row + 7);
+  }
+  h->prof_on = saved;
+  return e;
 }
 
 template cudaError_t mg_apply<double>(const st_handle_s*, int, int, const double*, double*);

@@ -237,7 +237,10 @@ void worker_loop(st_server_s* s) {
         if (st != ST_OK) return fail_server(s, st, "active flags");
         g->joining.clear();
       }
-      st_status st = step_enqueue(g->h);
+      // only the occupied prefix of the slots is computed (free slots cost nothing)
+      int nb = g->slots;
+      while (nb > 0 && !g->slot[nb - 1]) --nb;
+      st_status st = step_enqueue(g->h, nb);
       if (st != ST_OK) return fail_server(s, st, "iteration");
       g->last_used = Clock::now();
     }

@@ -101,6 +101,9 @@ struct st_handle_s {
   int last_iters, last_outer;
   double last_relres;
   int B;             // problems in the batch (vectors are B x N_t x N_x)
+  // Gauss-Seidel kernel per [element type: 0 binary64, 1 binary32][mass couplings][level]:
+  // 0 shared-memory tiles (default), 1 register wavefront (chosen by st_autotune)
+  unsigned char gs_kind[2][2][16];
   // CUDA graphs of the PCG iteration bodies (0: binary64 PCG, 1: binary32 inner PCG,
   // 2: binary64 PCG with binary32 preconditioner), re-captured when `graph_key` changes
   cudaGraphExec_t graph_exec[3];
@@ -150,6 +153,9 @@ cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, cu
 // coef_class < 0: per-slice class 1 + level(slice) (K_X); else a fixed class.
 template <typename T>
 cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x);
+// times both Gauss-Seidel kernels per level and records the faster in h->gs_kind; table[8 k + i]
+// receives the times (ms) of (binary64 K_x tile, wave, binary64 K_l tile, wave, binary32 ...)
+cudaError_t mg_autotune(st_handle_s* h, float* table);
 
 // The time-coupled launchers act on nb problems stored back to back (N_t x N_x each).
 // wavelet transforms over N_t x N_x
@@ -195,7 +201,7 @@ st_status rhs_impl(st_handle_s* h, int nb, const double* g, const double* u0, do
 st_status pcg_impl(st_handle_s* h, const double* fhat, double* w, int* iters, double* relres);
 // continuous batching on a handle's slots (ST_FP64 or ST_MIXED_PRECOND): see api.cu
 st_status slot_start(st_handle_s* h, int b);
-st_status step_enqueue(st_handle_s* h);
+st_status step_enqueue(st_handle_s* h, int nb);
 st_status slot_result(st_handle_s* h, int b, double* u_host);
 st_status push_active(st_handle_s* h);
 

@@ -142,6 +142,19 @@ class Solver:
         _lib.check(st)
         return it.value, rr.value
 
+    def autotune(self):
+        """Time both Gauss-Seidel kernels per level and keep the faster (st_autotune).
+        Returns {level: {"f64_Kx": (tiles_ms, wave_ms), "f64_Kl": ..., "f32_Kx": ..., "f32_Kl": ...}}."""
+        t = (ctypes.c_float * 128)()
+        _lib.check(_lib.load().st_autotune(self._h, t))
+        names = ("f64_Kx", "f64_Kl", "f32_Kx", "f32_Kl")
+        return {k: {nm: (t[8 * k + 2 * i], t[8 * k + 2 * i + 1]) for i, nm in enumerate(names)}
+                for k in range(2, self.K + 1) if any(t[8 * k + i] for i in range(8))}
+
+    def set_smoother(self, kind):
+        """Force the Gauss-Seidel kernel on every level: 'tiles' or 'wavefront' (st_set_smoother)."""
+        _lib.check(_lib.load().st_set_smoother(self._h, {"tiles": 0, "wavefront": 1}[kind]))
+
     def profile_begin(self):
         """Start counting launches and timing finest-level sweeps (measurement hook)."""
         _lib.check(_lib.load().st_profile_begin(self._h))

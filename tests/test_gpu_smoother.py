@@ -1,0 +1,77 @@
+"""The two Gauss-Seidel kernels (shared-memory tiles, register wavefront) and the autotuner.
+
+Both kernels perform the same three-colour sweeps with the same summation order per point, so
+every operator that runs the multigrid preconditioner (K_x, K_X, and the binary32 K_X) must give
+bitwise the same result with either, on the square and on the L-shape, for one problem and for a
+batch.  The autotuner only picks between them, so a solve after st_autotune must give bitwise the
+solve before it.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2009_08875_gb300 import Solver, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def run_ops(s, x):
+    out = {}
+    y = torch.empty_like(x)
+    s.apply_KX(x, y)
+    out["KX"] = y.clone()
+    x32 = x.float()
+    y32 = torch.empty_like(x32)
+    s.apply_KX_f32(x32, y32)
+    out["KX32"] = y32.clone()
+    b = torch.cat([x.reshape(-1, s.Nx), x.reshape(-1, s.Nx)]).contiguous()
+    xk = torch.empty_like(b)
+    s.apply_Kx(b, xk)
+    out["Kx"] = xk.clone()
+    torch.cuda.synchronize()
+    return out
+
+
+# K = 3 (one tile / strip), K = 6 and K = 8 (several strips and vertical segments, ragged edges)
+@pytest.mark.parametrize("K,J,domain,B", [(3, 3, 0, 1), (6, 4, 0, 1), (8, 2, 0, 1), (6, 3, 1, 1), (5, 3, 0, 3),
+                                          (7, 2, 1, 2)])
+def test_tiles_and_wavefront_bitwise_equal(K, J, domain, B):
+    with Solver(K, J, domain=domain, batch=B) as s:
+        rng = np.random.default_rng(K * 100 + J)
+        x = rng.standard_normal(s.shape)
+        if domain == 1:
+            x = x * inputs.grid_mask(K, 1).reshape(-1)
+        x = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        s.set_smoother("tiles")
+        a = run_ops(s, x)
+        s.set_smoother("wavefront")
+        b = run_ops(s, x)
+        for name in a:
+            assert torch.equal(a[name], b[name]), name
+
+
+def test_set_smoother_rejects_unknown_kind():
+    from paper_2009_08875_gb300 import _lib
+    with Solver(3, 2) as s:
+        assert _lib.load().st_set_smoother(s._h, 2) == 1  # ST_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_precond"])
+def test_autotune_keeps_solution_bitwise(precision):
+    K, J = 6, 4
+    g, u0 = inputs.smooth_forcing(K, J, seed=3)
+    g = torch.from_numpy(inputs.to_grid(K, 0, g)).pin_memory()
+    u0 = torch.from_numpy(inputs.to_grid(K, 0, u0)).pin_memory()
+    with Solver(K, J, precision=precision, use_graphs=True) as s:
+        u1 = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
+        it1, _ = s.solve_host(g, u0, u1)
+        table = s.autotune()
+        assert set(table) == set(range(2, K + 1))
+        for row in table.values():
+            for tiles_ms, wave_ms in row.values():
+                assert tiles_ms > 0 and wave_ms > 0
+        u2 = torch.zeros_like(u1)
+        it2, _ = s.solve_host(g, u0, u2)
+    assert it1 == it2
+    assert torch.equal(u1, u2)
