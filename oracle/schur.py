@@ -36,16 +36,21 @@ def rows(Bx, U):
 
 
 class Problem:
-    """The discrete heat-equation problem of Sec. 5 on mesh level K, time level J."""
+    """The discrete problem of Sec. 5 on mesh level K, time level J: the heat equation, or with
+    D (2 x 2 symmetric positive definite) and c >= 0 the reaction-diffusion equation of Sec. 4,
+    whose A_x = <D grad, grad> + c M_x enters S, f and every K (Lemma 4.1, Thm. 3.1)."""
 
     def __init__(self, K: int, J: int, domain: int = space.SQUARE, alpha: float = 0.3,
-                 n_cycles: int = 2, n_pre: int = 3, n_post: int = 3, inverses: str = "mg"):
+                 n_cycles: int = 2, n_pre: int = 3, n_post: int = 3, inverses: str = "mg",
+                 D=None, c: float = 0.0):
         if J < 1:
             raise ValueError("time level must be >= 1")
         self.K, self.J, self.domain, self.alpha = K, J, domain, alpha
+        self.D = None if D is None else np.asarray(D, dtype=np.float64).reshape(2, 2)
+        self.c = float(c)
         self.mesh = space.Mesh(K, domain)
         self.Mx = space.mass_matrix(self.mesh)
-        self.Ax = space.stiffness_matrix(self.mesh)
+        self.Ax = space.operator_matrix(self.mesh, self.D, self.c)
         tm = tmod.time_matrices(J)
         self.Mt, self.At, self.L = tm["Mt"], tm["At"], tm["L"]
         self.T, self.Nm, self.O, self.Gamma0 = tm["T"], tm["N"], tm["O"], tm["Gamma0"]
@@ -57,9 +62,9 @@ class Problem:
 
         def make(a, s):
             if inverses == "mg":
-                return space.Multigrid(K, domain, a, s, n_cycles, n_pre, n_post)
+                return space.Multigrid(K, domain, a, s, n_cycles, n_pre, n_post, self.D, self.c)
             if inverses == "direct":
-                return space.DirectInverse(K, domain, a, s)
+                return space.DirectInverse(K, domain, a, s, self.D, self.c)
             raise ValueError(inverses)
 
         # K_x ~ A_x^-1 inside K_Y (Sec. 3.1); K_l ~ (alpha A_x + 2^l M_x)^-1 inside K_X

@@ -11,9 +11,11 @@ What is computed, and where the paper fixes it
   Reading: the paper's "4^K triangles" is taken as 2^K x 2^K squares, each cut
   along its lower-left to upper-right diagonal, which is what the stated
   N_x = (2^K - 1)^2 requires.
-* Lemma 4.1: M_x = <phi, phi>_{L2}, A_x = <grad phi, grad phi>_{L2} (D = Id,
-  c = 0 for the heat equation, Sec. 5).  Both are assembled here element by
-  element from the P1 element matrices; no stencil is written down.
+* Lemma 4.1: M_x = <phi, phi>_{L2}, A_x = <D grad phi, grad phi>_{L2} + c M_x
+  for the reaction-diffusion form of Sec. 4 (a constant symmetric positive
+  definite 2 x 2 matrix D and a constant c >= 0; D = Id, c = 0 is the heat
+  equation of Sec. 5).  Both are assembled here element by element from the P1
+  element matrices; no stencil is written down.
 * Sec. 3.1 / Thm. 3.1 / Sec. 5.1: K_x ~ A_x^-1 and K_j ~ (alpha A_x + 2^j M_x)^-1
   are "2 V-cycles with 3 Gauss-Seidel smoothing steps per grid".  The paper does
   not define the smoother ordering or the coarse grid.  Reading used here:
@@ -82,8 +84,8 @@ class Mesh:
         return self.node_i * self.h, self.node_j * self.h
 
 
-def _assemble(mesh: Mesh, kind: str) -> sp.csr_matrix:
-    """Assemble the P1 mass ('M') or stiffness ('A') matrix over the active nodes."""
+def _assemble(mesh: Mesh, kind: str, D=None) -> sp.csr_matrix:
+    """Assemble the P1 mass ('M') or stiffness ('A', <D grad, grad>) matrix over the active nodes."""
     P = mesh.tri.astype(np.float64) * mesh.h          # (T, 3, 2) vertex coordinates
     e1 = P[:, 1] - P[:, 0]
     e2 = P[:, 2] - P[:, 0]
@@ -100,7 +102,8 @@ def _assemble(mesh: Mesh, kind: str) -> sp.csr_matrix:
             edge = P[:, c] - P[:, b]
             grads[:, a, 0] = edge[:, 1] / det
             grads[:, a, 1] = -edge[:, 0] / det
-        Ke = area[:, None, None] * np.einsum("tad,tbd->tab", grads, grads)
+        Dm = np.eye(2) if D is None else np.asarray(D, dtype=np.float64).reshape(2, 2)
+        Ke = area[:, None, None] * np.einsum("tad,de,tbe->tab", grads, Dm, grads)
     else:
         raise ValueError(kind)
     gid = mesh.dof[mesh.tri[:, :, 1], mesh.tri[:, :, 0]]   # (T, 3), -1 for Dirichlet nodes
@@ -119,9 +122,18 @@ def mass_matrix(mesh: Mesh) -> sp.csr_matrix:
     return _assemble(mesh, "M")
 
 
-def stiffness_matrix(mesh: Mesh) -> sp.csr_matrix:
-    """A_x = <grad phi_q, grad phi_p>_{L2(Omega)} (Lemma 4.1 with D = Id, c = 0)."""
-    return _assemble(mesh, "A")
+def stiffness_matrix(mesh: Mesh, D=None) -> sp.csr_matrix:
+    """<D grad phi_q, grad phi_p>_{L2(Omega)} (D = Id when None)."""
+    return _assemble(mesh, "A", D)
+
+
+def operator_matrix(mesh: Mesh, D=None, c: float = 0.0) -> sp.csr_matrix:
+    """A_x of Lemma 4.1 for the reaction-diffusion form of Sec. 4:
+    <D grad phi_q, grad phi_p> + c <phi_q, phi_p>."""
+    A = stiffness_matrix(mesh, D)
+    if c != 0.0:
+        A = (A + float(c) * mass_matrix(mesh)).tocsr()
+    return A
 
 
 def prolongation(coarse: Mesh, fine: Mesh) -> sp.csr_matrix:
@@ -155,7 +167,8 @@ def coarsest_level(domain: int) -> int:
 
 
 class Multigrid:
-    """Symmetric multigrid for C = a*A_x + s*M_x on the hierarchy coarsest..level.
+    """Symmetric multigrid for C = a*A_x + s*M_x on the hierarchy coarsest..level,
+    A_x = <D grad, grad> + c M_x rediscretised on every level.
 
     `apply(B)` returns X with each column X[:, m] = K B[:, m], where K is
     `n_cycles` V-cycles started from zero (Sec. 5.1: 2 V-cycles, 3 Gauss-Seidel
@@ -163,7 +176,7 @@ class Multigrid:
     """
 
     def __init__(self, level: int, domain: int, a: float, s: float,
-                 n_cycles: int = 2, n_pre: int = 3, n_post: int = 3):
+                 n_cycles: int = 2, n_pre: int = 3, n_post: int = 3, D=None, c: float = 0.0):
         self.level = level
         self.domain = domain
         self.a, self.s = float(a), float(s)
@@ -177,7 +190,7 @@ class Multigrid:
         self.colour = {}
         self.P = {}
         for k, mesh in self.meshes.items():
-            C = (self.a * stiffness_matrix(mesh) + self.s * mass_matrix(mesh)).tocsr()
+            C = (self.a * operator_matrix(mesh, D, c) + self.s * mass_matrix(mesh)).tocsr()
             self.C[k] = C
             self.diag[k] = C.diagonal()
             self.colour[k] = (mesh.node_i + mesh.node_j) % 3
@@ -220,10 +233,10 @@ class Multigrid:
 class DirectInverse:
     """K = C^-1 exactly (sparse LU), for C = a*A_x + s*M_x (the 'direct inverses' of Sec. 5.1)."""
 
-    def __init__(self, level: int, domain: int, a: float, s: float):
+    def __init__(self, level: int, domain: int, a: float, s: float, D=None, c: float = 0.0):
         import scipy.sparse.linalg as spla
         mesh = Mesh(level, domain)
-        C = (a * stiffness_matrix(mesh) + s * mass_matrix(mesh)).tocsc()
+        C = (a * operator_matrix(mesh, D, c) + s * mass_matrix(mesh)).tocsc()
         self._lu = spla.splu(C)
 
     def apply(self, B):

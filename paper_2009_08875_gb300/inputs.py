@@ -38,17 +38,22 @@ def time_nodes(J: int):
     return np.arange(2 ** J + 1) / 2.0 ** J
 
 
-def manufactured(K: int, J: int, domain: int = SQUARE):
+def manufactured(K: int, J: int, domain: int = SQUARE, D=None, c: float = 0.0):
     """u = (1 + t^2) sin(k pi x) sin(k pi y), k = 1 on the square, 2 on the L-shape.
 
-    Returns (g_nodal, u0_nodal, u_nodal) with g = u_t - Laplace(u) sampled at the nodes.
+    Returns (g_nodal, u0_nodal, u_nodal) with g = u_t - div(D grad u) + c u sampled at the
+    nodes (D = Id, c = 0: the heat equation).
     """
     x, y = node_coords(K, domain)
     t = time_nodes(J)
     k = 1.0 if domain == SQUARE else 2.0
+    d11, d12, d22 = (1.0, 0.0, 1.0) if D is None else (D[0][0], D[0][1], D[1][1])
     phi = np.sin(k * np.pi * x) * np.sin(k * np.pi * y)
-    u = (1.0 + t[:, None] ** 2) * phi[None, :]
-    g = (2.0 * t[:, None] + 2.0 * (k * np.pi) ** 2 * (1.0 + t[:, None] ** 2)) * phi[None, :]
+    cross = np.cos(k * np.pi * x) * np.cos(k * np.pi * y)
+    tt = (1.0 + t[:, None] ** 2)
+    u = tt * phi[None, :]
+    g = (2.0 * t[:, None] + ((d11 + d22) * (k * np.pi) ** 2 + c) * tt) * phi[None, :] \
+        - 2.0 * d12 * (k * np.pi) ** 2 * tt * cross[None, :]
     return g, phi.copy(), u
 
 
