@@ -83,10 +83,18 @@ typedef struct {
   int use_graphs;   /* 1: capture each PCG iteration body once as a CUDA graph and replay it
                        (only on a stream other than the legacy/per-thread default streams
                        and outside st_profile_begin/end); 0: plain launches               */
+  double diffusion[3]; /* D = [[d11, d12], [d12, d22]] as (d11, d12, d22) and             */
+  double reaction;     /* c of the reaction-diffusion form of Sec. 4,
+                          a(eta, zeta) = <D grad eta, grad zeta> + c <eta, zeta>, which
+                          defines A_x (Lemma 4.1) in S, f and every K.  D must be symmetric
+                          positive definite and c >= 0 (else ST_ERR_ARG); D = Id, c = 0 is
+                          the heat equation.  st_apply_Kx_static always uses the heat
+                          equation's A_x.                                                 */
 } st_config;
 
 /* Fills *cfg with the paper's settings (alpha 0.3, 2 V-cycles, 3+3 sweeps, Sec. 5.1),
- * tol 1e-10 relative, maxit 200, FP64; inner_tol 1e-5, inner_maxit 60, use_graphs 1. */
+ * tol 1e-10 relative, maxit 200, FP64; inner_tol 1e-5, inner_maxit 60, use_graphs 1;
+ * D = Id, c = 0 (the heat equation of Sec. 5). */
 void st_default_config(st_config* cfg);
 
 /* Creates a handle for `domain` (0 unit square, 1 L-shape) at space level K (1..12; 2..12 for
@@ -269,15 +277,20 @@ st_status st_set_smoother(st_handle h, int kind);
 /* Measurement hooks (not part of the method).  Between st_profile_begin and st_profile_end the
  * handle counts every kernel it launches and brackets each finest-level Gauss-Seidel sweep
  * launch (the dominant kernel) with a pair of CUDA events on the bound stream, adding up the
- * launch's algorithmic work: per point and sweep 5 FP64 operations for K_x (7 with the mass
- * couplings of K_l), and 24 bytes (read x and b, write x; 16 on a sweep that starts from
- * x = 0).  st_profile_end synchronises the stream and reports the sums. */
+ * launch's algorithmic work: per point and sweep 4 FP64 operations for K_x (3 adds, 1 fma; 6
+ * with the mass couplings of K_l: 1 more add and fma), and 3 values moved (read x and b, write
+ * x; 2 on a sweep that starts from x = 0) of the element type.  st_profile_end synchronises
+ * the stream and reports the sums, in total and for the sweeps with mass couplings alone. */
 typedef struct {
   int64_t launches;        /* kernels launched by the handle                        */
   int64_t sweep_launches;  /* finest-level Gauss-Seidel sweep launches timed        */
   double sweep_ms;         /* their summed CUDA-event durations                     */
   double sweep_fp64_ops;   /* their algorithmic FP64 operations (add, mul, fma = 1) */
   double sweep_bytes;      /* their algorithmic DRAM bytes                          */
+  int64_t diag_launches;   /* the subset with mass couplings (K_l): launches        */
+  double diag_ms;          /*   CUDA-event time                                     */
+  double diag_fp64_ops;    /*   FP64 operations                                     */
+  double diag_bytes;       /*   DRAM bytes                                          */
 } st_profile;
 
 st_status st_profile_begin(st_handle h);

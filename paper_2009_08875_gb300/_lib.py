@@ -18,7 +18,8 @@ class StConfig(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("n_vcycles", ctypes.c_int), ("n_pre", ctypes.c_int),
                 ("n_post", ctypes.c_int), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("inner_maxit", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("inner_maxit", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("diffusion", ctypes.c_double * 3), ("reaction", ctypes.c_double)]
 
 
 class StSolveInfo(ctypes.Structure):
@@ -30,7 +31,9 @@ ST_FP64, ST_MIXED_FP32, ST_MIXED_PRECOND = 0, 1, 2
 
 class StProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("sweep_launches", ctypes.c_int64), ("sweep_ms", ctypes.c_double),
-                ("sweep_fp64_ops", ctypes.c_double), ("sweep_bytes", ctypes.c_double)]
+                ("sweep_fp64_ops", ctypes.c_double), ("sweep_bytes", ctypes.c_double),
+                ("diag_launches", ctypes.c_int64), ("diag_ms", ctypes.c_double),
+                ("diag_fp64_ops", ctypes.c_double), ("diag_bytes", ctypes.c_double)]
 
 
 class STError(RuntimeError):

@@ -32,6 +32,9 @@ bool prof_start(const st_handle_s* h) {
   if (h->prof_n + 2 > h->prof_cap) {
     // grow the event pool (outside steady state: st_profile_begin preallocates)
     int cap = h->prof_cap ? 2 * h->prof_cap : 4096;
+    unsigned char* cat = static_cast<unsigned char*>(std::realloc(h->prof_cat, cap));
+    if (!cat) return false;
+    h->prof_cat = cat;
     cudaEvent_t* ev = static_cast<cudaEvent_t*>(std::realloc(h->prof_ev, sizeof(cudaEvent_t) * cap));
     if (!ev) return false;
     for (int i = h->prof_cap; i < cap; ++i)
@@ -48,11 +51,12 @@ bool prof_start(const st_handle_s* h) {
   return true;
 }
 
-void prof_stop(const st_handle_s* h, double ops, double bytes) {
+void prof_stop(const st_handle_s* h, int cat, double ops, double bytes) {
   cudaEventRecord(h->prof_ev[h->prof_n + 1], h->stream);
+  h->prof_cat[h->prof_n] = (unsigned char)cat;
   h->prof_n += 2;
-  h->prof_ops += ops;
-  h->prof_bytes += bytes;
+  h->prof_ops[cat] += ops;
+  h->prof_bytes[cat] += bytes;
 }
 
 }  // namespace st
@@ -85,6 +89,13 @@ static inline st_status check_cuda_(cudaError_t e, const char* where) {
   } while (0)
 
 namespace {
+
+// D = [[d11, d12], [d12, d22]] symmetric positive definite, c >= 0, all finite (Sec. 4)
+bool check_phys(const st_config& c) {
+  const double d11 = c.diffusion[0], d12 = c.diffusion[1], d22 = c.diffusion[2], r = c.reaction;
+  return std::isfinite(d11) && std::isfinite(d12) && std::isfinite(d22) && std::isfinite(r) && d11 > 0.0 &&
+         d22 > 0.0 && d11 * d22 - d12 * d12 > 0.0 && r >= 0.0;
+}
 
 void free_all(st_handle_s* h) {
   double** bufs[] = {&h->U, &h->Y, &h->X, &h->Xalt, &h->Bs,   &h->Z, &h->V1, &h->V2,       &h->r,
@@ -126,7 +137,9 @@ void free_all(st_handle_s* h) {
   }
   for (int i = 0; i < h->prof_cap; ++i) cudaEventDestroy(h->prof_ev[i]);
   std::free(h->prof_ev);
+  std::free(h->prof_cat);
   h->prof_ev = nullptr;
+  h->prof_cat = nullptr;
   h->prof_cap = h->prof_n = 0;
 }
 
@@ -607,6 +620,10 @@ void st_default_config(st_config* cfg) {
   cfg->inner_tol = 1e-5;
   cfg->inner_maxit = 60;
   cfg->use_graphs = 1;
+  cfg->diffusion[0] = 1.0;
+  cfg->diffusion[1] = 0.0;
+  cfg->diffusion[2] = 1.0;
+  cfg->reaction = 0.0;
 }
 
 const char* st_last_error(void) { return g_last_error.c_str(); }
@@ -635,6 +652,7 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
              "st_setup: unsupported precision");
   ST_REQUIRE(c.inner_tol > 0.0 && c.inner_tol < 1.0 && c.inner_maxit >= 1,
              "st_setup: inner_tol must be in (0, 1) and inner_maxit >= 1");
+  ST_REQUIRE(check_phys(c), "st_setup: D must be symmetric positive definite and c >= 0 (finite)");
 
   st_handle_s* h = new (std::nothrow) st_handle_s();
   if (!h) {
@@ -650,6 +668,8 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   h->Nx = (int64_t)h->n * h->n;
   h->Nt = nt;
   h->cfg = c;
+  h->phys = Phys{c.diffusion[0], c.diffusion[1], c.diffusion[2], c.reaction};
+  h->diag0 = c.diffusion[1] != 0.0 || c.reaction != 0.0;
   h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
@@ -727,8 +747,8 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   }
   if (s == ST_OK) {
     e = mg_set_attributes();
-    if (e == cudaSuccess) e = launch_make_coef(h->coef, h->K, h->J, c.alpha, h->stream);
-    if (e == cudaSuccess) e = launch_make_coef32(h->coef32, h->K, h->J, c.alpha, h->stream);
+    if (e == cudaSuccess) e = launch_make_coef(h->coef, h->K, h->J, c.alpha, h->phys, h->stream);
+    if (e == cudaSuccess) e = launch_make_coef32(h->coef32, h->K, h->J, c.alpha, h->phys, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->scal, 0, sizeof(double) * SC_COUNT * batch, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = cuda_fail("st_setup", e);
@@ -899,7 +919,7 @@ st_status st_profile_begin(st_handle h) {
   ST_CHECK(check_handle(h));
   h->launches = 0;
   h->prof_n = 0;
-  h->prof_ops = h->prof_bytes = 0.0;
+  h->prof_ops[0] = h->prof_ops[1] = h->prof_bytes[0] = h->prof_bytes[1] = 0.0;
   h->prof_on = true;
   // preallocate events so that recording inside the timed region never creates them
   if (h->prof_cap < 16384 && prof_start(h)) {
@@ -918,17 +938,23 @@ st_status st_profile_end(st_handle h, st_profile* out) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(out != nullptr, "st_profile_end: null output");
   ST_CHECK_CUDA(cudaStreamSynchronize(h->stream), "st_profile_end");
-  double ms = 0.0;
+  double ms[2] = {0.0, 0.0};
+  int64_t n[2] = {0, 0};
   for (int i = 0; i + 1 < h->prof_n; i += 2) {
     float t = 0.f;
     ST_CHECK_CUDA(cudaEventElapsedTime(&t, h->prof_ev[i], h->prof_ev[i + 1]), "cudaEventElapsedTime");
-    ms += t;
+    ms[h->prof_cat[i]] += t;
+    n[h->prof_cat[i]] += 1;
   }
   out->launches = h->launches;
-  out->sweep_launches = h->prof_n / 2;
-  out->sweep_ms = ms;
-  out->sweep_fp64_ops = h->prof_ops;
-  out->sweep_bytes = h->prof_bytes;
+  out->sweep_launches = n[0] + n[1];
+  out->sweep_ms = ms[0] + ms[1];
+  out->sweep_fp64_ops = h->prof_ops[0] + h->prof_ops[1];
+  out->sweep_bytes = h->prof_bytes[0] + h->prof_bytes[1];
+  out->diag_launches = n[1];
+  out->diag_ms = ms[1];
+  out->diag_fp64_ops = h->prof_ops[1];
+  out->diag_bytes = h->prof_bytes[1];
   h->prof_on = false;
   h->prof_n = 0;
   return ST_OK;

@@ -14,25 +14,30 @@ namespace st {
 namespace {
 
 // ---------------------------------------------------------------------------------------
-// coefficient table: class 0 -> (a, s) = (1, 0); class 1 + l -> (alpha, 2^l), l = 0..J
+// coefficient table: class 0 -> (a, s) = (1, 0); class 1 + l -> (alpha, 2^l), l = 0..J, of
+// C = a A_x + s M_x with A_x = <D grad, grad> + c M_x (Sec. 4)
 // ---------------------------------------------------------------------------------------
 template <typename T>
-__global__ void k_make_coef(Coef<T>* coef, int K, int J, double alpha) {
+__global__ void k_make_coef(Coef<T>* coef, int K, int J, double alpha, Phys ph) {
   int nclass = J + 2;
   for (int e = threadIdx.x; e < nclass * (K + 1); e += blockDim.x) {
     int cls = e / (K + 1), k = e % (K + 1);
     double a = cls == 0 ? 1.0 : alpha;
     double s = cls == 0 ? 0.0 : ldexp(1.0, cls - 1);
-    double h2 = ldexp(1.0, -2 * k);
-    const double cc = 4.0 * a + s * h2 / 2.0;
-    const double ax = -a + s * h2 / 12.0, dg = s * h2 / 12.0;
-    const double cc_coarse = 4.0 * a + s * (h2 * 4.0) / 2.0;  // level k - 1
+    const double m = (a * ph.c + s) * ldexp(1.0, -2 * k) / 12.0;            // level k
+    const double mc = (a * ph.c + s) * ldexp(1.0, -2 * (k - 1)) / 12.0;      // level k - 1
+    const double stiff_c = a * 2.0 * (ph.d11 + ph.d22 - ph.d12);
+    const double cc = stiff_c + 6.0 * m;
+    const double ax = a * (ph.d12 - ph.d11) + m, ay = a * (ph.d12 - ph.d22) + m, dg = -a * ph.d12 + m;
+    const double cc_coarse = stiff_c + 6.0 * mc;
     Coef<T> c;
     c.c = (T)cc;
     c.ax = (T)ax;
+    c.ay = (T)ay;
     c.dg = (T)dg;
     c.inv_c = (T)(1.0 / cc);
     c.axs = (T)(ax / cc);
+    c.ays = (T)(ay / cc);
     c.dgs = (T)(dg / cc);
     c.rho = (T)(cc / cc_coarse);
     c.pad = T(0);
@@ -98,7 +103,7 @@ __global__ void k_coarse_dense3(T* __restrict__ x, const T* __restrict__ b, int 
     for (int t = 0; t < 6; ++t) {
       const int jx = ix + nb[t][0], jy = iy + nb[t][1];
       if (jx < 0 || jx > 2 || jy < 0 || jy > 2 || outside_domain(jx, jy, 3, lshape)) continue;
-      A[p][jy * 3 + jx] = t < 4 ? cf.ax : cf.dg;
+      A[p][jy * 3 + jx] = t < 2 ? cf.ax : (t < 4 ? cf.ay : cf.dg);
     }
   }
   for (int c = 0; c < 9; ++c) {
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
     // stored, so R independent FP64 chains are in flight (points of one colour never couple)
     constexpr int R = 2;
     for (int ry0 = ry_lo + warp; ry0 < ry_hi; ry0 += R * nwarp) {
-      T sa[R], sd[R], bv[R];
+      T sx[R], sy[R], sd[R], bv[R];
       int at[R];
 #pragma unroll
       for (int q = 0; q < R; ++q) {
@@ -183,14 +188,16 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
         const bool ok = ry < ry_hi && rx >= rx_lo && rx < rx_hi && !outside_domain(gx0 + rx, gy, n, lshape);
         const int i = ok ? ry * kWR + rx : kWR + 1;  // a harmless interior address when idle
         at[q] = ok ? i : -1;
-        sa[q] = (xs[i - 1] + xs[i + 1]) + (xs[i - kWR] + xs[i + kWR]);
+        sx[q] = xs[i - 1] + xs[i + 1];
+        sy[q] = xs[i - kWR] + xs[i + kWR];
         sd[q] = DIAG ? (xs[i + kWR + 1] + xs[i - kWR - 1]) : T(0);
         bv[q] = bs[i];
       }
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        // scaled system: x = b' - (ax/c) s4 - (dg/c) s2 with b' = b / c
-        T v = bv[q] - cf.axs * sa[q];
+        // scaled system: x = b' - (ax/c) sx - (ay/c) sy - (dg/c) sd with b' = b / c
+        T v = bv[q] - cf.axs * sx[q];
+        v -= cf.ays * sy[q];
         if (DIAG) v -= cf.dgs * sd[q];
         if (at[q] >= 0) xs[at[q]] = v;
       }
@@ -282,15 +289,18 @@ __global__ void __launch_bounds__(128) k_gs_wave(T* __restrict__ x_out, const T*
       dn_n0 = __shfl_down_sync(0xffffffffu, xn[0], 1);
     }
     if (m == 0) {
-      T v = bc[0] - cf.axs * ((up_c2 + xcr[1]) + (xs[0] + xn[0]));
+      T v = bc[0] - cf.axs * (up_c2 + xcr[1]);
+      v -= cf.ays * (xs[0] + xn[0]);
       if (DIAG) v -= cf.dgs * (xn[1] + up_s2);
       if (ok) xcr[0] = v;
     } else if (m == 1) {
-      T v = bc[1] - cf.axs * ((xcr[0] + xcr[2]) + (xs[1] + xn[1]));
+      T v = bc[1] - cf.axs * (xcr[0] + xcr[2]);
+      v -= cf.ays * (xs[1] + xn[1]);
       if (DIAG) v -= cf.dgs * (xn[2] + xs[0]);
       if (ok) xcr[1] = v;
     } else {
-      T v = bc[2] - cf.axs * ((xcr[1] + dn_c0) + (xs[2] + xn[2]));
+      T v = bc[2] - cf.axs * (xcr[1] + dn_c0);
+      v -= cf.ays * (xs[2] + xn[2]);
       if (DIAG) v -= cf.dgs * (dn_n0 + xs[1]);
       if (ok) xcr[2] = v;
     }
@@ -395,9 +405,9 @@ __global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, c
     T r = T(0);
     if (gx < n && gy < n && !outside_domain(gx, gy, n, lshape)) {
       const int i = (ry + 1) * kRXX + (rx + 1);
-      // scaled residual r' = D^-1 (b - C x) = b' - x - (ax/c) s4 - (dg/c) s2
-      T s4 = (xs[i - 1] + xs[i + 1]) + (xs[i - kRXX] + xs[i + kRXX]);
-      T v = bsl[(int64_t)gy * n + gx] - cf.axs * s4;
+      // scaled residual r' = D^-1 (b - C x) = b' - x - (ax/c) sx - (ay/c) sy - (dg/c) sd
+      T v = bsl[(int64_t)gy * n + gx] - cf.axs * (xs[i - 1] + xs[i + 1]);
+      v -= cf.ays * (xs[i - kRXX] + xs[i + kRXX]);
       if (DIAG) v -= cf.dgs * (xs[i + kRXX + 1] + xs[i - kRXX - 1]);
       r = v - xs[i];
     }
@@ -486,7 +496,7 @@ cudaError_t gs_launch(const st_handle_s* h, int k, int nslices, int cls, T* x_ou
     // per point and sweep: 3 adds + 1 fma (+ 1 add + 1 fma with diagonal couplings);
     // bytes: read x and b, write x (x is not read when the launch starts from x = 0)
     const double pts = (double)n * n * nslices;
-    prof_stop(h, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(T) * (zero_init ? 2.0 : 3.0));
+    prof_stop(h, DIAG ? 1 : 0, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(T) * (zero_init ? 2.0 : 3.0));
   }
   return cudaGetLastError();
 }
@@ -509,7 +519,7 @@ cudaError_t wave_launch(const st_handle_s* h, int k, int nslices, int cls, T* x_
   count_launch(h);
   if (prof) {
     const double pts = (double)n * n * nslices;
-    prof_stop(h, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(T) * (zero_init ? 2.0 : 3.0));
+    prof_stop(h, DIAG ? 1 : 0, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(T) * (zero_init ? 2.0 : 3.0));
   }
   return cudaGetLastError();
 }
@@ -604,13 +614,13 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, T* const x
 
 }  // namespace
 
-cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, cudaStream_t s) {
-  k_make_coef<double><<<1, 256, 0, s>>>(coef, K, J, alpha);
+cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, Phys ph, cudaStream_t s) {
+  k_make_coef<double><<<1, 256, 0, s>>>(coef, K, J, alpha, ph);
   return cudaGetLastError();
 }
 
-cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, cudaStream_t s) {
-  k_make_coef<float><<<1, 256, 0, s>>>(coef, K, J, alpha);
+cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, Phys ph, cudaStream_t s) {
+  k_make_coef<float><<<1, 256, 0, s>>>(coef, K, J, alpha, ph);
   return cudaGetLastError();
 }
 
@@ -639,8 +649,9 @@ cudaError_t mg_set_attributes() {
 
 template <typename T>
 cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x) {
-  // class 0 (K_x: s = 0) has no diagonal couplings; the K_l classes do
-  const bool diag = coef_class != 0;
+  // class 0 (K_x: s = 0) has no diagonal couplings unless D has d12 != 0 or c != 0; the K_l
+  // classes always do
+  const bool diag = coef_class != 0 || h->diag0;
   T* const xb[2] = {x, reinterpret_cast<T*>(h->Xalt)};
   int cur = 0;
   T* bs = reinterpret_cast<T*>(h->Bs);

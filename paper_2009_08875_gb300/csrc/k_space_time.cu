@@ -10,7 +10,8 @@ namespace {
 // ---------------------------------------------------------------------------------------
 // spatial stencils on one slice (interior index p = iy n + ix; outside the grid = 0)
 //   M_x: h^2/12 [6 at p; 1 at (+-1,0), (0,+-1), (1,1), (-1,-1)]
-//   A_x: [4 at p; -1 at (+-1,0), (0,+-1)]
+//   A_x: the 7-point stencil of <D grad, grad> + c M_x (Stencil7; the heat equation's
+//        [4; -1 at (+-1,0), (0,+-1)] when D = Id, c = 0)
 // ---------------------------------------------------------------------------------------
 template <typename T>
 struct Nbr {
@@ -36,8 +37,8 @@ __device__ __forceinline__ T mass_of(const Nbr<T>& v, T mh) {
 }
 
 template <typename T>
-__device__ __forceinline__ T stiff_of(const Nbr<T>& v) {
-  return T(4) * v.c - ((v.w + v.e) + (v.s + v.nn));
+__device__ __forceinline__ T stiff_of(const Nbr<T>& v, const Stencil7<T>& a) {
+  return a.c0 * v.c + a.cx * (v.w + v.e) + a.cy * (v.s + v.nn) + a.cd * (v.ne + v.sw);
 }
 
 // tridiagonal time matrices on the uniform P1 mesh (h = 2^-J), row i of N_t:
@@ -88,8 +89,8 @@ __device__ __forceinline__ T tri_dot(const Tri<T>& t, T a, T b, T c) {
 // rows i-1, i, i+1 in registers (the chunk edges recompute one halo row).
 template <typename T>
 __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __restrict__ Y1, T* __restrict__ Y2,
-                                                 int n, int Nt, int chunk, T mh, TimeConsts<T> tk, int mode,
-                                                 int lshape) {
+                                                 int n, int Nt, int chunk, T mh, Stencil7<T> sa,
+                                                 TimeConsts<T> tk, int mode, int lshape) {
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
@@ -112,18 +113,18 @@ __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __r
   if (i0 > 0) {
     Nbr<T> v = load_nbr(U + (int64_t)(i0 - 1) * N, p, ix, iy, n);
     um_m = mass_of(v, mh);
-    ua_m = stiff_of(v);
+    ua_m = stiff_of(v, sa);
   }
   {
     Nbr<T> v = load_nbr(U + (int64_t)i0 * N, p, ix, iy, n);
     um_c = mass_of(v, mh);
-    ua_c = stiff_of(v);
+    ua_c = stiff_of(v, sa);
   }
   for (int i = i0; i < i1; ++i) {
     if (i + 1 < Nt) {
       Nbr<T> v = load_nbr(U + (int64_t)(i + 1) * N, p, ix, iy, n);
       um_p = mass_of(v, mh);
-      ua_p = mode == 0 ? stiff_of(v) : T(0);
+      ua_p = mode == 0 ? stiff_of(v, sa) : T(0);
     } else {
       um_p = T(0);
       ua_p = T(0);
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __r
 template <typename T>
 __global__ void __launch_bounds__(256) k_epilogue(const T* __restrict__ X1, const T* __restrict__ X2,
                                                   const T* __restrict__ row0, int64_t row0_stride, T* __restrict__ Z,
-                                                  int n, int Nt, T mh, int lshape) {
+                                                  int n, int Nt, T mh, Stencil7<T> sa, int lshape) {
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
@@ -165,19 +166,20 @@ __global__ void __launch_bounds__(256) k_epilogue(const T* __restrict__ X1, cons
     Z[off + p] = T(0);
     return;
   }
-  T z = mass_of(load_nbr(X1 + off, p, ix, iy, n), mh) + stiff_of(load_nbr(X2 + off, p, ix, iy, n));
+  T z = mass_of(load_nbr(X1 + off, p, ix, iy, n), mh) + stiff_of(load_nbr(X2 + off, p, ix, iy, n), sa);
   if (i == 0 && row0 != nullptr) z += mass_of(load_nbr(row0, p, ix, iy, n), mh);
   Z[off + p] = z;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_apply_A(const T* __restrict__ X, T* __restrict__ Y, int n, int lshape) {
+__global__ void __launch_bounds__(256) k_apply_A(const T* __restrict__ X, T* __restrict__ Y, int n, Stencil7<T> sa,
+                                                 int lshape) {
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   const int iy = p / n, ix = p - iy * n;
   const int64_t off = (int64_t)blockIdx.y * N;
-  Y[off + p] = outside_domain(ix, iy, n, lshape) ? T(0) : stiff_of(load_nbr(X + off, p, ix, iy, n));
+  Y[off + p] = outside_domain(ix, iy, n, lshape) ? T(0) : stiff_of(load_nbr(X + off, p, ix, iy, n), sa);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -239,6 +241,13 @@ __global__ void k_wanal(const T* __restrict__ Xf, T* C, T* D, int64_t Nx, int j,
   }
 }
 
+// A_x on the finest level of the handle, in element type T
+template <typename T>
+Stencil7<T> fine_A(const st_handle_s* h) {
+  const Stencil7<double> a = operator_stencil(h->phys, 1.0, 0.0, ldexp(1.0, -h->K));
+  return Stencil7<T>{(T)a.c0, (T)a.cx, (T)a.cy, (T)a.cd};
+}
+
 template <typename T>
 TimeConsts<T> time_consts(int J) {
   const double h = ldexp(1.0, -J);
@@ -255,7 +264,7 @@ cudaError_t launch_timemix(const st_handle_s* h, int nb, int mode, const T* U, T
   dim3 grid((N + 255) / 256, (int)((h->Nt + chunk - 1) / chunk), nb);
   const double hx = ldexp(1.0, -h->K);
   k_timemix<T><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, chunk,
-                                            (T)(hx * hx / 12.0),
+                                            (T)(hx * hx / 12.0), fine_A<T>(h),
                                             time_consts<T>(h->J), mode, h->domain);
   count_launch(h);
   return cudaGetLastError();
@@ -268,7 +277,7 @@ cudaError_t launch_epilogue(const st_handle_s* h, int nb, const T* X, const T* r
   dim3 grid((N + 255) / 256, (int)h->Nt, nb);
   const double hx = ldexp(1.0, -h->K);
   k_epilogue<T><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt,
-                                             (T)(hx * hx / 12.0), h->domain);
+                                             (T)(hx * hx / 12.0), fine_A<T>(h), h->domain);
   count_launch(h);
   return cudaGetLastError();
 }
@@ -278,7 +287,7 @@ cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y) {
   const int n = h->n;
   const int N = n * n;
   dim3 grid((N + 255) / 256, nrows);
-  k_apply_A<T><<<grid, 256, 0, h->stream>>>(X, Y, n, h->domain);
+  k_apply_A<T><<<grid, 256, 0, h->stream>>>(X, Y, n, fine_A<T>(h), h->domain);
   count_launch(h);
   return cudaGetLastError();
 }

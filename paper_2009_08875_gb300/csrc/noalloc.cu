@@ -101,6 +101,7 @@ extern "C" st_status st_apply_Kx_static(int space_level, int nslices, const doub
   h.Nx = (int64_t)h.n * h.n;
   h.Nt = 3;
   st_default_config(&h.cfg);
+  h.phys = Phys{1.0, 0.0, 1.0, 0.0};  // the heat equation's A_x
   h.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   h.mg.K = space_level;
   h.mg.kmin = 1;
@@ -121,7 +122,7 @@ extern "C" st_status st_apply_Kx_static(int space_level, int nslices, const doub
   // Nothing in the scratch has to start at zero: every call rewrites the coefficient table, and
   // every multigrid buffer is written before it is read within the call (each coarse level, and
   // the finest level in the first cycle, start from x = 0 without reading the iterate buffer).
-  e = launch_make_coef(h.coef, h.K, h.J, h.cfg.alpha, h.stream);
+  e = launch_make_coef(h.coef, h.K, h.J, h.cfg.alpha, h.phys, h.stream);
   if (e != cudaSuccess) return cuda_fail("st_apply_Kx_static: coefficient table", e);
   e = mg_apply(&h, nslices, 0, b, x);
   if (e != cudaSuccess) return cuda_fail("st_apply_Kx_static: multigrid", e);

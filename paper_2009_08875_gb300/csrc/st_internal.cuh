@@ -12,9 +12,10 @@ namespace st {
 
 // ---------------------------------------------------------------------------------------
 // Multigrid operator coefficients.  On mesh level k (h = 2^-k) the P1 matrix
-// C = a A_x + s M_x has the 7-point stencil
-//   centre 4a + s h^2/2,  axis neighbours -a + s h^2/12,  (1,1)/(-1,-1) diagonal s h^2/12
-// (A_x: 5-point Laplacian; M_x: h^2/12 [6; 1 x 6] on the (i,j)-(i+1,j+1) triangulation).
+// C = a A_x + s M_x has a 7-point stencil (x neighbours, y neighbours, (1,1)/(-1,-1)
+// diagonal neighbours); for the heat equation (A_x: 5-point Laplacian; M_x: h^2/12 [6; 1 x 6]
+// on the (i,j)-(i+1,j+1) triangulation) it is centre 4a + s h^2/2, axis neighbours
+// -a + s h^2/12, diagonal s h^2/12.  Phys below gives the general reaction-diffusion one.
 // One entry per (coefficient class, level).  Class 0 is K_x (a = 1, s = 0); class 1 + l is
 // K_l (a = alpha, s = 2^l), l = 0..J.
 // The multigrid works with the Jacobi-scaled system D^-1 C x = D^-1 b (D = the centre
@@ -25,13 +26,37 @@ template <typename T>
 struct Coef {
   T inv_c;  // 1 / centre
   T c;      // centre
-  T ax;     // axis-neighbour coefficient
-  T dg;     // diagonal-neighbour coefficient
+  T ax;     // coefficient of the x neighbours (+-1, 0)
+  T ay;     // coefficient of the y neighbours (0, +-1)
+  T dg;     // coefficient of the (1,1) / (-1,-1) diagonal neighbours
   T axs;    // ax / c
+  T ays;    // ay / c
   T dgs;    // dg / c
   T rho;    // c of this level / c of the next coarser level (rescales restricted residuals)
   T pad;
 };
+
+// Constant coefficients of the reaction-diffusion form of Sec. 4, a(eta, zeta) =
+// <D grad eta, grad zeta> + c <eta, zeta> with D = [[d11, d12], [d12, d22]] (D = Id, c = 0: the
+// heat equation).  On the mesh (squares cut along their (1,1) diagonal) the P1 stiffness of D is
+// the 7-point stencil centre 2(d11 + d22 - d12), x neighbours d12 - d11, y neighbours d12 - d22,
+// (1,1)/(-1,-1) neighbours -d12; c adds c times the mass stencil h^2/12 [6; 1 at the six].
+struct Phys {
+  double d11, d12, d22, c;
+};
+
+// A 7-point stencil [centre; x, y, (1,1)/(-1,-1) neighbours] in element type T.
+template <typename T>
+struct Stencil7 {
+  T c0, cx, cy, cd;
+};
+
+// The stencil of a A_x + s M_x on mesh width h (A_x = <D grad, grad> + c M_x).
+inline Stencil7<double> operator_stencil(const Phys& ph, double a, double s, double h) {
+  const double m = (a * ph.c + s) * h * h / 12.0;
+  return Stencil7<double>{a * 2.0 * (ph.d11 + ph.d22 - ph.d12) + 6.0 * m, a * (ph.d12 - ph.d11) + m,
+                          a * (ph.d12 - ph.d22) + m, -a * ph.d12 + m};
+}
 
 // Level |lambda| of in-place wavelet row i (rows 0 and 2^J: level 0; else J - ctz(i)).
 __host__ __device__ inline int wavelet_row_level(int i, int J) {
@@ -69,6 +94,8 @@ struct st_handle_s {
   int64_t Nt, Nx;
   int n;  // 2^K - 1
   st_config cfg;
+  st::Phys phys;     // D and c of the reaction-diffusion form (from cfg)
+  bool diag0;        // K_x's operator couples the (1,1) diagonal (d12 != 0 or c != 0)
   cudaStream_t stream;
   int device;
 
@@ -125,7 +152,8 @@ struct st_handle_s {
   mutable bool prof_on;
   mutable int prof_cap, prof_n;
   mutable cudaEvent_t* prof_ev;
-  mutable double prof_ops, prof_bytes;
+  mutable unsigned char* prof_cat;  // per event pair: 0 sweep without, 1 with mass couplings
+  mutable double prof_ops[2], prof_bytes[2];
 };
 
 namespace st {
@@ -134,7 +162,7 @@ namespace st {
 inline void count_launch(const st_handle_s* h, int n = 1) { h->launches += n; }
 // event pair around one profiled launch (no-op unless profiling); returns false if out of events
 bool prof_start(const st_handle_s* h);
-void prof_stop(const st_handle_s* h, double ops, double bytes);
+void prof_stop(const st_handle_s* h, int cat, double ops, double bytes);
 
 // error helpers (thread-local message)
 void set_error(const std::string& msg);
@@ -143,8 +171,8 @@ st_status cuda_fail(const char* where, cudaError_t e);
 // ---------------------------------------------------------------------------------------
 // launchers (all enqueue on `s`; return cudaGetLastError())
 // ---------------------------------------------------------------------------------------
-cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, cudaStream_t s);
-cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, cudaStream_t s);
+cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, Phys ph, cudaStream_t s);
+cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, Phys ph, cudaStream_t s);
 
 // The operator launchers below are instantiated for T = double and T = float; the float
 // versions reuse the handle's double workspace (half of each buffer).

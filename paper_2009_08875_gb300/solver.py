@@ -31,7 +31,7 @@ class Solver:
 
     def __init__(self, K, J, domain=0, alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0,
                  maxit=200, precision="fp64", inner_tol=1e-5, inner_maxit=60, batch=1, use_graphs=True,
-                 stream=None):
+                 stream=None, D=None, c=0.0):
         import torch
         lib = _lib.load()
         cfg = _lib.StConfig()
@@ -42,6 +42,7 @@ class Solver:
                          "mixed_precond": _lib.ST_MIXED_PRECOND}[precision]
         cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
         cfg.use_graphs = 1 if use_graphs else 0
+        _set_phys(cfg, D, c)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -166,8 +167,17 @@ class Solver:
         return {f: getattr(out, f) for f, _ in _lib.StProfile._fields_}
 
 
+def _set_phys(cfg, D, c):
+    """D (2 x 2 symmetric, or None for the identity) and c of the reaction-diffusion form."""
+    if D is not None:
+        cfg.diffusion[0], cfg.diffusion[1], cfg.diffusion[2] = float(D[0][0]), float(D[0][1]), float(D[1][1])
+        if float(D[1][0]) != float(D[0][1]):
+            raise ValueError("D must be symmetric")
+    cfg.reaction = float(c)
+
+
 def _config(alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0, maxit=200, precision="fp64",
-            inner_tol=1e-5, inner_maxit=60, use_graphs=True):
+            inner_tol=1e-5, inner_maxit=60, use_graphs=True, D=None, c=0.0):
     lib = _lib.load()
     cfg = _lib.StConfig()
     lib.st_default_config(ctypes.byref(cfg))
@@ -177,6 +187,7 @@ def _config(alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0, ma
                      "mixed_precond": _lib.ST_MIXED_PRECOND}[precision]
     cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
     cfg.use_graphs = 1 if use_graphs else 0
+    _set_phys(cfg, D, c)
     return cfg
 
 

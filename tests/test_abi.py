@@ -45,6 +45,22 @@ def test_default_config_is_the_papers():
     cfg = _lib.StConfig()
     lib.st_default_config(ctypes.byref(cfg))
     assert (cfg.alpha, cfg.n_vcycles, cfg.n_pre, cfg.n_post) == (0.3, 2, 3, 3)
+    # the heat equation: D = Id, c = 0
+    assert tuple(cfg.diffusion) == (1.0, 0.0, 1.0) and cfg.reaction == 0.0
+
+
+@pytest.mark.parametrize("d11,d12,d22,c", [(0.0, 0.0, 1.0, 0.0), (1.0, 1.0, 1.0, 0.0), (1.0, 2.0, 1.0, 0.0),
+                                           (-1.0, 0.0, -1.0, 0.0), (1.0, 0.0, 1.0, -0.5),
+                                           (1.0, 0.0, float("nan"), 0.0)])
+def test_setup_rejects_non_spd_D_or_negative_c_without_gpu(d11, d12, d22, c):
+    lib = lib_or_skip()
+    cfg = _lib.StConfig()
+    lib.st_default_config(ctypes.byref(cfg))
+    cfg.diffusion[0], cfg.diffusion[1], cfg.diffusion[2], cfg.reaction = d11, d12, d22, c
+    h = ctypes.c_void_p()
+    assert lib.st_setup(ctypes.byref(h), 0, 3, 3, ctypes.byref(cfg), None) == _lib.ST_ERR_ARG
+    assert h.value is None
+    assert "positive definite" in lib.st_last_error().decode()
 
 
 @pytest.mark.parametrize("domain,K,J", [(2, 3, 3), (1, 1, 3), (0, 0, 3), (0, 13, 3), (0, 3, 0), (0, 3, 15)])
