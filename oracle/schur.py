@@ -22,6 +22,17 @@ row-wise), i.e. B_x applied to every row followed by B_t across rows.
 * Sec. 3.4, Eq. (3.3): PCG on S_hat w = f_hat with K_X, from w_0 = 0, monitoring
   r^T K_X r.  Stopping: absolute (sqrt(r^T K_X r) <= eps, as in Sec. 5.2) or
   relative to the initial value (this project's default for its workloads).
+* Sec. 4.4 (complexity with nested iteration, after Hackbusch Ch. 5): solve on a
+  hierarchy of meshes refined in space and time together, each solve started from
+  the previous level's solution and stopped at an algebraic error proportional to
+  the discretisation error.  The paper gives no details; readings used here:
+  levels (K - m, J - m) for m = levels-1 .. 0; the data g, u_0 of a coarse level are
+  the fine nodal values at the coarse nodes; the previous solution enters the next
+  level exactly (the coarse wavelet basis is the first 2^(J-1) + 1 functions of the
+  fine one, Eq. 3.1 with zero new details, and the coarse P1 space in x is a subspace
+  of the fine one); level m stops when sqrt(r^T K_X r) <= eps 2^(rate m) (Eq. 3.3,
+  absolute), eps being the finest level's tolerance and 2^rate the expected ratio of
+  discretisation errors between consecutive levels.
 """
 from __future__ import annotations
 
@@ -215,3 +226,47 @@ def solve(prob: Problem, g_nodal, u0_nodal, tol=1e-10, tol_mode="rel", maxit=500
     fhat = prob.rhs_hat(g_nodal, u0_nodal)
     w, info = pcg(prob.apply_Shat, prob.apply_KX, fhat, tol=tol, tol_mode=tol_mode, maxit=maxit)
     return prob.synth(w), w, info
+
+
+# -- nested iteration (Sec. 4.4) ------------------------------------------------------------
+def inject_nodal(fine: Problem, coarse: Problem, V):
+    """Nodal values on the coarse space-time mesh of a function given by its fine nodal values V
+    (N_t x N_x, or N_x): time node i of the coarse mesh is fine node 2i, space grid node (i, j)
+    is fine grid node (2i, 2j)."""
+    assert fine.K == coarse.K + 1 and fine.J == coarse.J + 1 and fine.domain == coarse.domain
+    fi = fine.mesh.dof[2 * coarse.mesh.node_j, 2 * coarse.mesh.node_i]
+    V = np.asarray(V, dtype=np.float64)
+    return V[::2][:, fi] if V.ndim == 2 else V[fi]
+
+
+def prolong_wavelet(coarse: Problem, fine: Problem, Wc):
+    """The coarse solution (wavelet coordinates, paper order) as a fine-level vector: the first
+    2^(J-1) + 1 fine wavelets are the coarse ones, the new details get 0; in x the coarse P1
+    function is written in the fine basis (prolongation P)."""
+    P = space.prolongation(coarse.mesh, fine.mesh)
+    Wf = np.zeros((fine.Nt, fine.Nx))
+    Wf[:coarse.Nt] = rows(P, Wc)
+    return Wf
+
+
+def nested_solve(K, J, levels, g_nodal, u0_nodal, eps, rate=1.0, domain=space.SQUARE, D=None, c=0.0,
+                 maxit=500):
+    """Nested iteration over the meshes (K - m, J - m), m = levels-1 .. 0, with level tolerances
+    eps 2^(rate m) (absolute, Eq. 3.3).  Returns (u, w, iterations per level, coarsest first)."""
+    if levels < 1 or K - levels + 1 < space.coarsest_level(domain) or J - levels + 1 < 1:
+        raise ValueError("too many nested levels for this mesh")
+    probs = [Problem(K - m, J - m, domain, D=D, c=c) for m in range(levels - 1, -1, -1)]
+    data = [None] * levels
+    data[-1] = (np.asarray(g_nodal, dtype=np.float64), np.asarray(u0_nodal, dtype=np.float64))
+    for l in range(levels - 2, -1, -1):
+        gf, uf = data[l + 1]
+        data[l] = (inject_nodal(probs[l + 1], probs[l], gf), inject_nodal(probs[l + 1], probs[l], uf))
+    w, its = None, []
+    for l, p in enumerate(probs):
+        m = levels - 1 - l
+        fhat = p.rhs_hat(*data[l])
+        x0 = None if w is None else prolong_wavelet(probs[l - 1], p, w)
+        w, info = pcg(p.apply_Shat, p.apply_KX, fhat, tol=eps * 2.0 ** (rate * m), tol_mode="abs",
+                      maxit=maxit, x0=x0)
+        its.append(info["iters"])
+    return probs[-1].synth(w), w, its
