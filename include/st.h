@@ -63,9 +63,14 @@ typedef enum {
                             the outer residual f_hat - S_hat w uses the binary64 S (with
                             its binary64 K_x), corrections and sums are binary64; the inner
                             solve runs S_hat and K_X in binary32 with binary64 inner products */
-  ST_MIXED_PRECOND = 2   /* one binary64 PCG (binary64 S_hat, recurrences and inner products)
+  ST_MIXED_PRECOND = 2,  /* one binary64 PCG (binary64 S_hat, recurrences and inner products)
                             preconditioned by K_X in binary32, with the flexible (Polak-Ribiere)
                             beta = r^T (z - z_old) / rho_old */
+  ST_MIXED_BF16 = 3      /* as ST_MIXED_FP32, but the inner PCG's preconditioner K_X keeps its
+                            multigrid vectors (iterates, right-hand sides, coarse levels) in
+                            bfloat16 storage with binary32 arithmetic, and the inner PCG uses
+                            the flexible beta; the inner S_hat and the outer stopping test
+                            stay binary32 / binary64 as in ST_MIXED_FP32 */
 } st_precision;
 
 typedef struct {
@@ -149,7 +154,7 @@ st_status st_rhs(st_handle h, const double* g_nodal, const double* u0_nodal, dou
  * input content of w is ignored and overwritten).  Stops by cfg.tol / cfg.tol_mode.
  * Synchronises the bound stream once per iteration (8 scalars read back).
  * *iters receives the iteration count; *relres sqrt(r^T K_X r / r_0^T K_X r_0).
- * With cfg.precision = ST_MIXED_FP32 the solve is iterative refinement: each outer step
+ * With cfg.precision = ST_MIXED_FP32 (or ST_MIXED_BF16) the solve is iterative refinement: each outer step
  * solves S_hat d = r with binary32 PCG to cfg.inner_tol, adds d to w in binary64 and
  * recomputes r = f_hat - S_hat w in binary64; it stops when the binary64 residual meets
  * cfg.tol in the K_X norm (K_X applied in binary32).  *iters is then the total number of
@@ -172,6 +177,11 @@ st_status st_problem_info(st_handle h, int b, st_solve_info* out, int* status);
  * st_apply_KX; float device vectors of N_t x N_x in wavelet order).  Valid on any handle. */
 st_status st_apply_S_f32(st_handle h, const float* w, float* q);
 st_status st_apply_KX_f32(st_handle h, const float* r, float* z);
+
+/* K_X of the ST_MIXED_BF16 inner solve: binary32 arithmetic with every multigrid vector stored
+ * as bfloat16 (r and z are float device vectors of N_t x N_x in wavelet order).  Not in the
+ * paper.  Valid on any handle. */
+st_status st_apply_KX_bf16(st_handle h, const float* r, float* z);
 
 /* End-to-end solve from host memory: copies g_nodal_host (B x N_t x N_x) and u0_host (B x N_x)
  * to the device, forms f_hat, runs PCG, synthesises u = W w and copies u to u_host
@@ -258,6 +268,22 @@ st_status st_server_poll(st_server s, int64_t ticket, int* state, st_solve_info*
 
 /* Serves every submitted request, stops the worker and frees all device memory. */
 st_status st_server_stop(st_server s);
+
+/* Nested iteration (Sec. 4.4: with the algebraic error kept proportional to the discretisation
+ * error, nested iteration after Hackbusch Ch. 5 makes the solve linear in N_t N_x; the paper
+ * gives no procedure).  Solves on the meshes (K - m, J - m), m = levels-1 .. 0, of the handle's
+ * domain with its st_config: level m's data are the fine nodal values g (B x N_t x N_x) and u0
+ * (B x N_x) at that mesh's nodes (injection), its PCG starts from the previous level's solution
+ * (coarse wavelet row i is fine row 2i, new details 0, rows prolongated by nested P1 in x) and
+ * stops when sqrt(r^T K_X r) <= eps 2^(rate m) (Eq. 3.3, absolute; 2^rate is the expected ratio
+ * of discretisation errors between consecutive levels).  w (B x N_t x N_x, wavelet order)
+ * receives the finest solution; iters_per_level (levels ints, coarsest first; may be NULL) the
+ * PCG iterations of each level.  The coarser handles are created on the first call and kept
+ * with h (about 1/8, 1/64, ... of its memory).  Needs K - levels + 1 >= 1 (>= 2 on the L-shape)
+ * and J - levels + 1 >= 1.  Synchronous.  Returns ST_ERR_MAXIT if some level stopped at maxit
+ * (the finer levels still run), ST_ERR_BREAKDOWN or ST_ERR_CUDA on failure. */
+st_status st_nested_solve(st_handle h, int levels, double eps, double rate, const double* g_nodal,
+                          const double* u0_nodal, double* w, int* iters_per_level);
 
 /* Autotuner (not in the paper).  Two Gauss-Seidel kernels compute identical sweeps: shared-
  * memory tiles (the default) and a register wavefront.  For every multigrid level above the

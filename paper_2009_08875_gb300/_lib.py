@@ -26,7 +26,7 @@ class StSolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("relres", ctypes.c_double)]
 
 
-ST_FP64, ST_MIXED_FP32, ST_MIXED_PRECOND = 0, 1, 2
+ST_FP64, ST_MIXED_FP32, ST_MIXED_PRECOND, ST_MIXED_BF16 = 0, 1, 2, 3
 
 
 class StProfile(ctypes.Structure):
@@ -67,9 +67,12 @@ _SIGS = {
     "st_solve_info_get": (ctypes.c_int, [_P, ctypes.POINTER(StSolveInfo)]),
     "st_apply_S_f32": (ctypes.c_int, [_P, _P, _P]),
     "st_apply_KX_f32": (ctypes.c_int, [_P, _P, _P]),
+    "st_apply_KX_bf16": (ctypes.c_int, [_P, _P, _P]),
     "st_solve_host": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double)]),
     "st_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "st_nested_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P,
+                                       ctypes.POINTER(ctypes.c_int)]),
     "st_set_smoother": (ctypes.c_int, [_P, ctypes.c_int]),
     "st_profile_begin": (ctypes.c_int, [_P]),
     "st_profile_end": (ctypes.c_int, [_P, ctypes.POINTER(StProfile)]),

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <type_traits>
+
 #include "st_internal.cuh"
 
 namespace st {
@@ -192,12 +194,21 @@ st_status apply_Shat_impl(st_handle h, int nb, const T* w, T* q) {
   return ST_OK;
 }
 
+// K_l multigrid on `rows` slices; narrow: binary32 work with bfloat16 storage
 template <typename T>
-st_status apply_KX_impl(st_handle h, int nb, const T* r, T* z) {
+cudaError_t mg_kl(st_handle h, int rows, const T* b, T* x, bool narrow) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (narrow) return mg_apply_bf16(h, rows, -1, b, x);
+  }
+  return mg_apply<T>(h, rows, -1, b, x);
+}
+
+template <typename T>
+st_status apply_KX_impl(st_handle h, int nb, const T* r, T* z, bool narrow = false) {
   const int rows = (int)(nb * h->Nt);
-  ST_CHECK_CUDA(mg_apply<T>(h, rows, -1, r, ws<T>(h->X)), "K_l multigrid (1)");
+  ST_CHECK_CUDA(mg_kl<T>(h, rows, r, ws<T>(h->X), narrow), "K_l multigrid (1)");
   ST_CHECK_CUDA(launch_apply_A<T>(h, rows, ws<T>(h->X), ws<T>(h->Y)), "A_x");
-  ST_CHECK_CUDA(mg_apply<T>(h, rows, -1, ws<T>(h->Y), z), "K_l multigrid (2)");
+  ST_CHECK_CUDA(mg_kl<T>(h, rows, ws<T>(h->Y), z, narrow), "K_l multigrid (2)");
   return ST_OK;
 }
 
@@ -330,6 +341,20 @@ st_status finish(st_handle h) {
   return s;
 }
 
+// Initial residual: r = f_hat - S_hat w from the caller's w when h->use_guess is set (nested
+// iteration), else w = 0 and r = f_hat.
+st_status init_residual(st_handle h, const double* fhat, double* w) {
+  const int64_t N = h->B * h->Nt * h->Nx;
+  if (h->use_guess) {
+    ST_CHECK(apply_Shat_impl<double>(h, h->B, w, h->q));
+    ST_CHECK_CUDA(launch_residual_split(h, h->r, nullptr, fhat, h->q, N), "initial residual");
+  } else {
+    ST_CHECK_CUDA(launch_zero<double>(h, w, N), "zero w");
+    ST_CHECK_CUDA(launch_copy<double, double>(h, h->r, fhat, N), "copy r");
+  }
+  return ST_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // PCG iteration bodies on all B problems: p = z + beta p, q = S_hat p, alpha, w and r updates,
 // z = K_X r, rho and beta (problems whose active flag is clear keep their vectors)
@@ -375,8 +400,7 @@ st_status pcg64_impl(st_handle h, const double* fhat, double* w) {
   Tracker t;
   for (int b = 0; b < nb; ++b) h->act_host[b] = 1;
   ST_CHECK(push_act(h));
-  ST_CHECK_CUDA(launch_zero<double>(h, w, n * nb), "zero w");
-  ST_CHECK_CUDA(launch_copy<double, double>(h, h->r, fhat, n * nb), "copy r");
+  ST_CHECK(init_residual(h, fhat, w));
   ST_CHECK(apply_KX_impl<double>(h, h->B, h->r, h->z));
   ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO, DOT_INIT), "dot r z");
   ST_CHECK_CUDA(launch_zero<double>(h, h->p, n * nb), "zero p");  // first body: p = z + 0 p
@@ -403,10 +427,13 @@ st_status pcg64_impl(st_handle h, const double* fhat, double* w) {
 // ---------------------------------------------------------------------------------------------
 // Binary32 PCG on S_hat x = ri for the problems with out_act[b] set, from x = 0, with
 // zi = K_X ri already formed; each stops at a relative reduction of inner_tol or inner_maxit.
+// ST_MIXED_BF16: the preconditioner stores its multigrid vectors as bfloat16, which makes it
+// slightly nonlinear, so beta takes the flexible (Polak-Ribiere) form r^T (z - z_old) / rho_old.
 st_status inner_pcg32(st_handle h, const std::vector<int>& out_act, std::vector<int>& its) {
   const int nb = h->B;
   const int64_t n = h->Nt * h->Nx;
   const st_config& c = h->cfg;
+  const bool narrow = c.precision == ST_MIXED_BF16;
   ST_CHECK_CUDA(launch_zero<float>(h, h->xi, n * nb), "zero inner x");
   ST_CHECK_CUDA(launch_zero<float>(h, h->pi, n * nb), "zero inner p");  // first body: p = z + 0 p
   ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RHO, DOT_INIT), "inner dot r z");
@@ -423,8 +450,11 @@ st_status inner_pcg32(st_handle h, const std::vector<int>& out_act, std::vector<
     ST_CHECK(apply_Shat_impl<float>(h, h->B, h->pi, h->qi));
     ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->pi, h->qi, n, SC_PQ, DOT_ALPHA), "inner dot p q");
     ST_CHECK_CUDA(launch_update_wr<float>(h, 0, nb, h->xi, h->ri, h->pi, h->qi, n), "inner update");
-    ST_CHECK(apply_KX_impl<float>(h, h->B, h->ri, h->zi));
-    ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RHO_NEW, DOT_BETA), "inner dot r z");
+    if (narrow)
+      ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RZOLD, DOT_STORE), "inner dot r z_old");
+    ST_CHECK(apply_KX_impl<float>(h, h->B, h->ri, h->zi, narrow));
+    ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RHO_NEW, narrow ? DOT_BETA_FLEX : DOT_BETA),
+                  "inner dot r z");
     return ST_OK;
   };
   for (int it = 1; it <= c.inner_maxit && any_active(h); ++it) {
@@ -451,9 +481,8 @@ st_status pcg_mixed_impl(st_handle h, const double* fhat, double* w) {
   const int64_t n = h->Nt * h->Nx;
   const st_config& c = h->cfg;
   Tracker t;
-  ST_CHECK_CUDA(launch_zero<double>(h, w, n * nb), "zero w");
-  ST_CHECK_CUDA(launch_copy<double, double>(h, h->r, fhat, n * nb), "copy r");
-  ST_CHECK_CUDA(launch_copy<float, double>(h, h->ri, fhat, n * nb), "round r");
+  ST_CHECK(init_residual(h, fhat, w));
+  ST_CHECK_CUDA(launch_copy<float, double>(h, h->ri, h->r, n * nb), "round r");
   ST_CHECK(apply_KX_impl<float>(h, h->B, h->ri, h->zi));
   ST_CHECK_CUDA(launch_dot<double, float>(h, 0, nb, h->r, h->zi, n, SC_OUTER, DOT_STORE), "outer dot");
   ST_CHECK(read_scalars(h));
@@ -505,8 +534,7 @@ st_status pcg_precond_impl(st_handle h, const double* fhat, double* w) {
   Tracker t;
   for (int b = 0; b < nb; ++b) h->act_host[b] = 1;
   ST_CHECK(push_act(h));
-  ST_CHECK_CUDA(launch_zero<double>(h, w, n * nb), "zero w");
-  ST_CHECK_CUDA(launch_copy<double, double>(h, h->r, fhat, n * nb), "copy r");
+  ST_CHECK(init_residual(h, fhat, w));
   ST_CHECK(precond32(h, nb, h->r, h->z, h->ri, h->zi));
   ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO, DOT_INIT), "dot r z");
   ST_CHECK_CUDA(launch_zero<double>(h, h->p, n * nb), "zero p");  // first body: p = z + 0 p
@@ -544,6 +572,7 @@ st_status pcg_impl(st_handle h, const double* fhat, double* w, int* iters, doubl
   st_status s;
   switch (h->cfg.precision) {
     case ST_MIXED_FP32:
+    case ST_MIXED_BF16:
       s = pcg_mixed_impl(h, fhat, w);
       break;
     case ST_MIXED_PRECOND:
@@ -648,7 +677,8 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   ST_REQUIRE(c.alpha > 0.0 && std::isfinite(c.alpha), "st_setup: alpha must be positive");
   ST_REQUIRE(c.maxit >= 0 && c.tol >= 0.0 && (c.tol_mode == 0 || c.tol_mode == 1),
              "st_setup: invalid tolerance settings");
-  ST_REQUIRE(c.precision == ST_FP64 || c.precision == ST_MIXED_FP32 || c.precision == ST_MIXED_PRECOND,
+  ST_REQUIRE(c.precision == ST_FP64 || c.precision == ST_MIXED_FP32 || c.precision == ST_MIXED_PRECOND ||
+                 c.precision == ST_MIXED_BF16,
              "st_setup: unsupported precision");
   ST_REQUIRE(c.inner_tol > 0.0 && c.inner_tol < 1.0 && c.inner_maxit >= 1,
              "st_setup: inner_tol must be in (0, 1) and inner_maxit >= 1");
@@ -715,7 +745,7 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   // binary32 vectors: the five of the inner PCG (ST_MIXED_FP32) or the preconditioner's input
   // and output (ST_MIXED_PRECOND)
   std::vector<float**> fplan;
-  if (c.precision == ST_MIXED_FP32) fplan = {&h->xi, &h->ri, &h->pi, &h->zi, &h->qi};
+  if (c.precision == ST_MIXED_FP32 || c.precision == ST_MIXED_BF16) fplan = {&h->xi, &h->ri, &h->pi, &h->zi, &h->qi};
   if (c.precision == ST_MIXED_PRECOND) fplan = {&h->ri, &h->zi};
   for (float** fp : fplan)
     if (s == ST_OK) s = alloc_bytes(reinterpret_cast<void**>(fp), V * sizeof(float), "binary32 vectors");
@@ -771,6 +801,8 @@ st_status st_destroy(st_handle h) {
   if (!h) return ST_OK;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
+  for (int m = 0; m < 16; ++m)
+    if (h->nest[m]) st_destroy(h->nest[m]);
   free_all(h);
   delete h;
   return ST_OK;
@@ -833,6 +865,12 @@ st_status st_apply_KX_f32(st_handle h, const float* r, float* z) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(r && z, "st_apply_KX_f32: null pointer");
   return apply_KX_impl<float>(h, h->B, r, z);
+}
+
+st_status st_apply_KX_bf16(st_handle h, const float* r, float* z) {
+  ST_CHECK(check_handle(h));
+  ST_REQUIRE(r && z, "st_apply_KX_bf16: null pointer");
+  return apply_KX_impl<float>(h, h->B, r, z, true);
 }
 
 st_status st_apply_KX(st_handle h, const double* r, double* z) {

@@ -7,6 +7,10 @@
 // Gauss-Seidel in three colours c = (i + j) mod 3 of the grid indices (i, j) = (ix+1, iy+1),
 // pre-sweeps in colour order 0,1,2 and post-sweeps 2,1,0 (a symmetric V-cycle), exact
 // solve on level 1 (one unknown), every application starting from x = 0.
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
 #include "st_internal.cuh"
 
 namespace st {
@@ -53,21 +57,7 @@ __device__ __forceinline__ Coef<T> slice_coef(const Coef<T>* coef, int coef_clas
   return coef[cls * (K + 1) + level];
 }
 
-// ---------------------------------------------------------------------------------------
-// Nested P1 prolongation: the value of P xc at fine grid node (i, j) (1-based grid indices):
-// the coarse value at even-even nodes, the average of the two coarse end points at the
-// midpoints of horizontal, vertical and (1,1)-diagonal coarse edges; coarse boundary values 0.
-// ---------------------------------------------------------------------------------------
-// Branch-free: with (I, J) = (i >> 1, j >> 1) the value is the average of the coarse values at
-// (I, J) and (I + i mod 2, J + j mod 2); at even-even nodes both are the same node and the
-// average is exact.
-template <typename T>
-__device__ __forceinline__ T prolong_value(const T* __restrict__ cs, int nc, int i, int j) {
-  const int I0 = i >> 1, J0 = j >> 1, I1 = I0 + (i & 1), J1 = J0 + (j & 1);
-  const T a = (I0 >= 1 && I0 <= nc && J0 >= 1 && J0 <= nc) ? cs[(J0 - 1) * nc + (I0 - 1)] : T(0);
-  const T b = (I1 >= 1 && I1 <= nc && J1 >= 1 && J1 <= nc) ? cs[(J1 - 1) * nc + (I1 - 1)] : T(0);
-  return T(0.5) * (a + b);
-}
+// Nested P1 prolongation: prolong_value (st_internal.cuh).
 
 // ---------------------------------------------------------------------------------------
 // Gauss-Seidel: NSW full 3-colour sweeps of one slice tile, staged in shared memory.
@@ -83,8 +73,8 @@ constexpr int kWR = 96;  // region width = 32 lanes x 3 columns
 // assembles C = a A + s M on the level's nodes (rows of nodes outside the domain become the
 // identity with zero right-hand side) and solves C x = D b' by Gaussian elimination (C is SPD on
 // the domain nodes, so no pivoting is needed).
-template <typename T>
-__global__ void k_coarse_dense3(T* __restrict__ x, const T* __restrict__ b, int nslices,
+template <typename T, typename G>
+__global__ void k_coarse_dense3(G* __restrict__ x, const G* __restrict__ b, int nslices,
                                 const Coef<T>* __restrict__ coef, int coef_class, int J, int K, int lshape) {
   const int sl = blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= nslices) return;
@@ -98,7 +88,7 @@ __global__ void k_coarse_dense3(T* __restrict__ x, const T* __restrict__ b, int 
       continue;
     }
     A[p][p] = cf.c;
-    A[p][9] = cf.c * b[(int64_t)sl * 9 + p];
+    A[p][9] = cf.c * T(b[(int64_t)sl * 9 + p]);
     const int nb[6][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}, {1, 1}, {-1, -1}};
     for (int t = 0; t < 6; ++t) {
       const int jx = ix + nb[t][0], jy = iy + nb[t][1];
@@ -117,16 +107,16 @@ __global__ void k_coarse_dense3(T* __restrict__ x, const T* __restrict__ b, int 
     for (int q = r + 1; q < 9; ++q) v -= A[r][q] * A[q][9];
     A[r][9] = v / A[r][r];
   }
-  for (int p = 0; p < 9; ++p) x[(int64_t)sl * 9 + p] = A[p][9];
+  for (int p = 0; p < 9; ++p) x[(int64_t)sl * 9 + p] = G(A[p][9]);
 }
 
 // The sweep is out of place (x_in -> x_out): a block's halo overlaps its neighbours' interiors,
 // so reading and writing one buffer in the same launch would race.
 // With PROL the launch first adds the prolongated coarse correction P xc to the iterate it loads
 // (the coarse-grid correction of the V-cycle, fused into the first post-smoothing launch).
-template <typename T, int NSW, int HR, bool DIAG, bool PROL>
-__global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T* __restrict__ x_in,
-                                                  const T* __restrict__ b, const T* __restrict__ xc, int n,
+template <typename T, typename G, int NSW, int HR, bool DIAG, bool PROL>
+__global__ void __launch_bounds__(256) k_gs_sweep(G* __restrict__ x_out, const G* __restrict__ x_in,
+                                                  const G* __restrict__ b, const G* __restrict__ xc, int n,
                                                   const Coef<T>* __restrict__ coef, int coef_class, int J,
                                                   int K, int level, int reverse, int zero_init, int lshape) {
   constexpr int H = 3 * NSW;
@@ -138,11 +128,11 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
 
   const int slice = blockIdx.z;
   const int64_t off = (int64_t)slice * n * n;
-  T* xsl = x_out + off;
-  const T* xin = x_in + off;
-  const T* bsl = b + off;
+  G* xsl = x_out + off;
+  const G* xin = x_in + off;
+  const G* bsl = b + off;
   const int nc = (n - 1) / 2;
-  const T* xcs = PROL ? xc + (int64_t)slice * nc * nc : nullptr;
+  const G* xcs = PROL ? xc + (int64_t)slice * nc * nc : nullptr;
   const int gx0 = blockIdx.x * TX - H;
   const int gy0 = blockIdx.y * TY - H;
   const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, level);
@@ -153,13 +143,13 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
     bool in = gx >= 0 && gx < n && gy >= 0 && gy < n && !outside_domain(gx, gy, n, lshape);
     int64_t gi = (int64_t)gy * n + gx;
     if (PROL) {
-      T v = (in && !zero_init) ? xin[gi] : T(0);
-      if (in) v += prolong_value(xcs, nc, gx + 1, gy + 1);
+      T v = (in && !zero_init) ? T(xin[gi]) : T(0);
+      if (in) v += prolong_value<T>(xcs, nc, gx + 1, gy + 1);
       xs[idx] = v;
     } else {
-      xs[idx] = (in && !zero_init) ? xin[gi] : T(0);
+      xs[idx] = (in && !zero_init) ? T(xin[gi]) : T(0);
     }
-    bs[idx] = in ? bsl[gi] : T(0);
+    bs[idx] = in ? T(bsl[gi]) : T(0);
   }
   __syncthreads();
 
@@ -208,7 +198,7 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
   for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
     int ty = idx / TX, tx = idx - ty * TX;
     int gx = gx0 + H + tx, gy = gy0 + H + ty;
-    if (gx < n && gy < n) xsl[(int64_t)gy * n + gx] = xs[(ty + H) * kWR + tx + H];
+    if (gx < n && gy < n) xsl[(int64_t)gy * n + gx] = G(xs[(ty + H) * kWR + tx + H]);
   }
 }
 
@@ -227,9 +217,9 @@ __global__ void __launch_bounds__(256) k_gs_sweep(T* __restrict__ x_out, const T
 // rows, each walked by its own warp over SEG + 2 S rows: errors from the segment's missing
 // neighbours travel one row per colour step, so after S steps the middle SEG rows are exact.
 // ---------------------------------------------------------------------------------------
-template <typename T, int S, bool DIAG, bool PROL>
-__global__ void __launch_bounds__(128) k_gs_wave(T* __restrict__ x_out, const T* __restrict__ x_in,
-                                                 const T* __restrict__ b, const T* __restrict__ xc, int n,
+template <typename T, typename G, int S, bool DIAG, bool PROL>
+__global__ void __launch_bounds__(128) k_gs_wave(G* __restrict__ x_out, const G* __restrict__ x_in,
+                                                 const G* __restrict__ b, const G* __restrict__ xc, int n,
                                                  const Coef<T>* __restrict__ coef, int coef_class, int J, int K,
                                                  int level, int reverse, int zero_init, int lshape, int nstrips,
                                                  int nseg, int seg, int nslices) {
@@ -245,11 +235,11 @@ __global__ void __launch_bounds__(128) k_gs_wave(T* __restrict__ x_out, const T*
   const int ybase = r0 - S;       // row of time step 0
   const int gx0 = strip * TXW - S;      // global column of the strip's column 0
   const int64_t off = (int64_t)slice * n * n;
-  const T* xin = x_in + off;
-  const T* bsl = b + off;
-  T* xo = x_out + off;
+  const G* xin = x_in + off;
+  const G* bsl = b + off;
+  G* xo = x_out + off;
   const int nc = (n - 1) / 2;
-  const T* xcs = PROL ? xc + (int64_t)slice * nc * nc : nullptr;
+  const G* xcs = PROL ? xc + (int64_t)slice * nc * nc : nullptr;
   const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, level);
   const int cbase = gx0 + 3 * lane;  // global column of this lane's element 0
 
@@ -265,10 +255,10 @@ __global__ void __launch_bounds__(128) k_gs_wave(T* __restrict__ x_out, const T*
       const int gx = cbase + e;
       const bool in = r >= 0 && r < n && gx >= 0 && gx < n && !outside_domain(gx, r, n, lshape);
       const int64_t gi = (int64_t)r * n + gx;
-      T v = (in && !zero_init) ? xin[gi] : T(0);
-      if (PROL && in) v += prolong_value(xcs, nc, gx + 1, r + 1);
+      T v = (in && !zero_init) ? T(xin[gi]) : T(0);
+      if (PROL && in) v += prolong_value<T>(xcs, nc, gx + 1, r + 1);
       xr[e] = v;
-      br[e] = in ? bsl[gi] : T(0);
+      br[e] = in ? T(bsl[gi]) : T(0);
     }
   };
 
@@ -332,7 +322,7 @@ __global__ void __launch_bounds__(128) k_gs_wave(T* __restrict__ x_out, const T*
           for (int e = 0; e < 3; ++e) {
             const int cl = 3 * lane + e;
             const int gx = cbase + e;
-            if (cl >= S && cl < kWR - S && gx < n) xo[(int64_t)ro * n + gx] = xr[e];
+            if (cl >= S && cl < kWR - S && gx < n) xo[(int64_t)ro * n + gx] = G(xr[e]);
           }
         }
       }
@@ -341,8 +331,8 @@ __global__ void __launch_bounds__(128) k_gs_wave(T* __restrict__ x_out, const T*
 }
 
 // b' = b / c on the finest level (the multigrid's scaled right-hand side)
-template <typename T>
-__global__ void k_scale_rhs(T* __restrict__ bs, const T* __restrict__ b, int n, const Coef<T>* __restrict__ coef,
+template <typename T, typename G>
+__global__ void k_scale_rhs(G* __restrict__ bs, const T* __restrict__ b, int n, const Coef<T>* __restrict__ coef,
                             int coef_class, int J, int K) {
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -350,12 +340,12 @@ __global__ void k_scale_rhs(T* __restrict__ bs, const T* __restrict__ b, int n, 
   const int slice = blockIdx.y;
   const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, K);
   const int64_t i = (int64_t)slice * N + p;
-  bs[i] = b[i] * cf.inv_c;
+  bs[i] = G(b[i] * cf.inv_c);
 }
 
 // x += P xc (used when there is no post-smoothing to fuse the correction into)
-template <typename T>
-__global__ void k_prolong_add(T* __restrict__ x, const T* __restrict__ xc, int nf, int lshape) {
+template <typename T, typename G>
+__global__ void k_prolong_add(G* __restrict__ x, const G* __restrict__ xc, int nf, int lshape) {
   const int N = nf * nf;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
@@ -363,7 +353,8 @@ __global__ void k_prolong_add(T* __restrict__ x, const T* __restrict__ xc, int n
   const int slice = blockIdx.y;
   const int iy = p / nf, ix = p - iy * nf;
   if (outside_domain(ix, iy, nf, lshape)) return;
-  x[(int64_t)slice * N + p] += prolong_value(xc + (int64_t)slice * nc * nc, nc, ix + 1, iy + 1);
+  const int64_t i = (int64_t)slice * N + p;
+  x[i] = G(T(x[i]) + prolong_value<T>(xc + (int64_t)slice * nc * nc, nc, ix + 1, iy + 1));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -377,9 +368,9 @@ constexpr int kRCX = 32, kRCY = 16;
 constexpr int kRFX = 2 * kRCX + 1, kRFY = 2 * kRCY + 1;  // residual points
 constexpr int kRXX = kRFX + 2, kRXY = kRFY + 2;          // x points (one-point halo)
 
-template <typename T, bool DIAG>
-__global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, const T* __restrict__ x,
-                                                           const T* __restrict__ b, int n,
+template <typename T, typename G, bool DIAG>
+__global__ void __launch_bounds__(256) k_residual_restrict(G* __restrict__ bc, const G* __restrict__ x,
+                                                           const G* __restrict__ b, int n,
                                                            const Coef<T>* __restrict__ coef, int coef_class, int J,
                                                            int K, int level, int lshape) {
   __shared__ T xs[kRXY * kRXX];
@@ -387,8 +378,8 @@ __global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, c
   const int nc = (n - 1) / 2;
   const int slice = blockIdx.z;
   const int64_t off = (int64_t)slice * n * n;
-  const T* xsl = x + off;
-  const T* bsl = b + off;
+  const G* xsl = x + off;
+  const G* bsl = b + off;
   const int cx0 = blockIdx.x * kRCX, cy0 = blockIdx.y * kRCY;
   const int fx0 = 2 * cx0, fy0 = 2 * cy0;  // first residual point (fine interior index)
   const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, level);
@@ -396,7 +387,7 @@ __global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, c
     const int ry = idx / kRXX, rx = idx - ry * kRXX;
     const int gx = fx0 - 1 + rx, gy = fy0 - 1 + ry;
     const bool in = gx >= 0 && gx < n && gy >= 0 && gy < n && !outside_domain(gx, gy, n, lshape);
-    xs[idx] = in ? xsl[(int64_t)gy * n + gx] : T(0);
+    xs[idx] = in ? T(xsl[(int64_t)gy * n + gx]) : T(0);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < kRFY * kRFX; idx += blockDim.x) {
@@ -406,7 +397,7 @@ __global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, c
     if (gx < n && gy < n && !outside_domain(gx, gy, n, lshape)) {
       const int i = (ry + 1) * kRXX + (rx + 1);
       // scaled residual r' = D^-1 (b - C x) = b' - x - (ax/c) sx - (ay/c) sy - (dg/c) sd
-      T v = bsl[(int64_t)gy * n + gx] - cf.axs * (xs[i - 1] + xs[i + 1]);
+      T v = T(bsl[(int64_t)gy * n + gx]) - cf.axs * (xs[i - 1] + xs[i + 1]);
       v -= cf.ays * (xs[i - kRXX] + xs[i + kRXX]);
       if (DIAG) v -= cf.dgs * (xs[i + kRXX + 1] + xs[i - kRXX - 1]);
       r = v - xs[i];
@@ -419,19 +410,19 @@ __global__ void __launch_bounds__(256) k_residual_restrict(T* __restrict__ bc, c
     const int cx = cx0 + tx, cy = cy0 + ty;
     if (cx >= nc || cy >= nc) continue;
     if (outside_domain(cx, cy, nc, lshape)) {
-      bc[(int64_t)slice * nc * nc + (int64_t)cy * nc + cx] = T(0);
+      bc[(int64_t)slice * nc * nc + (int64_t)cy * nc + cx] = G(0.0f);
       continue;
     }
     const int i = (2 * ty + 1) * kRFX + (2 * tx + 1);
     T e = (rs[i - 1] + rs[i + 1]) + (rs[i - kRFX] + rs[i + kRFX]) + (rs[i + kRFX + 1] + rs[i - kRFX - 1]);
     // coarse scaled rhs: D_c^-1 P^T D r' = (c / c_coarse) P^T r'
-    bc[(int64_t)slice * nc * nc + (int64_t)cy * nc + cx] = cf.rho * rs[i] + (T(0.5) * cf.rho) * e;
+    bc[(int64_t)slice * nc * nc + (int64_t)cy * nc + cx] = G(cf.rho * rs[i] + (T(0.5) * cf.rho) * e);
   }
 }
 
 // exact solve on level 1 (one unknown per slice)
-template <typename T>
-__global__ void k_coarse1(T* __restrict__ x, const T* __restrict__ b, int nslices) {
+template <typename G>
+__global__ void k_coarse1(G* __restrict__ x, const G* __restrict__ b, int nslices) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nslices) return;
   // one unknown: the scaled right-hand side is the solution
@@ -478,9 +469,9 @@ struct SweepShape<float> {
   static constexpr int kFusedNSW = ST_GS_NSW32, kFusedHR = ST_GS_HR32, kSingleHR = 64;
 };
 
-template <typename T, int NSW, int HR, bool DIAG, bool PROL>
-cudaError_t gs_launch(const st_handle_s* h, int k, int nslices, int cls, T* x_out, const T* x_in, const T* b,
-                      const T* xc, bool reverse, bool zero_init) {
+template <typename T, typename G, int NSW, int HR, bool DIAG, bool PROL>
+cudaError_t gs_launch(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in, const G* b,
+                      const G* xc, bool reverse, bool zero_init) {
   constexpr int H = 3 * NSW;
   const int n = (1 << k) - 1;
   const int TX = kWR - 2 * H, TY = HR - 2 * H;
@@ -488,22 +479,22 @@ cudaError_t gs_launch(const st_handle_s* h, int k, int nslices, int cls, T* x_ou
   const size_t smem = 2 * sizeof(T) * HR * kWR;
   // profiled: the finest level, which carries three quarters of the sweep work
   const bool prof = (k == h->K) && prof_start(h);
-  k_gs_sweep<T, NSW, HR, DIAG, PROL><<<grid, 256, smem, h->stream>>>(x_out, x_in, b, xc, n, coef_table<T>(h), cls,
-                                                                      h->J, h->K, k, reverse ? 1 : 0,
-                                                                      zero_init ? 1 : 0, h->domain);
+  k_gs_sweep<T, G, NSW, HR, DIAG, PROL><<<grid, 256, smem, h->stream>>>(x_out, x_in, b, xc, n, coef_table<T>(h),
+                                                                         cls, h->J, h->K, k, reverse ? 1 : 0,
+                                                                         zero_init ? 1 : 0, h->domain);
   count_launch(h);
   if (prof) {
     // per point and sweep: 3 adds + 1 fma (+ 1 add + 1 fma with diagonal couplings);
     // bytes: read x and b, write x (x is not read when the launch starts from x = 0)
     const double pts = (double)n * n * nslices;
-    prof_stop(h, DIAG ? 1 : 0, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(T) * (zero_init ? 2.0 : 3.0));
+    prof_stop(h, DIAG ? 1 : 0, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(G) * (zero_init ? 2.0 : 3.0));
   }
   return cudaGetLastError();
 }
 
-template <typename T, int NSW, bool DIAG, bool PROL>
-cudaError_t wave_launch(const st_handle_s* h, int k, int nslices, int cls, T* x_out, const T* x_in, const T* b,
-                        const T* xc, bool reverse, bool zero_init) {
+template <typename T, typename G, int NSW, bool DIAG, bool PROL>
+cudaError_t wave_launch(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in, const G* b,
+                        const G* xc, bool reverse, bool zero_init) {
   constexpr int S = 3 * NSW;
   const int n = (1 << k) - 1;
   const int TXW = kWR - 2 * S;
@@ -513,13 +504,13 @@ cudaError_t wave_launch(const st_handle_s* h, int k, int nslices, int cls, T* x_
   const int64_t warps = (int64_t)nstrips * nseg * nslices;
   const unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
   const bool prof = (k == h->K) && prof_start(h);
-  k_gs_wave<T, S, DIAG, PROL><<<blocks, 128, 0, h->stream>>>(x_out, x_in, b, xc, n, coef_table<T>(h), cls, h->J,
-                                                              h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0,
-                                                              h->domain, nstrips, nseg, seg, nslices);
+  k_gs_wave<T, G, S, DIAG, PROL><<<blocks, 128, 0, h->stream>>>(x_out, x_in, b, xc, n, coef_table<T>(h), cls,
+                                                                 h->J, h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0,
+                                                                 h->domain, nstrips, nseg, seg, nslices);
   count_launch(h);
   if (prof) {
     const double pts = (double)n * n * nslices;
-    prof_stop(h, DIAG ? 1 : 0, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(T) * (zero_init ? 2.0 : 3.0));
+    prof_stop(h, DIAG ? 1 : 0, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(G) * (zero_init ? 2.0 : 3.0));
   }
   return cudaGetLastError();
 }
@@ -533,30 +524,30 @@ int gs_kind(const st_handle_s* h, bool diag, int k) {
   return h->gs_kind[sizeof(T) == 4 ? 1 : 0][diag ? 1 : 0][k];
 }
 
-template <typename T, bool DIAG>
-cudaError_t gs_sweeps(const st_handle_s* h, int k, int nslices, int cls, T* x_out, const T* x_in, const T* b,
-                      const T* xc, bool reverse, bool zero_init, int nsw) {
+template <typename T, typename G, bool DIAG>
+cudaError_t gs_sweeps(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in, const G* b,
+                      const G* xc, bool reverse, bool zero_init, int nsw) {
   constexpr int F = SweepShape<T>::kFusedNSW;
   if (gs_kind<T>(h, DIAG, k) == 1) {
     if (F > 1 && nsw == F)
-      return xc ? wave_launch<T, F, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
-                : wave_launch<T, F, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
-    return xc ? wave_launch<T, 1, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
-              : wave_launch<T, 1, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+      return xc ? wave_launch<T, G, F, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
+                : wave_launch<T, G, F, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+    return xc ? wave_launch<T, G, 1, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
+              : wave_launch<T, G, 1, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
   }
   constexpr int FHR = SweepShape<T>::kFusedHR, HR1 = SweepShape<T>::kSingleHR;
   if (F > 1 && nsw == F) {
-    return xc ? gs_launch<T, F, FHR, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
-              : gs_launch<T, F, FHR, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+    return xc ? gs_launch<T, G, F, FHR, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
+              : gs_launch<T, G, F, FHR, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
   }
-  return xc ? gs_launch<T, 1, HR1, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
-            : gs_launch<T, 1, HR1, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+  return xc ? gs_launch<T, G, 1, HR1, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
+            : gs_launch<T, G, 1, HR1, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
 }
 
 // One V-cycle on level k.  xb[0], xb[1] are the level's two iterate buffers and *cur the one
 // holding the iterate; every sweep moves it to the other buffer.
-template <typename T, bool DIAG>
-cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, T* const xb[2], int* cur, const T* b,
+template <typename T, typename G, bool DIAG>
+cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, G* const xb[2], int* cur, const G* b,
                    bool x_is_zero) {
   const st::MGLevels& L = h->mg;
   const int n = (1 << k) - 1;
@@ -564,16 +555,16 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, T* const x
   cudaError_t e;
   if (k == L.kmin) {
     if (k == 1)
-      k_coarse1<T><<<(nslices + 255) / 256, 256, 0, h->stream>>>(xb[*cur], b, nslices);
+      k_coarse1<G><<<(nslices + 255) / 256, 256, 0, h->stream>>>(xb[*cur], b, nslices);
     else
-      k_coarse_dense3<T><<<(nslices + 127) / 128, 128, 0, h->stream>>>(xb[*cur], b, nslices, coef_table<T>(h), cls,
-                                                                        h->J, h->K, h->domain);
+      k_coarse_dense3<T, G><<<(nslices + 127) / 128, 128, 0, h->stream>>>(xb[*cur], b, nslices, coef_table<T>(h),
+                                                                           cls, h->J, h->K, h->domain);
     count_launch(h);
     return cudaGetLastError();
   }
   for (int s = 0; s < h->cfg.n_pre;) {
     const int nsw = (h->cfg.n_pre - s >= SweepShape<T>::kFusedNSW) ? SweepShape<T>::kFusedNSW : 1;
-    if ((e = gs_sweeps<T, DIAG>(h, k, nslices, cls, xb[*cur ^ 1], xb[*cur], b, nullptr, false,
+    if ((e = gs_sweeps<T, G, DIAG>(h, k, nslices, cls, xb[*cur ^ 1], xb[*cur], b, nullptr, false,
                                 x_is_zero && s == 0, nsw)) != cudaSuccess)
       return e;
     *cur ^= 1;
@@ -581,35 +572,42 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, T* const x
   }
   if (h->cfg.n_pre == 0 && x_is_zero) {
     // nothing smoothed yet: the iterate must hold zeros before the residual is formed
-    if ((e = cudaMemsetAsync(xb[*cur], 0, sizeof(T) * (size_t)N * nslices, h->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(xb[*cur], 0, sizeof(G) * (size_t)N * nslices, h->stream)) != cudaSuccess) return e;
   }
-  T* x = xb[*cur];
-  T* bc = reinterpret_cast<T*>(L.bc[k - 1]);
+  G* x = xb[*cur];
+  G* bc = reinterpret_cast<G*>(L.bc[k - 1]);
   const int nc = (1 << (k - 1)) - 1;
   dim3 gr((nc + kRCX - 1) / kRCX, (nc + kRCY - 1) / kRCY, nslices);
-  k_residual_restrict<T, DIAG><<<gr, 256, 0, h->stream>>>(bc, x, b, n, coef_table<T>(h), cls, h->J, h->K, k,
-                                                          h->domain);
+  k_residual_restrict<T, G, DIAG><<<gr, 256, 0, h->stream>>>(bc, x, b, n, coef_table<T>(h), cls, h->J, h->K, k,
+                                                             h->domain);
   count_launch(h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  T* const xcb[2] = {reinterpret_cast<T*>(L.xc[k - 1]), reinterpret_cast<T*>(L.xc2[k - 1])};
+  G* const xcb[2] = {reinterpret_cast<G*>(L.xc[k - 1]), reinterpret_cast<G*>(L.xc2[k - 1])};
   int ccur = 0;
-  if ((e = vcycle<T, DIAG>(h, k - 1, nslices, cls, xcb, &ccur, bc, true)) != cudaSuccess) return e;
+  if ((e = vcycle<T, G, DIAG>(h, k - 1, nslices, cls, xcb, &ccur, bc, true)) != cudaSuccess) return e;
   if (h->cfg.n_post == 0) {
     dim3 g1((N + 255) / 256, nslices);
-    k_prolong_add<T><<<g1, 256, 0, h->stream>>>(x, xcb[ccur], n, h->domain);
+    k_prolong_add<T, G><<<g1, 256, 0, h->stream>>>(x, xcb[ccur], n, h->domain);
     count_launch(h);
     return cudaGetLastError();
   }
   for (int s = 0; s < h->cfg.n_post;) {
     const int nsw = (h->cfg.n_post - s >= SweepShape<T>::kFusedNSW) ? SweepShape<T>::kFusedNSW : 1;
     // the first post-smoothing launch also applies the coarse-grid correction x += P xc
-    if ((e = gs_sweeps<T, DIAG>(h, k, nslices, cls, xb[*cur ^ 1], xb[*cur], b, s == 0 ? xcb[ccur] : nullptr, true,
+    if ((e = gs_sweeps<T, G, DIAG>(h, k, nslices, cls, xb[*cur ^ 1], xb[*cur], b, s == 0 ? xcb[ccur] : nullptr, true,
                                 false, nsw)) != cudaSuccess)
       return e;
     *cur ^= 1;
     s += nsw;
   }
   return cudaSuccess;
+}
+
+// x = the iterate, widened from the storage type (binary16 storage of binary32 work)
+template <typename T, typename G>
+__global__ void k_widen(T* __restrict__ x, const G* __restrict__ g, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = T(g[i]);
 }
 
 }  // namespace
@@ -624,53 +622,73 @@ cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, Ph
   return cudaGetLastError();
 }
 
-template <typename T, int NSW, int HR>
+template <typename T, typename G, int NSW, int HR>
 cudaError_t set_smem_attr() {
   const int smem = 2 * sizeof(T) * HR * kWR;
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gs_sweep<T, NSW, HR, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gs_sweep<T, NSW, HR, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gs_sweep<T, NSW, HR, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gs_sweep<T, NSW, HR, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_gs_sweep<T, G, NSW, HR, true, true>, attr, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gs_sweep<T, G, NSW, HR, true, false>, attr, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gs_sweep<T, G, NSW, HR, false, true>, attr, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gs_sweep<T, G, NSW, HR, false, false>, attr, smem);
   return e;
 }
 
 cudaError_t mg_set_attributes() {
-  cudaError_t e = set_smem_attr<double, SweepShape<double>::kFusedNSW, SweepShape<double>::kFusedHR>();
-  if (e == cudaSuccess) e = set_smem_attr<double, 1, SweepShape<double>::kSingleHR>();
-  if (e == cudaSuccess) e = set_smem_attr<float, SweepShape<float>::kFusedNSW, SweepShape<float>::kFusedHR>();
-  if (e == cudaSuccess) e = set_smem_attr<float, 1, SweepShape<float>::kSingleHR>();
+  using SD = SweepShape<double>;
+  using SF = SweepShape<float>;
+  cudaError_t e = set_smem_attr<double, double, SD::kFusedNSW, SD::kFusedHR>();
+  if (e == cudaSuccess) e = set_smem_attr<double, double, 1, SD::kSingleHR>();
+  if (e == cudaSuccess) e = set_smem_attr<float, float, SF::kFusedNSW, SF::kFusedHR>();
+  if (e == cudaSuccess) e = set_smem_attr<float, float, 1, SF::kSingleHR>();
+  if (e == cudaSuccess) e = set_smem_attr<float, __nv_bfloat16, SF::kFusedNSW, SF::kFusedHR>();
+  if (e == cudaSuccess) e = set_smem_attr<float, __nv_bfloat16, 1, SF::kSingleHR>();
   return e;
 }
 
-template <typename T>
-cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x) {
+// x = K b on nslices slices: n_vcycles V-cycles from x = 0.  The multigrid keeps its vectors in
+// the storage type G (T, or binary16 bfloat16 for binary32 work) and computes in T.
+template <typename T, typename G>
+cudaError_t mg_run(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x) {
   // class 0 (K_x: s = 0) has no diagonal couplings unless D has d12 != 0 or c != 0; the K_l
   // classes always do
   const bool diag = coef_class != 0 || h->diag0;
-  T* const xb[2] = {x, reinterpret_cast<T*>(h->Xalt)};
+  constexpr bool same = std::is_same<T, G>::value;
+  const size_t npts = (size_t)h->Nx * nslices;
+  // iterate buffers: the output and the alternate buffer, or (narrower storage) two halves of
+  // the alternate buffer, which holds 2 B N_t N_x doubles
+  G* const xb[2] = {same ? reinterpret_cast<G*>(x) : reinterpret_cast<G*>(h->Xalt),
+                    same ? reinterpret_cast<G*>(h->Xalt) : reinterpret_cast<G*>(h->Xalt) + npts};
   int cur = 0;
-  T* bs = reinterpret_cast<T*>(h->Bs);
+  G* bs = reinterpret_cast<G*>(h->Bs);
   const int n = h->n;
   dim3 gs((n * n + 255) / 256, nslices);
-  k_scale_rhs<T><<<gs, 256, 0, h->stream>>>(bs, b, n, coef_table<T>(h), coef_class, h->J, h->K);
+  k_scale_rhs<T, G><<<gs, 256, 0, h->stream>>>(bs, b, n, coef_table<T>(h), coef_class, h->J, h->K);
   count_launch(h);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int c = 0; c < h->cfg.n_vcycles; ++c) {
-    e = diag ? vcycle<T, true>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0)
-             : vcycle<T, false>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0);
+    e = diag ? vcycle<T, G, true>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0)
+             : vcycle<T, G, false>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0);
     if (e != cudaSuccess) return e;
   }
-  const size_t bytes = sizeof(T) * (size_t)h->Nx * nslices;
-  if (h->cfg.n_vcycles == 0) return cudaMemsetAsync(x, 0, bytes, h->stream);
+  if (h->cfg.n_vcycles == 0) return cudaMemsetAsync(x, 0, sizeof(T) * npts, h->stream);
+  if (!same) {
+    k_widen<T, G><<<(unsigned)((npts + 255) / 256), 256, 0, h->stream>>>(x, xb[cur], (int64_t)npts);
+    count_launch(h);
+    return cudaGetLastError();
+  }
   // an odd total number of sweeps leaves the iterate in the alternate buffer
-  if (cur == 1) return cudaMemcpyAsync(x, xb[1], bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (cur == 1) return cudaMemcpyAsync(x, xb[1], sizeof(T) * npts, cudaMemcpyDeviceToDevice, h->stream);
   return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x) {
+  return mg_run<T, T>(h, nslices, coef_class, b, x);
+}
+
+cudaError_t mg_apply_bf16(const st_handle_s* h, int nslices, int coef_class, const float* b, float* x) {
+  return mg_run<float, __nv_bfloat16>(h, nslices, coef_class, b, x);
 }
 
 // Times both Gauss-Seidel kernels on every level of the handle's shapes (the pre-smoothing
@@ -694,7 +712,7 @@ cudaError_t autotune_one(st_handle_s* h, int k, float* ms_tile, float* ms_wave) 
     float t = 1e30f;
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
       cudaEventRecord(e0, h->stream);
-      err = gs_sweeps<T, DIAG>(h, k, nslices, cls, xo, xi, b, nullptr, false, false, nsw);
+      err = gs_sweeps<T, T, DIAG>(h, k, nslices, cls, xo, xi, b, nullptr, false, false, nsw);
       cudaEventRecord(e1, h->stream);
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);
       float ms = 0.f;

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_add_correction(double* __restrict__ w, 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) w[i] += (double)d[i];
 }
 
-// r = f - q (binary64) and rs = r rounded to binary32
+// r = f - q (binary64) and, if rs is not null, rs = r rounded to binary32
 __global__ void __launch_bounds__(256) k_residual_split(double* __restrict__ r, float* __restrict__ rs,
                                                         const double* __restrict__ f, const double* __restrict__ q,
                                                         int64_t n) {
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_residual_split(double* __restrict__ r, 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
     const double v = f[i] - q[i];
     r[i] = v;
-    rs[i] = (float)v;
+    if (rs) rs[i] = (float)v;
   }
 }
 

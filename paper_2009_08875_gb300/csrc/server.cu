@@ -65,7 +65,8 @@ size_t group_bytes(int K, int J, int slots, int precision) {
   const double V = slots * Nt * n * n;
   double coarse = 0.0;
   for (int k = 1; k < K; ++k) coarse += 3.0 * 2.0 * slots * Nt * ((1 << k) - 1) * ((1 << k) - 1);
-  double floats = precision == ST_MIXED_PRECOND ? 2.0 : (precision == ST_MIXED_FP32 ? 5.0 : 0.0);
+  double floats = precision == ST_MIXED_PRECOND ? 2.0
+                  : ((precision == ST_MIXED_FP32 || precision == ST_MIXED_BF16) ? 5.0 : 0.0);
   return (size_t)(8.0 * (26.0 * V + coarse) + 4.0 * floats * V + 64.0 * 1024 * 1024);
 }
 

@@ -58,6 +58,20 @@ inline Stencil7<double> operator_stencil(const Phys& ph, double a, double s, dou
                           a * (ph.d12 - ph.d22) + m, -a * ph.d12 + m};
 }
 
+// Nested P1 prolongation: the value at fine grid node (i, j) (1-based grid indices, coarse grid of
+// nc x nc interior nodes stored in cs) of the coarse P1 function: the coarse value at even-even
+// nodes, the average of the two coarse end points at the midpoints of horizontal, vertical and
+// (1,1)-diagonal coarse edges; coarse boundary values are 0.  Branch-free: with (I, J) = (i >> 1,
+// j >> 1) it is the average of the coarse values at (I, J) and (I + i mod 2, J + j mod 2); at
+// even-even nodes both are the same node and the average is exact.  G is the storage type.
+template <typename T, typename G>
+__device__ __forceinline__ T prolong_value(const G* __restrict__ cs, int nc, int i, int j) {
+  const int I0 = i >> 1, J0 = j >> 1, I1 = I0 + (i & 1), J1 = J0 + (j & 1);
+  const T a = (I0 >= 1 && I0 <= nc && J0 >= 1 && J0 <= nc) ? T(cs[(J0 - 1) * nc + (I0 - 1)]) : T(0);
+  const T b = (I1 >= 1 && I1 <= nc && J1 >= 1 && J1 <= nc) ? T(cs[(J1 - 1) * nc + (I1 - 1)]) : T(0);
+  return T(0.5) * (a + b);
+}
+
 // Level |lambda| of in-place wavelet row i (rows 0 and 2^J: level 0; else J - ctz(i)).
 __host__ __device__ inline int wavelet_row_level(int i, int J) {
   if (i == 0 || i == (1 << J)) return 0;
@@ -128,6 +142,10 @@ struct st_handle_s {
   int last_iters, last_outer;
   double last_relres;
   int B;             // problems in the batch (vectors are B x N_t x N_x)
+  // PCG starts from the content of w (r = f_hat - S_hat w) instead of w = 0 (nested iteration)
+  bool use_guess;
+  // handles of the coarser meshes (K - m, J - m), m = 1.., of st_nested_solve (created on first use)
+  st_handle_s* nest[16];
   // Gauss-Seidel kernel per [element type: 0 binary64, 1 binary32][mass couplings][level]:
   // 0 shared-memory tiles (default), 1 register wavefront (chosen by st_autotune)
   unsigned char gs_kind[2][2][16];
@@ -181,6 +199,8 @@ cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, Ph
 // coef_class < 0: per-slice class 1 + level(slice) (K_X); else a fixed class.
 template <typename T>
 cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x);
+// the same in binary32 arithmetic with the multigrid's vectors stored as bfloat16
+cudaError_t mg_apply_bf16(const st_handle_s* h, int nslices, int coef_class, const float* b, float* x);
 // times both Gauss-Seidel kernels per level and records the faster in h->gs_kind; table[8 k + i]
 // receives the times (ms) of (binary64 K_x tile, wave, binary64 K_l tile, wave, binary32 ...)
 cudaError_t mg_autotune(st_handle_s* h, float* table);
@@ -220,6 +240,7 @@ cudaError_t launch_copy(const st_handle_s* h, Td* dst, const Ts* src, int64_t n)
 template <typename T>
 cudaError_t launch_zero(const st_handle_s* h, T* dst, int64_t n);
 cudaError_t launch_add_correction(const st_handle_s* h, double* w, const float* d, int64_t n);
+// r = f - q, and rs = (float) r unless rs is null
 cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, const double* f, const double* q,
                                   int64_t n);
 

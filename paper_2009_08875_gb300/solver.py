@@ -39,7 +39,7 @@ class Solver:
         cfg.alpha, cfg.n_vcycles, cfg.n_pre, cfg.n_post = alpha, n_vcycles, n_pre, n_post
         cfg.tol, cfg.tol_mode, cfg.maxit = tol, tol_mode, maxit
         cfg.precision = {"fp64": _lib.ST_FP64, "mixed": _lib.ST_MIXED_FP32,
-                         "mixed_precond": _lib.ST_MIXED_PRECOND}[precision]
+                         "mixed_precond": _lib.ST_MIXED_PRECOND, "mixed_bf16": _lib.ST_MIXED_BF16}[precision]
         cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
         cfg.use_graphs = 1 if use_graphs else 0
         _set_phys(cfg, D, c)
@@ -110,6 +110,12 @@ class Solver:
         _lib.check(_lib.load().st_apply_KX_f32(self._h, _ptr(r, self.shape, "r", dtype=torch.float32),
                                                _ptr(z, self.shape, "z", dtype=torch.float32)))
 
+    def apply_KX_bf16(self, r, z):
+        """K_X in binary32 arithmetic with bfloat16 multigrid storage (st_apply_KX_bf16)."""
+        import torch
+        _lib.check(_lib.load().st_apply_KX_bf16(self._h, _ptr(r, self.shape, "r", dtype=torch.float32),
+                                                _ptr(z, self.shape, "z", dtype=torch.float32)))
+
     def solve_info(self):
         """Iterations, refinement steps and final relative residual of the last solve."""
         out = _lib.StSolveInfo()
@@ -142,6 +148,17 @@ class Solver:
                                        _ptr(u, self.shape, "u", False), ctypes.byref(it), ctypes.byref(rr))
         _lib.check(st)
         return it.value, rr.value
+
+    def nested_solve(self, levels, eps, g, u0, w, rate=1.0):
+        """Nested iteration over (K - m, J - m), m = levels-1..0 (st_nested_solve): g, u0 nodal
+        device tensors of this handle's mesh, w receives the finest solution (wavelet order).
+        Returns (status, iterations per level, coarsest first)."""
+        its = (ctypes.c_int * levels)()
+        st = _lib.load().st_nested_solve(self._h, levels, eps, rate, _ptr(g, self.shape, "g"),
+                                         _ptr(u0, self.u0_shape, "u0"), _ptr(w, self.shape, "w"), its)
+        if st not in (0, _lib.ST_ERR_MAXIT):
+            _lib.check(st)
+        return st, list(its)
 
     def autotune(self):
         """Time both Gauss-Seidel kernels per level and keep the faster (st_autotune).
@@ -184,7 +201,7 @@ def _config(alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0, ma
     cfg.alpha, cfg.n_vcycles, cfg.n_pre, cfg.n_post = alpha, n_vcycles, n_pre, n_post
     cfg.tol, cfg.tol_mode, cfg.maxit = tol, tol_mode, maxit
     cfg.precision = {"fp64": _lib.ST_FP64, "mixed": _lib.ST_MIXED_FP32,
-                     "mixed_precond": _lib.ST_MIXED_PRECOND}[precision]
+                     "mixed_precond": _lib.ST_MIXED_PRECOND, "mixed_bf16": _lib.ST_MIXED_BF16}[precision]
     cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
     cfg.use_graphs = 1 if use_graphs else 0
     _set_phys(cfg, D, c)
