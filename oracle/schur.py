@@ -59,7 +59,7 @@ class Problem:
         self.K, self.J, self.domain, self.alpha = K, J, domain, alpha
         self.D = None if D is None else np.asarray(D, dtype=np.float64).reshape(2, 2)
         self.c = float(c)
-        self.mesh = space.Mesh(K, domain)
+        self.mesh = space.make_mesh(K, domain)
         self.Mx = space.mass_matrix(self.mesh)
         self.Ax = space.operator_matrix(self.mesh, self.D, self.c)
         tm = tmod.time_matrices(J)
@@ -234,7 +234,10 @@ def inject_nodal(fine: Problem, coarse: Problem, V):
     (N_t x N_x, or N_x): time node i of the coarse mesh is fine node 2i, space grid node (i, j)
     is fine grid node (2i, 2j)."""
     assert fine.K == coarse.K + 1 and fine.J == coarse.J + 1 and fine.domain == coarse.domain
-    fi = fine.mesh.dof[2 * coarse.mesh.node_j, 2 * coarse.mesh.node_i]
+    if fine.domain == space.CUBE:
+        fi = fine.mesh.dof[2 * coarse.mesh.node_k, 2 * coarse.mesh.node_j, 2 * coarse.mesh.node_i]
+    else:
+        fi = fine.mesh.dof[2 * coarse.mesh.node_j, 2 * coarse.mesh.node_i]
     V = np.asarray(V, dtype=np.float64)
     return V[::2][:, fi] if V.ndim == 2 else V[fi]
 
