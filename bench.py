@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solves measurement")
     ap.add_argument("--no-nested", action="store_true", help="skip the nested-iteration measurement")
+    ap.add_argument("--no-cube", action="store_true", help="skip the 3D (unit cube) measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=0.25, help="seconds of Poisson arrivals replayed")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate (requests/s)")
@@ -431,6 +432,41 @@ def run_ours(args):
                   "max_rel_error_to_exact_u": err_nested, "converged_solve_max_rel_error_to_exact_u": err_full,
                   "note": "time to discretisation accuracy: nested iteration vs PCG to relative 1e-10"}
 
+    # the 3D problem of the paper's weak-scaling table (unit cube, N_x = 250047, N_t = 513):
+    # FP64 solve to the same relative 1e-10 of u = (1 + t^2) sin sin sin
+    cube = None
+    if not args.no_cube:
+        Kc, Jc = 6, J
+        gc_np, u0c_np, _ = inputs.manufactured(Kc, Jc, inputs.CUBE)
+        cs = Solver(Kc, Jc, domain=inputs.CUBE, tol=TOL, tol_mode=0, maxit=500)
+        gc, u0c = torch.from_numpy(gc_np).cuda(), torch.from_numpy(u0c_np).cuda()
+        fc = torch.empty(cs.shape, dtype=torch.float64, device="cuda")
+        wc, uc = torch.empty_like(fc), torch.empty_like(fc)
+
+        def cstep():
+            cs.rhs(gc, u0c, fc)
+            its_c, _ = cs.pcg_solve(fc, wc)
+            cs.synthesize(wc, uc)
+            return its_c
+
+        for _ in range(max(1, args.warmup)):
+            cstep()
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        its_c = 0
+        c0.record(cs.stream)
+        for _ in range(args.steps):
+            its_c += cstep()
+        c1.record(cs.stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1)
+        cube = {"workload": f"3D heat eq., unit cube (Kuhn tetrahedra), K={Kc} (N_x={cs.Nx}), J={Jc} (N_t={cs.Nt}), "
+                            "u=(1+t^2)sin(pi x)sin(pi y)sin(pi z), PCG to rel. 1e-10",
+                "value": world * cs.Nt * cs.Nx * its_c / (cms / 1e3), "unit": "DoF-iter/s", "dtype": "f64",
+                "ms_per_solve": cms / args.steps, "pcg_iterations": its_c / args.steps}
+        cs.close()
+
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
@@ -570,6 +606,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "nested": nested,
+        "cube": cube,
         "mixed": mixed.get("mixed"),
         "mixed_bf16": mixed.get("mixed_bf16"),
         "batch": batch,

@@ -661,9 +661,11 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
                          const st_config* cfg, void* cuda_stream) {
   ST_REQUIRE(out != nullptr, "st_setup: null output pointer");
   *out = nullptr;
-  ST_REQUIRE(domain == 0 || domain == 1, "st_setup: domain must be 0 (unit square) or 1 (L-shape)");
+  ST_REQUIRE(domain == 0 || domain == 1 || domain == 2,
+             "st_setup: domain must be 0 (unit square), 1 (L-shape) or 2 (unit cube)");
+  ST_REQUIRE(domain != 2 || space_level <= 8, "st_setup: the cube needs space level <= 8");
   ST_REQUIRE(space_level >= 1 && space_level <= 12, "st_setup: space level must be in 1..12");
-  ST_REQUIRE(domain == 0 || space_level >= 2, "st_setup: the L-shape needs space level >= 2");
+  ST_REQUIRE(domain != 1 || space_level >= 2, "st_setup: the L-shape needs space level >= 2");
   ST_REQUIRE(time_level >= 1 && time_level <= 14, "st_setup: time level must be in 1..14");
   const int64_t nt = ((int64_t)1 << time_level) + 1;
   ST_REQUIRE(batch >= 1 && 2 * batch * nt <= 65535,
@@ -683,6 +685,10 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   ST_REQUIRE(c.inner_tol > 0.0 && c.inner_tol < 1.0 && c.inner_maxit >= 1,
              "st_setup: inner_tol must be in (0, 1) and inner_maxit >= 1");
   ST_REQUIRE(check_phys(c), "st_setup: D must be symmetric positive definite and c >= 0 (finite)");
+  ST_REQUIRE(domain != 2 || (c.diffusion[0] == 1.0 && c.diffusion[1] == 0.0 && c.diffusion[2] == 1.0),
+             "st_setup: the cube supports D = Id only (c >= 0 is allowed)");
+  ST_REQUIRE(domain != 2 || c.precision != ST_MIXED_BF16,
+             "st_setup: ST_MIXED_BF16 is not available on the cube");
 
   st_handle_s* h = new (std::nothrow) st_handle_s();
   if (!h) {
@@ -695,7 +701,7 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   h->J = time_level;
   h->B = batch;
   h->n = (1 << space_level) - 1;
-  h->Nx = (int64_t)h->n * h->n;
+  h->Nx = (int64_t)h->n * h->n * (domain == 2 ? h->n : 1);
   h->Nt = nt;
   h->cfg = c;
   h->phys = Phys{c.diffusion[0], c.diffusion[1], c.diffusion[2], c.reaction};
@@ -737,7 +743,8 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   for (auto& a : plan)
     if (s == ST_OK) s = alloc(a.p, a.n, a.name);
   for (int k = h->mg.kmin; k < h->K && s == ST_OK; ++k) {
-    const size_t nk = (size_t)((1 << k) - 1) * ((1 << k) - 1) * (size_t)h->mg.max_slices;
+    const size_t nkx = (size_t)((1 << k) - 1);
+    const size_t nk = nkx * nkx * (domain == 2 ? nkx : 1) * (size_t)h->mg.max_slices;
     s = alloc(&h->mg.xc[k], nk, "multigrid x");
     if (s == ST_OK) s = alloc(&h->mg.xc2[k], nk, "multigrid x (second buffer)");
     if (s == ST_OK) s = alloc(&h->mg.bc[k], nk, "multigrid b");
@@ -777,8 +784,9 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   }
   if (s == ST_OK) {
     e = mg_set_attributes();
-    if (e == cudaSuccess) e = launch_make_coef(h->coef, h->K, h->J, c.alpha, h->phys, h->stream);
-    if (e == cudaSuccess) e = launch_make_coef32(h->coef32, h->K, h->J, c.alpha, h->phys, h->stream);
+    const int dim = domain == 2 ? 3 : 2;
+    if (e == cudaSuccess) e = launch_make_coef(h->coef, h->K, h->J, c.alpha, h->phys, dim, h->stream);
+    if (e == cudaSuccess) e = launch_make_coef32(h->coef32, h->K, h->J, c.alpha, h->phys, dim, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->scal, 0, sizeof(double) * SC_COUNT * batch, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = cuda_fail("st_setup", e);
@@ -870,6 +878,7 @@ st_status st_apply_KX_f32(st_handle h, const float* r, float* z) {
 st_status st_apply_KX_bf16(st_handle h, const float* r, float* z) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(r && z, "st_apply_KX_bf16: null pointer");
+  ST_REQUIRE(h->domain != 2, "st_apply_KX_bf16: not available on the cube");
   return apply_KX_impl<float>(h, h->B, r, z, true);
 }
 

@@ -21,13 +21,35 @@ namespace {
 // coefficient table: class 0 -> (a, s) = (1, 0); class 1 + l -> (alpha, 2^l), l = 0..J, of
 // C = a A_x + s M_x with A_x = <D grad, grad> + c M_x (Sec. 4)
 // ---------------------------------------------------------------------------------------
+// In 3D (the unit cube, Kuhn tetrahedra, heat equation plus c): A_x = h [6; -1 at the axis
+// neighbours] and M_x = h^3 [2/5; 1/20 at the axis and body-diagonal, 1/30 at the face-diagonal
+// neighbours]; ax, ay, dg then hold the axis, face-diagonal and body-diagonal coefficients.
 template <typename T>
-__global__ void k_make_coef(Coef<T>* coef, int K, int J, double alpha, Phys ph) {
+__global__ void k_make_coef(Coef<T>* coef, int K, int J, double alpha, Phys ph, int dim) {
   int nclass = J + 2;
   for (int e = threadIdx.x; e < nclass * (K + 1); e += blockDim.x) {
     int cls = e / (K + 1), k = e % (K + 1);
     double a = cls == 0 ? 1.0 : alpha;
     double s = cls == 0 ? 0.0 : ldexp(1.0, cls - 1);
+    if (dim == 3) {
+      const double h = ldexp(1.0, -k), hc = ldexp(1.0, -(k - 1));
+      const double ms = (a * ph.c + s) * h * h * h, msc = (a * ph.c + s) * hc * hc * hc;
+      const double cc = 6.0 * a * h + 0.4 * ms, cc_coarse = 6.0 * a * hc + 0.4 * msc;
+      const double ax = -a * h + ms / 20.0, face = ms / 30.0, body = ms / 20.0;
+      Coef<T> c;
+      c.c = (T)cc;
+      c.ax = (T)ax;
+      c.ay = (T)face;
+      c.dg = (T)body;
+      c.inv_c = (T)(1.0 / cc);
+      c.axs = (T)(ax / cc);
+      c.ays = (T)(face / cc);
+      c.dgs = (T)(body / cc);
+      c.rho = (T)(cc / cc_coarse);
+      c.pad = T(0);
+      coef[e] = c;
+      continue;
+    }
     const double m = (a * ph.c + s) * ldexp(1.0, -2 * k) / 12.0;            // level k
     const double mc = (a * ph.c + s) * ldexp(1.0, -2 * (k - 1)) / 12.0;      // level k - 1
     const double stiff_c = a * 2.0 * (ph.d11 + ph.d22 - ph.d12);
@@ -612,13 +634,13 @@ __global__ void k_widen(T* __restrict__ x, const G* __restrict__ g, int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, Phys ph, cudaStream_t s) {
-  k_make_coef<double><<<1, 256, 0, s>>>(coef, K, J, alpha, ph);
+cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, Phys ph, int dim, cudaStream_t s) {
+  k_make_coef<double><<<1, 256, 0, s>>>(coef, K, J, alpha, ph, dim);
   return cudaGetLastError();
 }
 
-cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, Phys ph, cudaStream_t s) {
-  k_make_coef<float><<<1, 256, 0, s>>>(coef, K, J, alpha, ph);
+cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, Phys ph, int dim, cudaStream_t s) {
+  k_make_coef<float><<<1, 256, 0, s>>>(coef, K, J, alpha, ph, dim);
   return cudaGetLastError();
 }
 
@@ -684,6 +706,7 @@ cudaError_t mg_run(const st_handle_s* h, int nslices, int coef_class, const T* b
 
 template <typename T>
 cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x) {
+  if (h->domain == 2) return mg_apply3<T>(h, nslices, coef_class, b, x);
   return mg_run<T, T>(h, nslices, coef_class, b, x);
 }
 
@@ -730,6 +753,7 @@ cudaError_t autotune_one(st_handle_s* h, int k, float* ms_tile, float* ms_wave) 
 }
 
 cudaError_t mg_autotune(st_handle_s* h, float* table) {
+  if (h->domain == 2) return cudaSuccess;  // the cube has one Gauss-Seidel kernel
   const size_t bytes = sizeof(double) * 2 * (size_t)h->B * h->Nt * h->Nx;
   cudaError_t e = cudaMemsetAsync(h->Xalt, 0, bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Bs, 0, bytes, h->stream);

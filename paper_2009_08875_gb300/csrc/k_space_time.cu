@@ -8,37 +8,69 @@ namespace st {
 namespace {
 
 // ---------------------------------------------------------------------------------------
-// spatial stencils on one slice (interior index p = iy n + ix; outside the grid = 0)
-//   M_x: h^2/12 [6 at p; 1 at (+-1,0), (0,+-1), (1,1), (-1,-1)]
-//   A_x: the 7-point stencil of <D grad, grad> + c M_x (Stencil7; the heat equation's
-//        [4; -1 at (+-1,0), (0,+-1)] when D = Id, c = 0)
+// spatial stencils on one slice (outside the grid = 0), as neighbour sums (c, s1, s2, s3):
+// 2D (interior index p = iy n + ix): s1 = west + east, s2 = south + north, s3 = (1,1) + (-1,-1)
+//   M_x: h^2/12 [6 at p; 1 at the six neighbours]
+//   A_x: the 7-point stencil of <D grad, grad> + c M_x (Stencil7 over (c, s1, s2, s3); the
+//        heat equation's [4; -1 at (+-1,0), (0,+-1)] when D = Id, c = 0)
+// 3D, the unit cube with Kuhn tetrahedra (p = (iz n + iy) n + ix): s1 = the 6 axis neighbours,
+//   s2 = the 6 face-diagonal neighbours +-(1,1,0), +-(1,0,1), +-(0,1,1), s3 = the 2 body-diagonal
+//   neighbours +-(1,1,1)
+//   M_x: h^3 [2/5; 1/20 on s1, 1/30 on s2, 1/20 on s3];  A_x: h [6; -1 on s1] + c M_x
 // ---------------------------------------------------------------------------------------
 template <typename T>
-struct Nbr {
-  T c, w, e, s, nn, ne, sw;
+struct Sums {
+  T c, s1, s2, s3;
 };
 
-template <typename T>
-__device__ __forceinline__ Nbr<T> load_nbr(const T* __restrict__ u, int p, int ix, int iy, int n) {
-  Nbr<T> v;
+template <typename T, int DIM>
+__device__ __forceinline__ Sums<T> load_nbr(const T* __restrict__ u, int64_t p, int ix, int iy, int iz, int n) {
+  Sums<T> v;
   v.c = u[p];
-  v.w = ix > 0 ? u[p - 1] : T(0);
-  v.e = ix < n - 1 ? u[p + 1] : T(0);
-  v.s = iy > 0 ? u[p - n] : T(0);
-  v.nn = iy < n - 1 ? u[p + n] : T(0);
-  v.ne = (ix < n - 1 && iy < n - 1) ? u[p + n + 1] : T(0);
-  v.sw = (ix > 0 && iy > 0) ? u[p - n - 1] : T(0);
+  const bool xm = ix > 0, xp = ix < n - 1, ym = iy > 0, yp = iy < n - 1;
+  if (DIM == 2) {
+    v.s1 = (xm ? u[p - 1] : T(0)) + (xp ? u[p + 1] : T(0));
+    v.s2 = (ym ? u[p - n] : T(0)) + (yp ? u[p + n] : T(0));
+    v.s3 = ((xp && yp) ? u[p + n + 1] : T(0)) + ((xm && ym) ? u[p - n - 1] : T(0));
+  } else {
+    const int64_t nn = (int64_t)n * n;
+    const bool zm = iz > 0, zp = iz < n - 1;
+    v.s1 = ((xm ? u[p - 1] : T(0)) + (xp ? u[p + 1] : T(0))) + ((ym ? u[p - n] : T(0)) + (yp ? u[p + n] : T(0))) +
+           ((zm ? u[p - nn] : T(0)) + (zp ? u[p + nn] : T(0)));
+    v.s2 = (((xp && yp) ? u[p + 1 + n] : T(0)) + ((xm && ym) ? u[p - 1 - n] : T(0))) +
+           (((xp && zp) ? u[p + 1 + nn] : T(0)) + ((xm && zm) ? u[p - 1 - nn] : T(0))) +
+           (((yp && zp) ? u[p + n + nn] : T(0)) + ((ym && zm) ? u[p - n - nn] : T(0)));
+    v.s3 = ((xp && yp && zp) ? u[p + 1 + n + nn] : T(0)) + ((xm && ym && zm) ? u[p - 1 - n - nn] : T(0));
+  }
   return v;
 }
 
 template <typename T>
-__device__ __forceinline__ T mass_of(const Nbr<T>& v, T mh) {
-  return mh * (T(6) * v.c + (((v.w + v.e) + (v.s + v.nn)) + (v.ne + v.sw)));
+__device__ __forceinline__ T stiff_of(const Sums<T>& v, const Stencil7<T>& a) {
+  return a.c0 * v.c + a.cx * v.s1 + a.cy * v.s2 + a.cd * v.s3;
 }
 
-template <typename T>
-__device__ __forceinline__ T stiff_of(const Nbr<T>& v, const Stencil7<T>& a) {
-  return a.c0 * v.c + a.cx * (v.w + v.e) + a.cy * (v.s + v.nn) + a.cd * (v.ne + v.sw);
+// mass stencil sm: 2D passes (6 mh, mh, mh, mh) and uses mh (6 c + ((s1 + s2) + s3)); 3D the
+// general form
+template <typename T, int DIM>
+__device__ __forceinline__ T mass_of(const Sums<T>& v, const Stencil7<T>& sm) {
+  if (DIM == 2) return sm.cx * (T(6) * v.c + ((v.s1 + v.s2) + v.s3));
+  return stiff_of(v, sm);
+}
+
+// grid coordinates of interior index p
+template <int DIM>
+__device__ __forceinline__ void coords_of(int64_t p, int n, int& ix, int& iy, int& iz) {
+  if (DIM == 2) {
+    iy = (int)(p / n);
+    ix = (int)(p - (int64_t)iy * n);
+    iz = 0;
+  } else {
+    const int64_t r = p / n;
+    ix = (int)(p - r * n);
+    iz = (int)(r / n);
+    iy = (int)(r - (int64_t)iz * n);
+  }
 }
 
 // tridiagonal time matrices on the uniform P1 mesh (h = 2^-J), row i of N_t:
@@ -87,19 +119,20 @@ __device__ __forceinline__ T tri_dot(const Tri<T>& t, T a, T b, T c) {
 // mode 1 (rhs): Y1 = L^T (G M),             Y2 = M_t (G M)
 // One thread per spatial point walks a chunk of time rows, keeping the stencil results of
 // rows i-1, i, i+1 in registers (the chunk edges recompute one halo row).
-template <typename T>
+template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __restrict__ Y1, T* __restrict__ Y2,
-                                                 int n, int Nt, int chunk, T mh, Stencil7<T> sa,
+                                                 int n, int Nt, int chunk, Stencil7<T> sm, Stencil7<T> sa,
                                                  TimeConsts<T> tk, int mode, int lshape) {
-  const int N = n * n;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t N = DIM == 2 ? (int64_t)n * n : (int64_t)n * n * n;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= N) return;
   const int64_t poff = (int64_t)blockIdx.z * Nt * N;  // problem blockIdx.z of the batch
   U += poff;
   Y1 += poff;
   Y2 += poff;
-  const int iy = p / n, ix = p - iy * n;
-  if (outside_domain(ix, iy, n, lshape)) {  // nodes outside the domain stay zero
+  int ix, iy, iz;
+  coords_of<DIM>(p, n, ix, iy, iz);
+  if (DIM == 2 && outside_domain(ix, iy, n, lshape)) {  // nodes outside the domain stay zero
     const int i0 = blockIdx.y * chunk, i1 = min(Nt, i0 + chunk);
     for (int i = i0; i < i1; ++i) {
       Y1[(int64_t)i * N + p] = T(0);
@@ -111,19 +144,19 @@ __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __r
   const int i1 = min(Nt, i0 + chunk);
   T um_m = T(0), ua_m = T(0), um_c, ua_c, um_p = T(0), ua_p = T(0);
   if (i0 > 0) {
-    Nbr<T> v = load_nbr(U + (int64_t)(i0 - 1) * N, p, ix, iy, n);
-    um_m = mass_of(v, mh);
+    Sums<T> v = load_nbr<T, DIM>(U + (int64_t)(i0 - 1) * N, p, ix, iy, iz, n);
+    um_m = mass_of<T, DIM>(v, sm);
     ua_m = stiff_of(v, sa);
   }
   {
-    Nbr<T> v = load_nbr(U + (int64_t)i0 * N, p, ix, iy, n);
-    um_c = mass_of(v, mh);
+    Sums<T> v = load_nbr<T, DIM>(U + (int64_t)i0 * N, p, ix, iy, iz, n);
+    um_c = mass_of<T, DIM>(v, sm);
     ua_c = stiff_of(v, sa);
   }
   for (int i = i0; i < i1; ++i) {
     if (i + 1 < Nt) {
-      Nbr<T> v = load_nbr(U + (int64_t)(i + 1) * N, p, ix, iy, n);
-      um_p = mass_of(v, mh);
+      Sums<T> v = load_nbr<T, DIM>(U + (int64_t)(i + 1) * N, p, ix, iy, iz, n);
+      um_p = mass_of<T, DIM>(v, sm);
       ua_p = mode == 0 ? stiff_of(v, sa) : T(0);
     } else {
       um_p = T(0);
@@ -147,12 +180,12 @@ __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __r
 }
 
 // Z_i = M X1_i + A X2_i (+ M row0 on row 0): the Schur epilogue (K_x already applied)
-template <typename T>
+template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_epilogue(const T* __restrict__ X1, const T* __restrict__ X2,
                                                   const T* __restrict__ row0, int64_t row0_stride, T* __restrict__ Z,
-                                                  int n, int Nt, T mh, Stencil7<T> sa, int lshape) {
-  const int N = n * n;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+                                                  int n, int Nt, Stencil7<T> sm, Stencil7<T> sa, int lshape) {
+  const int64_t N = DIM == 2 ? (int64_t)n * n : (int64_t)n * n * n;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= N) return;
   const int i = blockIdx.y;
   const int64_t poff = (int64_t)blockIdx.z * Nt * N;  // problem blockIdx.z of the batch
@@ -160,26 +193,31 @@ __global__ void __launch_bounds__(256) k_epilogue(const T* __restrict__ X1, cons
   X2 += poff;
   Z += poff;
   if (row0 != nullptr) row0 += blockIdx.z * row0_stride;
-  const int iy = p / n, ix = p - iy * n;
+  int ix, iy, iz;
+  coords_of<DIM>(p, n, ix, iy, iz);
   const int64_t off = (int64_t)i * N;
-  if (outside_domain(ix, iy, n, lshape)) {
+  if (DIM == 2 && outside_domain(ix, iy, n, lshape)) {
     Z[off + p] = T(0);
     return;
   }
-  T z = mass_of(load_nbr(X1 + off, p, ix, iy, n), mh) + stiff_of(load_nbr(X2 + off, p, ix, iy, n), sa);
-  if (i == 0 && row0 != nullptr) z += mass_of(load_nbr(row0, p, ix, iy, n), mh);
+  T z = mass_of<T, DIM>(load_nbr<T, DIM>(X1 + off, p, ix, iy, iz, n), sm) +
+        stiff_of(load_nbr<T, DIM>(X2 + off, p, ix, iy, iz, n), sa);
+  if (i == 0 && row0 != nullptr) z += mass_of<T, DIM>(load_nbr<T, DIM>(row0, p, ix, iy, iz, n), sm);
   Z[off + p] = z;
 }
 
-template <typename T>
+template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_apply_A(const T* __restrict__ X, T* __restrict__ Y, int n, Stencil7<T> sa,
                                                  int lshape) {
-  const int N = n * n;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t N = DIM == 2 ? (int64_t)n * n : (int64_t)n * n * n;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= N) return;
-  const int iy = p / n, ix = p - iy * n;
+  int ix, iy, iz;
+  coords_of<DIM>(p, n, ix, iy, iz);
   const int64_t off = (int64_t)blockIdx.y * N;
-  Y[off + p] = outside_domain(ix, iy, n, lshape) ? T(0) : stiff_of(load_nbr(X + off, p, ix, iy, n), sa);
+  Y[off + p] = (DIM == 2 && outside_domain(ix, iy, n, lshape))
+                   ? T(0)
+                   : stiff_of(load_nbr<T, DIM>(X + off, p, ix, iy, iz, n), sa);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -241,11 +279,27 @@ __global__ void k_wanal(const T* __restrict__ Xf, T* C, T* D, int64_t Nx, int j,
   }
 }
 
-// A_x on the finest level of the handle, in element type T
+// A_x and M_x on the finest level of the handle, in element type T (the cube: Kuhn tetrahedra)
 template <typename T>
 Stencil7<T> fine_A(const st_handle_s* h) {
-  const Stencil7<double> a = operator_stencil(h->phys, 1.0, 0.0, ldexp(1.0, -h->K));
+  const double hx = ldexp(1.0, -h->K);
+  if (h->domain == 2) {
+    const double m = h->phys.c * hx * hx * hx;
+    return Stencil7<T>{(T)(6.0 * hx + 0.4 * m), (T)(-hx + m / 20.0), (T)(m / 30.0), (T)(m / 20.0)};
+  }
+  const Stencil7<double> a = operator_stencil(h->phys, 1.0, 0.0, hx);
   return Stencil7<T>{(T)a.c0, (T)a.cx, (T)a.cy, (T)a.cd};
+}
+
+template <typename T>
+Stencil7<T> fine_M(const st_handle_s* h) {
+  const double hx = ldexp(1.0, -h->K);
+  if (h->domain == 2) {
+    const double h3 = hx * hx * hx;
+    return Stencil7<T>{(T)(0.4 * h3), (T)(h3 / 20.0), (T)(h3 / 30.0), (T)(h3 / 20.0)};
+  }
+  const T mh = (T)(hx * hx / 12.0);  // 2D: mass_of uses mh (6 c + (s1 + s2 + s3))
+  return Stencil7<T>{T(6) * mh, mh, mh, mh};
 }
 
 template <typename T>
@@ -259,13 +313,15 @@ TimeConsts<T> time_consts(int J) {
 template <typename T>
 cudaError_t launch_timemix(const st_handle_s* h, int nb, int mode, const T* U, T* Y) {
   const int n = h->n;
-  const int N = n * n;
+  const int64_t N = h->Nx;
   const int chunk = 32;
-  dim3 grid((N + 255) / 256, (int)((h->Nt + chunk - 1) / chunk), nb);
-  const double hx = ldexp(1.0, -h->K);
-  k_timemix<T><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, chunk,
-                                            (T)(hx * hx / 12.0), fine_A<T>(h),
-                                            time_consts<T>(h->J), mode, h->domain);
+  dim3 grid((unsigned)((N + 255) / 256), (int)((h->Nt + chunk - 1) / chunk), nb);
+  if (h->domain == 2)
+    k_timemix<T, 3><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, chunk, fine_M<T>(h),
+                                                 fine_A<T>(h), time_consts<T>(h->J), mode, 0);
+  else
+    k_timemix<T, 2><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, chunk, fine_M<T>(h),
+                                                 fine_A<T>(h), time_consts<T>(h->J), mode, h->domain);
   count_launch(h);
   return cudaGetLastError();
 }
@@ -273,11 +329,14 @@ cudaError_t launch_timemix(const st_handle_s* h, int nb, int mode, const T* U, T
 template <typename T>
 cudaError_t launch_epilogue(const st_handle_s* h, int nb, const T* X, const T* row0, int64_t row0_stride, T* Z) {
   const int n = h->n;
-  const int N = n * n;
-  dim3 grid((N + 255) / 256, (int)h->Nt, nb);
-  const double hx = ldexp(1.0, -h->K);
-  k_epilogue<T><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt,
-                                             (T)(hx * hx / 12.0), fine_A<T>(h), h->domain);
+  const int64_t N = h->Nx;
+  dim3 grid((unsigned)((N + 255) / 256), (int)h->Nt, nb);
+  if (h->domain == 2)
+    k_epilogue<T, 3><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt,
+                                                  fine_M<T>(h), fine_A<T>(h), 0);
+  else
+    k_epilogue<T, 2><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt,
+                                                  fine_M<T>(h), fine_A<T>(h), h->domain);
   count_launch(h);
   return cudaGetLastError();
 }
@@ -285,9 +344,12 @@ cudaError_t launch_epilogue(const st_handle_s* h, int nb, const T* X, const T* r
 template <typename T>
 cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y) {
   const int n = h->n;
-  const int N = n * n;
-  dim3 grid((N + 255) / 256, nrows);
-  k_apply_A<T><<<grid, 256, 0, h->stream>>>(X, Y, n, fine_A<T>(h), h->domain);
+  const int64_t N = h->Nx;
+  dim3 grid((unsigned)((N + 255) / 256), nrows);
+  if (h->domain == 2)
+    k_apply_A<T, 3><<<grid, 256, 0, h->stream>>>(X, Y, n, fine_A<T>(h), 0);
+  else
+    k_apply_A<T, 2><<<grid, 256, 0, h->stream>>>(X, Y, n, fine_A<T>(h), h->domain);
   count_launch(h);
   return cudaGetLastError();
 }

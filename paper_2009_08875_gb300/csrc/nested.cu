@@ -41,8 +41,40 @@ __global__ void __launch_bounds__(256) k_prolong_w(double* __restrict__ wf, cons
   wf[(b * ntf + i) * nf * nf + p] = v;
 }
 
+// the cube: coarse (b, t, z, y, x) = fine (b, tstep t, 2z + 1, 2y + 1, 2x + 1)
+__global__ void __launch_bounds__(256) k_inject3(double* __restrict__ c, const double* __restrict__ f, int nc, int nf,
+                                                 int64_t ntc, int64_t ntf, int tstep) {
+  const int64_t Nc = (int64_t)nc * nc * nc;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= Nc) return;
+  const int ix = (int)(p % nc), iy = (int)((p / nc) % nc), iz = (int)(p / ((int64_t)nc * nc));
+  const int64_t t = blockIdx.y, b = blockIdx.z;
+  const int64_t Nf = (int64_t)nf * nf * nf;
+  c[(b * ntc + t) * Nc + p] =
+      f[(b * ntf + t * tstep) * Nf + ((int64_t)(2 * iz + 1) * nf + (2 * iy + 1)) * nf + 2 * ix + 1];
+}
+
+__global__ void __launch_bounds__(256) k_prolong_w3(double* __restrict__ wf, const double* __restrict__ wc, int nf,
+                                                    int nc, int64_t ntf, int64_t ntc) {
+  const int64_t Nf = (int64_t)nf * nf * nf;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= Nf) return;
+  const int ix = (int)(p % nf), iy = (int)((p / nf) % nf), iz = (int)(p / ((int64_t)nf * nf));
+  const int64_t i = blockIdx.y, b = blockIdx.z;
+  double v = 0.0;
+  if (!(i & 1)) v = prolong_value3<double>(wc + (b * ntc + i / 2) * nc * nc * nc, nc, ix + 1, iy + 1, iz + 1);
+  wf[(b * ntf + i) * Nf + p] = v;
+}
+
 cudaError_t inject(const st_handle_s* fine, const st_handle_s* coarse, const double* f, double* c, bool time) {
   const int nc = coarse->n, nf = fine->n;
+  if (fine->domain == 2) {
+    const int64_t ntc = time ? coarse->Nt : 1, ntf = time ? fine->Nt : 1;
+    dim3 grid((unsigned)((coarse->Nx + 255) / 256), (unsigned)ntc, fine->B);
+    k_inject3<<<grid, 256, 0, fine->stream>>>(c, f, nc, nf, ntc, ntf, time ? 2 : 0);
+    count_launch(fine);
+    return cudaGetLastError();
+  }
   const int64_t ntc = time ? coarse->Nt : 1, ntf = time ? fine->Nt : 1;
   dim3 grid((nc * nc + 255) / 256, (unsigned)ntc, fine->B);
   k_inject<<<grid, 256, 0, fine->stream>>>(c, f, nc, nf, ntc, ntf, time ? 2 : 0);
@@ -52,6 +84,12 @@ cudaError_t inject(const st_handle_s* fine, const st_handle_s* coarse, const dou
 
 cudaError_t prolong_w(const st_handle_s* coarse, const st_handle_s* fine, const double* wc, double* wf) {
   const int nf = fine->n;
+  if (fine->domain == 2) {
+    dim3 grid((unsigned)((fine->Nx + 255) / 256), (unsigned)fine->Nt, fine->B);
+    k_prolong_w3<<<grid, 256, 0, fine->stream>>>(wf, wc, nf, coarse->n, fine->Nt, coarse->Nt);
+    count_launch(fine);
+    return cudaGetLastError();
+  }
   dim3 grid((nf * nf + 255) / 256, (unsigned)fine->Nt, fine->B);
   k_prolong_w<<<grid, 256, 0, fine->stream>>>(wf, wc, nf, coarse->n, fine->Nt, coarse->Nt, fine->domain);
   count_launch(fine);

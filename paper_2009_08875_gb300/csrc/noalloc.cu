@@ -122,7 +122,7 @@ extern "C" st_status st_apply_Kx_static(int space_level, int nslices, const doub
   // Nothing in the scratch has to start at zero: every call rewrites the coefficient table, and
   // every multigrid buffer is written before it is read within the call (each coarse level, and
   // the finest level in the first cycle, start from x = 0 without reading the iterate buffer).
-  e = launch_make_coef(h.coef, h.K, h.J, h.cfg.alpha, h.phys, h.stream);
+  e = launch_make_coef(h.coef, h.K, h.J, h.cfg.alpha, h.phys, 2, h.stream);
   if (e != cudaSuccess) return cuda_fail("st_apply_Kx_static: coefficient table", e);
   e = mg_apply(&h, nslices, 0, b, x);
   if (e != cudaSuccess) return cuda_fail("st_apply_Kx_static: multigrid", e);

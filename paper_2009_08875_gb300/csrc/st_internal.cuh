@@ -72,6 +72,24 @@ __device__ __forceinline__ T prolong_value(const G* __restrict__ cs, int nc, int
   return T(0.5) * (a + b);
 }
 
+// The same on the unit cube's Kuhn mesh (nc^3 coarse interior nodes): the fine node (i, j, k)
+// (1-based) takes the average of the coarse values at (i >> 1, j >> 1, k >> 1) and
+// (i >> 1 + i mod 2, ...), the end points of the coarse edge (axis, face diagonal or body
+// diagonal) whose midpoint it is; the same node at even-even-even nodes.
+template <typename T>
+__device__ __forceinline__ T prolong_value3(const T* __restrict__ cs, int nc, int i, int j, int k) {
+  const int I0 = i >> 1, J0 = j >> 1, L0 = k >> 1;
+  const int I1 = I0 + (i & 1), J1 = J0 + (j & 1), L1 = L0 + (k & 1);
+  const int64_t nn = (int64_t)nc * nc;
+  const T a = (I0 >= 1 && I0 <= nc && J0 >= 1 && J0 <= nc && L0 >= 1 && L0 <= nc)
+                  ? cs[(L0 - 1) * nn + (int64_t)(J0 - 1) * nc + (I0 - 1)]
+                  : T(0);
+  const T c = (I1 >= 1 && I1 <= nc && J1 >= 1 && J1 <= nc && L1 >= 1 && L1 <= nc)
+                  ? cs[(L1 - 1) * nn + (int64_t)(J1 - 1) * nc + (I1 - 1)]
+                  : T(0);
+  return T(0.5) * (a + c);
+}
+
 // Level |lambda| of in-place wavelet row i (rows 0 and 2^J: level 0; else J - ctz(i)).
 __host__ __device__ inline int wavelet_row_level(int i, int J) {
   if (i == 0 || i == (1 << J)) return 0;
@@ -189,8 +207,8 @@ st_status cuda_fail(const char* where, cudaError_t e);
 // ---------------------------------------------------------------------------------------
 // launchers (all enqueue on `s`; return cudaGetLastError())
 // ---------------------------------------------------------------------------------------
-cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, Phys ph, cudaStream_t s);
-cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, Phys ph, cudaStream_t s);
+cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, Phys ph, int dim, cudaStream_t s);
+cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, Phys ph, int dim, cudaStream_t s);
 
 // The operator launchers below are instantiated for T = double and T = float; the float
 // versions reuse the handle's double workspace (half of each buffer).
@@ -199,6 +217,9 @@ cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, Ph
 // coef_class < 0: per-slice class 1 + level(slice) (K_X); else a fixed class.
 template <typename T>
 cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x);
+// the unit cube's multigrid (domain 2)
+template <typename T>
+cudaError_t mg_apply3(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x);
 // the same in binary32 arithmetic with the multigrid's vectors stored as bfloat16
 cudaError_t mg_apply_bf16(const st_handle_s* h, int nslices, int coef_class, const float* b, float* x);
 // times both Gauss-Seidel kernels per level and records the faster in h->gs_kind; table[8 k + i]

@@ -63,7 +63,8 @@ def test_setup_rejects_non_spd_D_or_negative_c_without_gpu(d11, d12, d22, c):
     assert "positive definite" in lib.st_last_error().decode()
 
 
-@pytest.mark.parametrize("domain,K,J", [(2, 3, 3), (1, 1, 3), (0, 0, 3), (0, 13, 3), (0, 3, 0), (0, 3, 15)])
+@pytest.mark.parametrize("domain,K,J", [(3, 3, 3), (1, 1, 3), (0, 0, 3), (0, 13, 3), (0, 3, 0), (0, 3, 15),
+                                        (2, 9, 3), (2, 0, 3)])
 def test_setup_rejects_bad_sizes_without_gpu(domain, K, J):
     lib = lib_or_skip()
     h = ctypes.c_void_p()
@@ -71,6 +72,20 @@ def test_setup_rejects_bad_sizes_without_gpu(domain, K, J):
     assert st == _lib.ST_ERR_ARG
     assert h.value is None
     assert lib.st_last_error().decode().startswith("st_setup")
+
+
+@pytest.mark.parametrize("field,value", [("diffusion", (2.0, 0.0, 2.0)), ("precision", 3)])
+def test_cube_rejects_unsupported_settings_without_gpu(field, value):
+    lib = lib_or_skip()
+    cfg = _lib.StConfig()
+    lib.st_default_config(ctypes.byref(cfg))
+    if field == "diffusion":
+        cfg.diffusion[0], cfg.diffusion[1], cfg.diffusion[2] = value
+    else:
+        cfg.precision = value
+    h = ctypes.c_void_p()
+    assert lib.st_setup(ctypes.byref(h), 2, 3, 3, ctypes.byref(cfg), None) == _lib.ST_ERR_ARG
+    assert h.value is None
 
 
 def test_null_handle_is_an_argument_error():
