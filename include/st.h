@@ -102,12 +102,17 @@ typedef struct {
  * D = Id, c = 0 (the heat equation of Sec. 5). */
 void st_default_config(st_config* cfg);
 
-/* Creates a handle for `domain` (0 unit square, 1 L-shape) at space level K (1..12; 2..12 for
- * the L-shape) and time level J (1..14), binds it to `cuda_stream` (a cudaStream_t; NULL =
- * legacy default stream) and allocates its device workspace (about 26 vectors of N_t x N_x
- * doubles) on the current device.  The multigrid's coarsest level is 1 (one unknown) on the
- * square and 2 (five unknowns, dense solve) on the L-shape.  cfg may be NULL (defaults).
- * Synchronous. */
+/* Creates a handle for `domain` at space level K and time level J (1..14), binds it to
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream) and allocates its device
+ * workspace (about 26 vectors of N_t x N_x doubles) on the current device.  Domains:
+ *   0  unit square, K in 1..12, N_x = (2^K - 1)^2 (Sec. 5.1);
+ *   1  L-shape (0,1)^2 minus [1/2,1)^2 stored on the square's grid with zeros outside,
+ *      K in 2..12;
+ *   2  unit cube, K in 1..8, N_x = (2^K - 1)^3, P1 on the six Kuhn tetrahedra of every grid
+ *      cube (the 3D problem of Sec. 5.2); D = Id only, c >= 0; not ST_MIXED_BF16;
+ *      the column index is (iz (2^K - 1) + iy) (2^K - 1) + ix.
+ * The multigrid's coarsest level is 1 (one unknown) on the square and the cube and 2 (five
+ * unknowns, dense solve) on the L-shape.  cfg may be NULL (defaults).  Synchronous. */
 st_status st_setup(st_handle* out, int domain, int space_level, int time_level,
                    const st_config* cfg, void* cuda_stream);
 
