@@ -54,7 +54,9 @@ typedef enum {
   ST_ERR_NOMEM = 2,      /* device workspace allocation failed                          */
   ST_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed                 */
   ST_ERR_BREAKDOWN = 4,  /* PCG breakdown: p^T S_hat p <= 0 or a non-finite scalar      */
-  ST_ERR_MAXIT = 5       /* PCG stopped at maxit before reaching the tolerance          */
+  ST_ERR_MAXIT = 5,      /* PCG stopped at maxit before reaching the tolerance          */
+  ST_ERR_TIMEOUT = 6,    /* a served request passed its deadline before it finished      */
+  ST_ERR_CANCELLED = 7   /* a served request was cancelled (st_server_cancel)            */
 } st_status;
 
 typedef enum {
@@ -266,10 +268,22 @@ st_status st_server_start(st_server* out, const st_config* cfg, int slots_per_gr
 st_status st_server_submit(st_server s, int domain, int space_level, int time_level, const double* g_host,
                            const double* u0_host, double* u_host, int64_t* ticket);
 
-/* State of a request: *state 0 queued, 1 running, 2 done, 3 failed (info->relres and
- * iterations describe the solve; a request that cannot fit in the budget fails).
+/* The same with a deadline timeout_s seconds after submission (<= 0 or infinite: none).  A
+ * request that has not finished by then fails with ST_ERR_TIMEOUT: before it starts, or at the
+ * next iteration boundary while it runs (u_host is then not written). */
+st_status st_server_submit_deadline(st_server s, int domain, int space_level, int time_level, const double* g_host,
+                                    const double* u0_host, double* u_host, double timeout_s, int64_t* ticket);
+
+/* Cancels a queued or running request: it fails with ST_ERR_CANCELLED before it starts or at the
+ * next iteration boundary (u_host is not written).  No effect on a finished request. */
+st_status st_server_cancel(st_server s, int64_t ticket);
+
+/* State of a request: *state 0 queued, 1 running, 2 done, 3 failed; *status (may be NULL) its
+ * st_status (ST_ERR_NOMEM: it cannot fit in the budget; ST_ERR_MAXIT, ST_ERR_BREAKDOWN,
+ * ST_ERR_TIMEOUT, ST_ERR_CANCELLED); info->relres and iterations describe the solve.
  * *latency_s (may be NULL): seconds from submission to completion, or -1 if not finished. */
-st_status st_server_poll(st_server s, int64_t ticket, int* state, st_solve_info* info, double* latency_s);
+st_status st_server_poll(st_server s, int64_t ticket, int* state, int* status, st_solve_info* info,
+                         double* latency_s);
 
 /* Serves every submitted request, stops the worker and frees all device memory. */
 st_status st_server_stop(st_server s);

@@ -9,9 +9,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libst.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "st.h")
 
-ST_OK, ST_ERR_ARG, ST_ERR_NOMEM, ST_ERR_CUDA, ST_ERR_BREAKDOWN, ST_ERR_MAXIT = range(6)
+ST_OK, ST_ERR_ARG, ST_ERR_NOMEM, ST_ERR_CUDA, ST_ERR_BREAKDOWN, ST_ERR_MAXIT, ST_ERR_TIMEOUT, ST_ERR_CANCELLED = range(8)
 STATUS_NAMES = {0: "ST_OK", 1: "ST_ERR_ARG", 2: "ST_ERR_NOMEM", 3: "ST_ERR_CUDA", 4: "ST_ERR_BREAKDOWN",
-                5: "ST_ERR_MAXIT"}
+                5: "ST_ERR_MAXIT", 6: "ST_ERR_TIMEOUT", 7: "ST_ERR_CANCELLED"}
 
 
 class StConfig(ctypes.Structure):
@@ -87,8 +87,11 @@ _SIGS = {
     "st_server_start": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(StConfig), ctypes.c_int, ctypes.c_double]),
     "st_server_submit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                         ctypes.POINTER(ctypes.c_int64)]),
-    "st_server_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(StSolveInfo),
-                                      ctypes.POINTER(ctypes.c_double)]),
+    "st_server_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(StSolveInfo), ctypes.POINTER(ctypes.c_double)]),
+    "st_server_submit_deadline": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                                 ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
+    "st_server_cancel": (ctypes.c_int, [_P, ctypes.c_int64]),
     "st_server_stop": (ctypes.c_int, [_P]),
     "st_last_error": (ctypes.c_char_p, []),
 }

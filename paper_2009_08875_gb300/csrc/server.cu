@@ -42,6 +42,9 @@ struct Request {
   const double* u0;
   double* u;
   Clock::time_point submitted, started, finished;
+  Clock::time_point deadline;  // meaningful if has_deadline
+  bool has_deadline = false;
+  bool cancel = false;         // set by st_server_cancel (under the server mutex)
   int state = REQ_QUEUED;
   st_solve_info info{};
   int status = ST_OK;
@@ -184,6 +187,18 @@ void worker_loop(st_server_s* s) {
         waiting.push_back(s->queue.front());
         s->queue.pop_front();
       }
+      // requests not yet started that were cancelled or are past their deadline
+      const Clock::time_point now = Clock::now();
+      for (auto it = waiting.begin(); it != waiting.end();) {
+        Request* r = *it;
+        if (r->cancel || (r->has_deadline && now >= r->deadline)) {
+          r->status = r->cancel ? ST_ERR_CANCELLED : ST_ERR_TIMEOUT;
+          finish_request(r, REQ_FAILED);
+          it = waiting.erase(it);
+        } else {
+          ++it;
+        }
+      }
       busy = !waiting.empty();
       for (auto& g : s->groups) busy = busy || !group_idle(g.get());
       if (s->stopping && !busy) return;
@@ -254,11 +269,26 @@ void worker_loop(st_server_s* s) {
       if (e != cudaSuccess) return fail_server(s, cuda_fail("stream synchronize", e), "iteration");
       bool changed = false;
       std::vector<int> done;
+      std::vector<char> stop(g->slots, 0);  // 1 cancelled, 2 past the deadline
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        const Clock::time_point now = Clock::now();
+        for (int b = 0; b < g->slots; ++b)
+          if (g->slot[b]) stop[b] = g->slot[b]->cancel ? 1 : ((g->slot[b]->has_deadline && now >= g->slot[b]->deadline) ? 2 : 0);
+      }
       for (int b = 0; b < g->slots; ++b) {
         Request* r = g->slot[b];
         if (!r) continue;
         const double* sc = h->scal_host + (size_t)b * SC_COUNT;
         const int it = ++h->info_iters[b];
+        if (stop[b]) {  // leaves at this iteration boundary without a result
+          r->info.iterations = it;
+          r->status = stop[b] == 1 ? ST_ERR_CANCELLED : ST_ERR_TIMEOUT;
+          h->act_host[b] = 0;
+          changed = true;
+          done.push_back(b);
+          continue;
+        }
         const double rho0 = sc[SC_RHO0], rho = sc[SC_RHO_NEW], pq = sc[SC_PQ];
         int status = ST_OK;
         bool fin = false;
@@ -347,10 +377,14 @@ st_status st_server_start(st_server* out, const st_config* cfg, int slots_per_gr
   return ST_OK;
 }
 
-st_status st_server_submit(st_server s, int domain, int space_level, int time_level, const double* g_host,
-                           const double* u0_host, double* u_host, int64_t* ticket) {
+st_status st_server_submit_deadline(st_server s, int domain, int space_level, int time_level, const double* g_host,
+                                    const double* u0_host, double* u_host, double timeout_s, int64_t* ticket) {
   if (!s || !g_host || !u0_host || !u_host) {
     set_error("st_server_submit: null pointer");
+    return ST_ERR_ARG;
+  }
+  if (std::isnan(timeout_s)) {
+    set_error("st_server_submit: timeout must not be NaN");
     return ST_ERR_ARG;
   }
   if ((domain != 0 && domain != 1) || space_level < 1 || space_level > 12 || (domain == 1 && space_level < 2) ||
@@ -366,6 +400,10 @@ st_status st_server_submit(st_server s, int domain, int space_level, int time_le
   r->u0 = u0_host;
   r->u = u_host;
   r->submitted = Clock::now();
+  if (timeout_s > 0.0 && std::isfinite(timeout_s)) {
+    r->has_deadline = true;
+    r->deadline = r->submitted + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+  }
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->error != ST_OK) {
     set_error("st_server_submit: the server stopped after an error: " + s->error_msg);
@@ -383,7 +421,31 @@ st_status st_server_submit(st_server s, int domain, int space_level, int time_le
   return ST_OK;
 }
 
-st_status st_server_poll(st_server s, int64_t ticket, int* state, st_solve_info* info, double* latency_s) {
+st_status st_server_submit(st_server s, int domain, int space_level, int time_level, const double* g_host,
+                           const double* u0_host, double* u_host, int64_t* ticket) {
+  return st_server_submit_deadline(s, domain, space_level, time_level, g_host, u0_host, u_host, 0.0, ticket);
+}
+
+st_status st_server_cancel(st_server s, int64_t ticket) {
+  if (!s) {
+    set_error("st_server_cancel: null server");
+    return ST_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (ticket < 0 || ticket >= (int64_t)s->all.size()) {
+    set_error("st_server_cancel: unknown ticket");
+    return ST_ERR_ARG;
+  }
+  Request* r = s->all[ticket].get();
+  if (r->state < REQ_DONE) {
+    r->cancel = true;
+    s->cv.notify_one();
+  }
+  return ST_OK;
+}
+
+st_status st_server_poll(st_server s, int64_t ticket, int* state, int* status, st_solve_info* info,
+                         double* latency_s) {
   if (!s || !state) {
     set_error("st_server_poll: null pointer");
     return ST_ERR_ARG;
@@ -395,6 +457,7 @@ st_status st_server_poll(st_server s, int64_t ticket, int* state, st_solve_info*
   }
   const Request* r = s->all[ticket].get();
   *state = r->state;
+  if (status) *status = r->status;
   if (info) *info = r->info;
   if (latency_s)
     *latency_s = (r->state >= REQ_DONE) ? std::chrono::duration<double>(r->finished - r->submitted).count() : -1.0;

@@ -273,23 +273,29 @@ class Server:
         self._h = h
         self._keep = {}
 
-    def submit(self, domain, K, J, g, u0, u):
+    def submit(self, domain, K, J, g, u0, u, timeout=None):
+        """Queue a solve; with timeout (seconds) it fails with ST_ERR_TIMEOUT if not done by then."""
         n = 2 ** K - 1
         Nt, Nx = 2 ** J + 1, n * n
         t = ctypes.c_int64()
-        _lib.check(_lib.load().st_server_submit(self._h, domain, K, J, _ptr(g, (Nt, Nx), "g", False),
-                                                _ptr(u0, (Nx,), "u0", False), _ptr(u, (Nt, Nx), "u", False),
-                                                ctypes.byref(t)))
+        _lib.check(_lib.load().st_server_submit_deadline(self._h, domain, K, J, _ptr(g, (Nt, Nx), "g", False),
+                                                         _ptr(u0, (Nx,), "u0", False),
+                                                         _ptr(u, (Nt, Nx), "u", False),
+                                                         float(timeout) if timeout else 0.0, ctypes.byref(t)))
         self._keep[t.value] = (g, u0, u)
         return t.value
 
+    def cancel(self, ticket):
+        _lib.check(_lib.load().st_server_cancel(self._h, ticket))
+
     def poll(self, ticket):
-        st, info, lat = ctypes.c_int(), _lib.StSolveInfo(), ctypes.c_double()
-        _lib.check(_lib.load().st_server_poll(self._h, ticket, ctypes.byref(st), ctypes.byref(info),
-                                              ctypes.byref(lat)))
+        st, status, info, lat = ctypes.c_int(), ctypes.c_int(), _lib.StSolveInfo(), ctypes.c_double()
+        _lib.check(_lib.load().st_server_poll(self._h, ticket, ctypes.byref(st), ctypes.byref(status),
+                                              ctypes.byref(info), ctypes.byref(lat)))
         if st.value >= self.DONE:
             self._keep.pop(ticket, None)
-        return {"state": st.value, "iterations": info.iterations, "relres": info.relres, "latency_s": lat.value}
+        return {"state": st.value, "status": status.value, "iterations": info.iterations, "relres": info.relres,
+                "latency_s": lat.value}
 
     def stop(self):
         if getattr(self, "_h", None):

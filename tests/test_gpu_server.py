@@ -88,3 +88,30 @@ def test_server_rejects_a_request_larger_than_the_budget():
     res = wait_all(srv, [t])
     srv.stop()
     assert res[t]["state"] == Server.FAILED
+
+
+def test_cancel_and_deadline():
+    from paper_2009_08875_gb300 import _lib
+    # one group slot and large problems, so that later requests wait in the queue
+    big = [make_request(0, 7, 7, 60 + i) for i in range(4)]
+    srv = Server(slots_per_group=1, memory_budget_gb=40.0, tol=1e-10)
+    t_run = srv.submit(*big[0])
+    t_queued = srv.submit(*big[1])
+    t_late = srv.submit(*big[2], timeout=1e-6)          # past its deadline before it can start
+    srv.cancel(t_queued)
+    # cancel the first request once it runs
+    t0 = time.time()
+    while srv.poll(t_run)["state"] == Server.QUEUED:
+        assert time.time() - t0 < 60
+        time.sleep(0.001)
+    srv.cancel(t_run)
+    t_ok = srv.submit(*big[3], timeout=600.0)           # generous deadline: completes
+    res = wait_all(srv, [t_run, t_queued, t_late, t_ok])
+    srv.stop()
+    assert res[t_queued]["state"] == Server.FAILED and res[t_queued]["status"] == _lib.ST_ERR_CANCELLED
+    assert res[t_late]["state"] == Server.FAILED and res[t_late]["status"] == _lib.ST_ERR_TIMEOUT
+    # the running request leaves at an iteration boundary (or had already finished)
+    assert res[t_run]["status"] in (_lib.ST_ERR_CANCELLED, _lib.ST_OK)
+    assert res[t_ok]["state"] == Server.DONE and res[t_ok]["status"] == _lib.ST_OK
+    u_alone, its = alone(*big[3][:5], "mixed_precond")
+    assert torch.equal(big[3][5], u_alone) and res[t_ok]["iterations"] == its
