@@ -304,6 +304,38 @@ st_status st_server_stop(st_server s);
 st_status st_nested_solve(st_handle h, int levels, double eps, double rate, const double* g_nodal,
                           const double* u0_nodal, double* w, int* iters_per_level);
 
+/* ---------------------------------------------------------------------------------------
+ * Time-sharded building blocks.  The paper distributes the time axis over processes (Sec. 5.2).
+ * A rank that owns the time rows [row0, row0 + nrows) of one problem (single-problem handle of the
+ * full mesh, which supplies coefficient tables and scratch) applies the operators of a PCG
+ * iteration to its rows; the wavelet transform acts along the whole time axis and is applied to a
+ * block of columns after a rows-to-columns exchange; inner products are reduced by the caller.
+ * The caller's vectors hold only its rows (N_x doubles each) or columns.  Errors: ST_ERR_ARG for
+ * a batch handle, rows outside 0..N_t-1, null pointers.
+ * --------------------------------------------------------------------------------------- */
+
+/* Nodal rows of S (mode 0, Lemma 4.2: time mix, K_x, epilogue) or of the right-hand side before
+ * the analysis (mode 1, Lemma 4.1: L^T G M and M_t G M, K_x, epilogue): y (nrows rows) from
+ * u_halo, which holds rows row0 - 1 .. row0 + nrows (nrows + 2 rows; rows outside 0..N_t-1 are
+ * not read).  u_row0: nodal row 0 of U (mode 0, Gamma_0 term) or u_0 (mode 1), used only when
+ * row0 = 0. */
+st_status st_rows_nodal(st_handle h, int mode, int64_t row0, int64_t nrows, const double* u_halo,
+                        const double* u_row0, double* y);
+
+/* z = K_X r on the wavelet rows row0 .. row0 + nrows - 1 (in-place row order; K_l of each row's
+ * level, Thm. 3.1). */
+st_status st_rows_KX(st_handle h, int64_t row0, int64_t nrows, const double* r, double* z);
+
+/* Wavelet synthesis (synthesize != 0, u = W w) or analysis (w = W^T u) of an N_t x ncols block
+ * of columns (row stride ncols, 1 <= ncols <= N_x; in-place wavelet row order). */
+st_status st_wavelet_cols(st_handle h, int synthesize, int64_t ncols, const double* in, double* out);
+
+/* *result = a^T b over n doubles (deterministic binary64 reduction; synchronous). */
+st_status st_vec_dot(st_handle h, int64_t n, const double* a, const double* b, double* result);
+
+/* y = alpha x + beta y over n doubles (asynchronous on the bound stream). */
+st_status st_vec_axpby(st_handle h, int64_t n, double alpha, const double* x, double beta, double* y);
+
 /* Autotuner (not in the paper).  Two Gauss-Seidel kernels compute identical sweeps: shared-
  * memory tiles (the default) and a register wavefront.  For every multigrid level above the
  * coarsest, for binary64 and binary32 and for K_x (no mass couplings, 2 B N_t slices) and K_l

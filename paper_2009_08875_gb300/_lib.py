@@ -71,6 +71,11 @@ _SIGS = {
     "st_solve_host": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double)]),
     "st_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "st_rows_nodal": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _P, _P, _P]),
+    "st_rows_KX": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
+    "st_wavelet_cols": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, _P, _P]),
+    "st_vec_dot": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "st_vec_axpby": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, ctypes.c_double, _P]),
     "st_nested_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P,
                                        ctypes.POINTER(ctypes.c_int)]),
     "st_set_smoother": (ctypes.c_int, [_P, ctypes.c_int]),

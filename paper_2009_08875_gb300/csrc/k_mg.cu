@@ -71,12 +71,11 @@ __global__ void k_make_coef(Coef<T>* coef, int K, int J, double alpha, Phys ph, 
   }
 }
 
-// K_X slices are the wavelet rows of B problems stored back to back: row = slice mod N_t
+// the coefficients of slice `slice` on level `level` (slice_class)
 template <typename T>
 __device__ __forceinline__ Coef<T> slice_coef(const Coef<T>* coef, int coef_class, int slice, int J, int K,
                                               int level) {
-  int cls = coef_class >= 0 ? coef_class : 1 + wavelet_row_level(slice % ((1 << J) + 1), J);
-  return coef[cls * (K + 1) + level];
+  return coef[slice_class(coef_class, slice, J) * (K + 1) + level];
 }
 
 // Nested P1 prolongation: prolong_value (st_internal.cuh).

@@ -32,8 +32,7 @@ const Coef<float>* coef3<float>(const st_handle_s* h) {
 
 template <typename T>
 __device__ __forceinline__ Coef<T> coef_of(const Coef<T>* coef, int cls, int slice, int J, int K, int level) {
-  const int c = cls >= 0 ? cls : 1 + wavelet_row_level(slice % ((1 << J) + 1), J);
-  return coef[c * (K + 1) + level];
+  return coef[slice_class(cls, slice, J) * (K + 1) + level];
 }
 
 // neighbour sums of point (ix, iy, iz) of an n^3 slice (zero outside the grid)

@@ -118,11 +118,14 @@ __device__ __forceinline__ T tri_dot(const Tri<T>& t, T a, T b, T c) {
 // mode 0 (S):  Y1 = A_t (U M) + L^T (U A),  Y2 = L (U M) + M_t (U A)
 // mode 1 (rhs): Y1 = L^T (G M),             Y2 = M_t (G M)
 // One thread per spatial point walks a chunk of time rows, keeping the stencil results of
-// rows i-1, i, i+1 in registers (the chunk edges recompute one halo row).
+// rows i-1, i, i+1 in registers (the chunk edges recompute one halo row).  Output rows are the
+// global rows row0 .. row0 + nrows - 1 of the N_t rows (Y row i - row0); U holds global row j at
+// its row j - row0 + halo (halo = 1: a time-sharded block with one neighbour row each side).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __restrict__ Y1, T* __restrict__ Y2,
-                                                 int n, int Nt, int chunk, Stencil7<T> sm, Stencil7<T> sa,
-                                                 TimeConsts<T> tk, int mode, int lshape) {
+                                                 int n, int Nt, int row0, int nrows, int halo, int chunk,
+                                                 Stencil7<T> sm, Stencil7<T> sa, TimeConsts<T> tk, int mode,
+                                                 int lshape) {
   const int64_t N = DIM == 2 ? (int64_t)n * n : (int64_t)n * n * n;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= N) return;
@@ -130,32 +133,34 @@ __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __r
   U += poff;
   Y1 += poff;
   Y2 += poff;
+  // global row i lives at U row i - row0 + halo and is output at Y row i - row0
+  auto urow = [&](int i) { return U + (int64_t)(i - row0 + halo) * N; };
+  auto yoff = [&](int i) { return (int64_t)(i - row0) * N + p; };
   int ix, iy, iz;
   coords_of<DIM>(p, n, ix, iy, iz);
+  const int i0 = row0 + blockIdx.y * chunk;
+  const int i1 = min(row0 + nrows, i0 + chunk);
   if (DIM == 2 && outside_domain(ix, iy, n, lshape)) {  // nodes outside the domain stay zero
-    const int i0 = blockIdx.y * chunk, i1 = min(Nt, i0 + chunk);
     for (int i = i0; i < i1; ++i) {
-      Y1[(int64_t)i * N + p] = T(0);
-      Y2[(int64_t)i * N + p] = T(0);
+      Y1[yoff(i)] = T(0);
+      Y2[yoff(i)] = T(0);
     }
     return;
   }
-  const int i0 = blockIdx.y * chunk;
-  const int i1 = min(Nt, i0 + chunk);
   T um_m = T(0), ua_m = T(0), um_c, ua_c, um_p = T(0), ua_p = T(0);
   if (i0 > 0) {
-    Sums<T> v = load_nbr<T, DIM>(U + (int64_t)(i0 - 1) * N, p, ix, iy, iz, n);
+    Sums<T> v = load_nbr<T, DIM>(urow(i0 - 1), p, ix, iy, iz, n);
     um_m = mass_of<T, DIM>(v, sm);
     ua_m = stiff_of(v, sa);
   }
   {
-    Sums<T> v = load_nbr<T, DIM>(U + (int64_t)i0 * N, p, ix, iy, iz, n);
+    Sums<T> v = load_nbr<T, DIM>(urow(i0), p, ix, iy, iz, n);
     um_c = mass_of<T, DIM>(v, sm);
     ua_c = stiff_of(v, sa);
   }
   for (int i = i0; i < i1; ++i) {
     if (i + 1 < Nt) {
-      Sums<T> v = load_nbr<T, DIM>(U + (int64_t)(i + 1) * N, p, ix, iy, iz, n);
+      Sums<T> v = load_nbr<T, DIM>(urow(i + 1), p, ix, iy, iz, n);
       um_p = mass_of<T, DIM>(v, sm);
       ua_p = mode == 0 ? stiff_of(v, sa) : T(0);
     } else {
@@ -170,8 +175,8 @@ __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __r
       y1 = tri_dot(tri_LT<T>(i, Nt), um_m, um_c, um_p);
       y2 = tri_dot(tri_Mt(i, Nt, tk), um_m, um_c, um_p);
     }
-    Y1[(int64_t)i * N + p] = y1;
-    Y2[(int64_t)i * N + p] = y2;
+    Y1[yoff(i)] = y1;
+    Y2[yoff(i)] = y2;
     um_m = um_c;
     ua_m = ua_c;
     um_c = um_p;
@@ -183,7 +188,8 @@ __global__ void __launch_bounds__(256) k_timemix(const T* __restrict__ U, T* __r
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_epilogue(const T* __restrict__ X1, const T* __restrict__ X2,
                                                   const T* __restrict__ row0, int64_t row0_stride, T* __restrict__ Z,
-                                                  int n, int Nt, Stencil7<T> sm, Stencil7<T> sa, int lshape) {
+                                                  int n, int Nt, int first_row, Stencil7<T> sm, Stencil7<T> sa,
+                                                  int lshape) {
   const int64_t N = DIM == 2 ? (int64_t)n * n : (int64_t)n * n * n;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= N) return;
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(256) k_epilogue(const T* __restrict__ X1, cons
   }
   T z = mass_of<T, DIM>(load_nbr<T, DIM>(X1 + off, p, ix, iy, iz, n), sm) +
         stiff_of(load_nbr<T, DIM>(X2 + off, p, ix, iy, iz, n), sa);
-  if (i == 0 && row0 != nullptr) z += mass_of<T, DIM>(load_nbr<T, DIM>(row0, p, ix, iy, iz, n), sm);
+  if (first_row + i == 0 && row0 != nullptr) z += mass_of<T, DIM>(load_nbr<T, DIM>(row0, p, ix, iy, iz, n), sm);
   Z[off + p] = z;
 }
 
@@ -317,10 +323,12 @@ cudaError_t launch_timemix(const st_handle_s* h, int nb, int mode, const T* U, T
   const int chunk = 32;
   dim3 grid((unsigned)((N + 255) / 256), (int)((h->Nt + chunk - 1) / chunk), nb);
   if (h->domain == 2)
-    k_timemix<T, 3><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, chunk, fine_M<T>(h),
+    k_timemix<T, 3><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, 0, (int)h->Nt, 0,
+                                                 chunk, fine_M<T>(h),
                                                  fine_A<T>(h), time_consts<T>(h->J), mode, 0);
   else
-    k_timemix<T, 2><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, chunk, fine_M<T>(h),
+    k_timemix<T, 2><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, 0, (int)h->Nt, 0,
+                                                 chunk, fine_M<T>(h),
                                                  fine_A<T>(h), time_consts<T>(h->J), mode, h->domain);
   count_launch(h);
   return cudaGetLastError();
@@ -332,10 +340,10 @@ cudaError_t launch_epilogue(const st_handle_s* h, int nb, const T* X, const T* r
   const int64_t N = h->Nx;
   dim3 grid((unsigned)((N + 255) / 256), (int)h->Nt, nb);
   if (h->domain == 2)
-    k_epilogue<T, 3><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt,
+    k_epilogue<T, 3><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt, 0,
                                                   fine_M<T>(h), fine_A<T>(h), 0);
   else
-    k_epilogue<T, 2><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt,
+    k_epilogue<T, 2><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt, 0,
                                                   fine_M<T>(h), fine_A<T>(h), h->domain);
   count_launch(h);
   return cudaGetLastError();
@@ -354,13 +362,48 @@ cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y) {
   return cudaGetLastError();
 }
 
+// Time-sharded row blocks (one problem): the time mix for output rows row0 .. row0 + nrows - 1
+// from U with one neighbour row each side (nrows + 2 rows; the rows outside 0 .. N_t - 1 are not
+// read), and the epilogue of those rows (X: X1 block then X2 block of nrows rows each; the Gamma_0
+// term only when the block holds row 0).
+cudaError_t launch_timemix_rows(const st_handle_s* h, int mode, int row0, int nrows, const double* U, double* Y) {
+  const int n = h->n;
+  const int64_t N = h->Nx;
+  const int chunk = 32;
+  dim3 grid((unsigned)((N + 255) / 256), (unsigned)((nrows + chunk - 1) / chunk), 1);
+  if (h->domain == 2)
+    k_timemix<double, 3><<<grid, 256, 0, h->stream>>>(U, Y, Y + (int64_t)nrows * N, n, (int)h->Nt, row0, nrows, 1,
+                                                      chunk, fine_M<double>(h), fine_A<double>(h),
+                                                      time_consts<double>(h->J), mode, 0);
+  else
+    k_timemix<double, 2><<<grid, 256, 0, h->stream>>>(U, Y, Y + (int64_t)nrows * N, n, (int)h->Nt, row0, nrows, 1,
+                                                      chunk, fine_M<double>(h), fine_A<double>(h),
+                                                      time_consts<double>(h->J), mode, h->domain);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_epilogue_rows(const st_handle_s* h, int row0, int nrows, const double* X, const double* u_row0,
+                                 double* Z) {
+  const int n = h->n;
+  const int64_t N = h->Nx;
+  dim3 grid((unsigned)((N + 255) / 256), (unsigned)nrows, 1);
+  if (h->domain == 2)
+    k_epilogue<double, 3><<<grid, 256, 0, h->stream>>>(X, X + (int64_t)nrows * N, u_row0, 0, Z, n, nrows, row0,
+                                                       fine_M<double>(h), fine_A<double>(h), 0);
+  else
+    k_epilogue<double, 2><<<grid, 256, 0, h->stream>>>(X, X + (int64_t)nrows * N, u_row0, 0, Z, n, nrows, row0,
+                                                       fine_M<double>(h), fine_A<double>(h), h->domain);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
 // u = W w.  Stage j reads c_j from the previous stage's output (stage 0: from w) and d_j from
 // w, and writes level j+1 into a buffer that differs from the one it reads; the last stage
 // writes u.  Scratch buffers V1/V2 alternate.
 template <typename T>
-cudaError_t wavelet_synth(const st_handle_s* h, int nb, const T* w, T* u) {
+cudaError_t wavelet_synth_n(const st_handle_s* h, int nb, int64_t Nx, const T* w, T* u) {
   const int J = h->J;
-  const int64_t Nx = h->Nx;
   const unsigned gx = (unsigned)((Nx + 255) / 256);
   T* V1 = reinterpret_cast<T*>(h->V1);
   T* V2 = reinterpret_cast<T*>(h->V2);
@@ -380,9 +423,8 @@ cudaError_t wavelet_synth(const st_handle_s* h, int nb, const T* w, T* u) {
 // w = W^T u = diag(W_{J-1}^T, I) M_{J-1}^T u: stage J-1 first.  c goes to alternating
 // scratch buffers, d straight to w; stage 0 writes c_0 into rows 0 and 2^J of w.
 template <typename T>
-cudaError_t wavelet_anal(const st_handle_s* h, int nb, const T* u, T* w) {
+cudaError_t wavelet_anal_n(const st_handle_s* h, int nb, int64_t Nx, const T* u, T* w) {
   const int J = h->J;
-  const int64_t Nx = h->Nx;
   const unsigned gx = (unsigned)((Nx + 255) / 256);
   T* V1 = reinterpret_cast<T*>(h->V1);
   T* V2 = reinterpret_cast<T*>(h->V2);
@@ -397,6 +439,22 @@ cudaError_t wavelet_anal(const st_handle_s* h, int nb, const T* u, T* w) {
     src = cdst;
   }
   return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t wavelet_synth(const st_handle_s* h, int nb, const T* w, T* u) {
+  return wavelet_synth_n<T>(h, nb, h->Nx, w, u);
+}
+
+template <typename T>
+cudaError_t wavelet_anal(const st_handle_s* h, int nb, const T* u, T* w) {
+  return wavelet_anal_n<T>(h, nb, h->Nx, u, w);
+}
+
+// the transforms of an N_t x ncols block of columns (a time-sharded rank's share after a
+// rows-to-columns transpose); ncols <= N_x
+cudaError_t wavelet_cols(const st_handle_s* h, int synth, int64_t ncols, const double* in, double* out) {
+  return synth ? wavelet_synth_n<double>(h, 1, ncols, in, out) : wavelet_anal_n<double>(h, 1, ncols, in, out);
 }
 
 #define ST_INSTANTIATE(T)                                                                           \

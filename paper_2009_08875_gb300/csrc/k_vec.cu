@@ -134,6 +134,14 @@ __global__ void __launch_bounds__(256) k_add_correction(double* __restrict__ w, 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) w[i] += (double)d[i];
 }
 
+// y = alpha x + beta y (binary64)
+__global__ void __launch_bounds__(256) k_axpby(double* __restrict__ y, const double* __restrict__ x, double alpha,
+                                               double beta, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = alpha * x[i] + beta * y[i];
+}
+
 // r = f - q (binary64) and, if rs is not null, rs = r rounded to binary32
 __global__ void __launch_bounds__(256) k_residual_split(double* __restrict__ r, float* __restrict__ rs,
                                                         const double* __restrict__ f, const double* __restrict__ q,
@@ -202,6 +210,12 @@ cudaError_t launch_copy(const st_handle_s* h, Td* dst, const Ts* src, int64_t n)
 template <typename T>
 cudaError_t launch_zero(const st_handle_s* h, T* dst, int64_t n) {
   k_zero<T><<<stream_grid(n), kThreads, 0, h->stream>>>(dst, n);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(const st_handle_s* h, double* y, const double* x, double alpha, double beta, int64_t n) {
+  k_axpby<<<stream_grid(n), kThreads, 0, h->stream>>>(y, x, alpha, beta, n);
   count_launch(h);
   return cudaGetLastError();
 }

@@ -90,6 +90,16 @@ __device__ __forceinline__ T prolong_value3(const T* __restrict__ cs, int nc, in
   return T(0.5) * (a + c);
 }
 
+// Coefficient class of multigrid slice `slice` for a coef_class argument: a class >= 0 applies to
+// every slice (0: K_x, 1 + l: K_l); a negative value -1 - r0 selects, per slice, K_l for the level
+// l of wavelet row (r0 + slice) mod N_t (slices are the wavelet rows of B problems stored back to
+// back, or rows r0, r0 + 1, ... of one problem for a rank that owns those rows).
+__host__ __device__ inline int wavelet_row_level(int i, int J);
+__host__ __device__ inline int slice_class(int coef_class, int slice, int J) {
+  if (coef_class >= 0) return coef_class;
+  return 1 + wavelet_row_level((slice + (-1 - coef_class)) % ((1 << J) + 1), J);
+}
+
 // Level |lambda| of in-place wavelet row i (rows 0 and 2^J: level 0; else J - ctz(i)).
 __host__ __device__ inline int wavelet_row_level(int i, int J) {
   if (i == 0 || i == (1 << J)) return 0;
@@ -261,6 +271,13 @@ cudaError_t launch_copy(const st_handle_s* h, Td* dst, const Ts* src, int64_t n)
 template <typename T>
 cudaError_t launch_zero(const st_handle_s* h, T* dst, int64_t n);
 cudaError_t launch_add_correction(const st_handle_s* h, double* w, const float* d, int64_t n);
+// y = alpha x + beta y
+cudaError_t launch_axpby(const st_handle_s* h, double* y, const double* x, double alpha, double beta, int64_t n);
+// time-sharded row blocks and column blocks (k_space_time.cu)
+cudaError_t launch_timemix_rows(const st_handle_s* h, int mode, int row0, int nrows, const double* U, double* Y);
+cudaError_t launch_epilogue_rows(const st_handle_s* h, int row0, int nrows, const double* X, const double* u_row0,
+                                 double* Z);
+cudaError_t wavelet_cols(const st_handle_s* h, int synth, int64_t ncols, const double* in, double* out);
 // r = f - q, and rs = (float) r unless rs is null
 cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, const double* f, const double* q,
                                   int64_t n);

@@ -1,0 +1,111 @@
+"""The time-sharded solver with its CUDA backend (st_rows_*, st_wavelet_cols, st_vec_*), P ranks as
+host threads on one GPU.
+
+The ranks exchange rows through host-side mailboxes (each rank's kernels finish before its data is
+handed over, and no kernel waits on another rank), so the schedule's data flow is exercised
+exactly as over NCCL.  Each rank's rows of the solution must match the single-handle solve with
+the same iteration count; they differ only in the order in which the inner products are summed,
+so the solution agrees to 1e-10 (the FP64 solve target).
+"""
+import threading
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2009_08875_gb300 import Solver, inputs, sharded  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+class _Shared:
+    def __init__(self, P):
+        self.barrier = threading.Barrier(P)
+        self.box = {}
+        self.vals = [0.0] * P
+
+
+class ThreadComm:
+    def __init__(self, shared, rank, size):
+        self.sh, self.rank, self.size = shared, rank, size
+
+    def exchange(self, sends, recvs):
+        torch.cuda.synchronize()
+        for s, t in sends.items():
+            self.sh.box[(self.rank, s)] = t
+        self.sh.barrier.wait()
+        for s, t in recvs.items():
+            t.copy_(self.sh.box[(s, self.rank)])
+        torch.cuda.synchronize()
+        self.sh.barrier.wait()
+
+    def allreduce_sum(self, x):
+        self.sh.vals[self.rank] = x
+        self.sh.barrier.wait()
+        total = 0.0
+        for v in self.sh.vals:
+            total += v
+        self.sh.barrier.wait()
+        return total
+
+
+def run_ranks(P, K, J, domain, g, u0, tol=1e-10, tol_mode=0):
+    shared = _Shared(P)
+    out = [None] * P
+    errors = []
+
+    def rank_main(r):
+        try:
+            be = sharded.CudaBackend(K, J, domain=domain)
+            ts = sharded.TimeShardedSolver(J, ThreadComm(shared, r, P), be)
+            gd = torch.from_numpy(np.ascontiguousarray(g[ts.lo:ts.hi])).cuda()
+            u, its, rel = ts.solve(gd, torch.from_numpy(u0).cuda(), tol=tol, tol_mode=tol_mode)
+            torch.cuda.synchronize()
+            out[r] = (ts.lo, ts.hi, u.cpu().numpy(), its)
+            be.close()
+        except BaseException as e:  # report, and release the other ranks
+            errors.append(e)
+            shared.barrier.abort()
+
+    threads = [threading.Thread(target=rank_main, args=(r,)) for r in range(P)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=600)
+    if errors:
+        raise errors[0]
+    return out
+
+
+@pytest.mark.parametrize("P,K,J,domain", [(2, 5, 4, 0), (4, 5, 4, 0), (2, 4, 3, 1), (2, 3, 3, 2), (8, 4, 3, 0)])
+def test_sharded_solve_matches_single_handle(P, K, J, domain):
+    g, u0, _ = inputs.manufactured(K, J, domain)
+    g, u0 = inputs.to_grid(K, domain, g), inputs.to_grid(K, domain, u0)
+    with Solver(K, J, domain=domain, tol=1e-10) as s:
+        u_ref = torch.zeros(s.shape, dtype=torch.float64).pin_memory()
+        its_ref, _ = s.solve_host(torch.from_numpy(g).pin_memory(), torch.from_numpy(u0).pin_memory(), u_ref)
+    u_ref = u_ref.numpy()
+    res = run_ranks(P, K, J, domain, g, u0)
+    covered = 0
+    for lo, hi, u, its in res:
+        assert its == its_ref
+        assert np.abs(u - u_ref[lo:hi]).max() <= 1e-10 * np.abs(u_ref).max()
+        covered += hi - lo
+    assert covered == u_ref.shape[0]
+
+
+def test_row_entry_points_reject_bad_ranges():
+    from paper_2009_08875_gb300 import _lib
+    import ctypes
+    with Solver(3, 2) as s:
+        x = torch.zeros((5, s.Nx), dtype=torch.float64, device="cuda")
+        p = ctypes.c_void_p(x.data_ptr())
+        lib = _lib.load()
+        assert lib.st_rows_KX(s._h, 3, 3, p, p) == _lib.ST_ERR_ARG       # rows past N_t = 5
+        assert lib.st_rows_KX(s._h, -1, 2, p, p) == _lib.ST_ERR_ARG
+        assert lib.st_wavelet_cols(s._h, 1, s.Nx + 1, p, p) == _lib.ST_ERR_ARG
+    with Solver(3, 2, batch=2) as s:
+        x = torch.zeros(s.shape, dtype=torch.float64, device="cuda")
+        p = ctypes.c_void_p(x.data_ptr())
+        assert _lib.load().st_rows_KX(s._h, 0, 1, p, p) == _lib.ST_ERR_ARG  # batch handle
