@@ -57,13 +57,14 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solves measurement")
     ap.add_argument("--no-nested", action="store_true", help="skip the nested-iteration measurement")
     ap.add_argument("--no-cube", action="store_true", help="skip the 3D (unit cube) measurement")
+    ap.add_argument("--no-df", action="store_true", help="skip the double-float multigrid measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=0.25, help="seconds of Poisson arrivals replayed")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate (requests/s)")
     ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--smoother", choices=["auto", "tiles", "wavefront"], default="auto",
                     help="Gauss-Seidel kernel: autotuned per level (default) or one kernel on every level")
-    ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_precond", "mixed_bf16"], default="fp64",
+    ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_precond", "mixed_bf16", "fp64_df"], default="fp64",
                     help="precision of the main timed solve (profiling aid; the bench line uses fp64)")
     ap.add_argument("--oracle-sample-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -456,6 +457,43 @@ def run_ours(args):
                   "max_rel_error_to_exact_u": err_nested, "converged_solve_max_rel_error_to_exact_u": err_full,
                   "note": "time to discretisation accuracy: nested iteration vs PCG to relative 1e-10"}
 
+    # the same FP64 solve with the multigrid in double-float (ST_FP64_DF): time per solve, error
+    # against the binary64 solution of the timed region, live sweep bandwidth
+    fp64_df = None
+    if not args.no_df:
+        dsol = Solver(K, J, tol=TOL, tol_mode=0, maxit=500, precision="fp64_df")
+        pick_smoother(dsol, args.smoother)
+        ud = torch.empty_like(u)
+
+        def dstep():
+            dsol.rhs(g, u0, f)
+            its_d, _ = dsol.pcg_solve(f, w)
+            dsol.synthesize(w, ud)
+            return its_d
+
+        for _ in range(max(1, args.warmup)):
+            dstep()
+        torch.cuda.synchronize()
+        dsol.profile_begin()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        its_d = 0
+        d0.record(dsol.stream)
+        for _ in range(args.steps):
+            its_d += dstep()
+        d1.record(dsol.stream)
+        torch.cuda.synchronize()
+        dprof = dsol.profile_end()
+        dms = d0.elapsed_time(d1)
+        err_d = ((ud - u).abs().max() / u.abs().max()).item()
+        fp64_df = {"value": world * N * its_d / (dms / 1e3), "unit": "DoF-iter/s", "ms_per_solve": dms / args.steps,
+                   "pcg_iterations": its_d / args.steps, "rel_err_vs_fp64_solution": err_d,
+                   "dtype": "f64 PCG and operators, double-float (2 x f32) multigrid",
+                   "finest_sweeps_hbm_gbs": dprof["sweep_bytes"] / (dprof["sweep_ms"] / 1e3) / 1e9
+                   if dprof["sweep_ms"] > 0 else None,
+                   "finest_sweeps_share_of_step": dprof["sweep_ms"] / dms if dms > 0 else None}
+        dsol.close()
+
     # the 3D problem of the paper's weak-scaling table (unit cube, N_x = 250047, N_t = 513):
     # FP64 solve to the same relative 1e-10 of u = (1 + t^2) sin sin sin
     cube = None
@@ -632,6 +670,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "nested": nested,
+        "fp64_df": fp64_df,
         "cube": cube,
         "mixed": mixed.get("mixed"),
         "mixed_bf16": mixed.get("mixed_bf16"),

@@ -68,11 +68,16 @@ typedef enum {
   ST_MIXED_PRECOND = 2,  /* one binary64 PCG (binary64 S_hat, recurrences and inner products)
                             preconditioned by K_X in binary32, with the flexible (Polak-Ribiere)
                             beta = r^T (z - z_old) / rho_old */
-  ST_MIXED_BF16 = 3      /* as ST_MIXED_FP32, but the inner PCG's preconditioner K_X keeps its
+  ST_MIXED_BF16 = 3,     /* as ST_MIXED_FP32, but the inner PCG's preconditioner K_X keeps its
                             multigrid vectors (iterates, right-hand sides, coarse levels) in
                             bfloat16 storage with binary32 arithmetic, and the inner PCG uses
                             the flexible beta; the inner S_hat and the outer stopping test
                             stay binary32 / binary64 as in ST_MIXED_FP32 */
+  ST_FP64_DF = 4         /* as ST_FP64, but every multigrid application (K_x in S and in the
+                            right-hand side, K_l in K_X) computes in double-float: pairs of
+                            binary32 values with error-free transformations, about 48
+                            significant bits (binary64: 53); inputs and outputs stay binary64.
+                            Not on the cube. */
 } st_precision;
 
 typedef struct {

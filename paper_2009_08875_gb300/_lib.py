@@ -26,7 +26,7 @@ class StSolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("relres", ctypes.c_double)]
 
 
-ST_FP64, ST_MIXED_FP32, ST_MIXED_PRECOND, ST_MIXED_BF16 = 0, 1, 2, 3
+ST_FP64, ST_MIXED_FP32, ST_MIXED_PRECOND, ST_MIXED_BF16, ST_FP64_DF = 0, 1, 2, 3, 4
 
 
 class StProfile(ctypes.Structure):

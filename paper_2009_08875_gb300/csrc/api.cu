@@ -116,6 +116,8 @@ void free_all(st_handle_s* h) {
   h->coef = nullptr;
   if (h->coef32) cudaFree(h->coef32);
   h->coef32 = nullptr;
+  if (h->coefdf) cudaFree(h->coefdf);
+  h->coefdf = nullptr;
   float** fb[] = {&h->xi, &h->ri, &h->pi, &h->zi, &h->qi};
   for (float** b : fb) {
     if (*b) cudaFree(*b);
@@ -680,15 +682,15 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   ST_REQUIRE(c.maxit >= 0 && c.tol >= 0.0 && (c.tol_mode == 0 || c.tol_mode == 1),
              "st_setup: invalid tolerance settings");
   ST_REQUIRE(c.precision == ST_FP64 || c.precision == ST_MIXED_FP32 || c.precision == ST_MIXED_PRECOND ||
-                 c.precision == ST_MIXED_BF16,
+                 c.precision == ST_MIXED_BF16 || c.precision == ST_FP64_DF,
              "st_setup: unsupported precision");
   ST_REQUIRE(c.inner_tol > 0.0 && c.inner_tol < 1.0 && c.inner_maxit >= 1,
              "st_setup: inner_tol must be in (0, 1) and inner_maxit >= 1");
   ST_REQUIRE(check_phys(c), "st_setup: D must be symmetric positive definite and c >= 0 (finite)");
   ST_REQUIRE(domain != 2 || (c.diffusion[0] == 1.0 && c.diffusion[1] == 0.0 && c.diffusion[2] == 1.0),
              "st_setup: the cube supports D = Id only (c >= 0 is allowed)");
-  ST_REQUIRE(domain != 2 || c.precision != ST_MIXED_BF16,
-             "st_setup: ST_MIXED_BF16 is not available on the cube");
+  ST_REQUIRE(domain != 2 || (c.precision != ST_MIXED_BF16 && c.precision != ST_FP64_DF),
+             "st_setup: ST_MIXED_BF16 and ST_FP64_DF are not available on the cube");
 
   st_handle_s* h = new (std::nothrow) st_handle_s();
   if (!h) {
@@ -706,6 +708,7 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   h->cfg = c;
   h->phys = Phys{c.diffusion[0], c.diffusion[1], c.diffusion[2], c.reaction};
   h->diag0 = c.diffusion[1] != 0.0 || c.reaction != 0.0;
+  h->mg_df = c.precision == ST_FP64_DF;
   h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
@@ -762,6 +765,9 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   if (s == ST_OK)
     s = alloc_bytes(reinterpret_cast<void**>(&h->coef), sizeof(Coef<double>) * (h->J + 2) * (h->K + 1),
                     "coefficient table");
+  if (s == ST_OK && h->mg_df)
+    s = alloc_bytes(reinterpret_cast<void**>(&h->coefdf), sizeof(Coef<df64>) * (h->J + 2) * (h->K + 1),
+                    "coefficient table");
   if (s == ST_OK) s = alloc_bytes(reinterpret_cast<void**>(&h->act), sizeof(int) * batch, "active flags");
   if (s == ST_OK) {
     e = cudaMallocHost(reinterpret_cast<void**>(&h->scal_host), sizeof(double) * SC_COUNT * batch);
@@ -787,6 +793,8 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
     const int dim = domain == 2 ? 3 : 2;
     if (e == cudaSuccess) e = launch_make_coef(h->coef, h->K, h->J, c.alpha, h->phys, dim, h->stream);
     if (e == cudaSuccess) e = launch_make_coef32(h->coef32, h->K, h->J, c.alpha, h->phys, dim, h->stream);
+    if (e == cudaSuccess && h->mg_df)
+      e = launch_make_coef_df(h->coefdf, h->K, h->J, c.alpha, h->phys, dim, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->scal, 0, sizeof(double) * SC_COUNT * batch, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = cuda_fail("st_setup", e);

@@ -11,6 +11,7 @@
 
 #include <type_traits>
 
+#include "df64.cuh"
 #include "st_internal.cuh"
 
 namespace st {
@@ -100,31 +101,32 @@ __global__ void k_coarse_dense3(G* __restrict__ x, const G* __restrict__ b, int 
   const int sl = blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= nslices) return;
   const Coef<T> cf = slice_coef(coef, coef_class, sl, J, K, 2);
-  T A[9][10];
+  using C = typename std::conditional<std::is_same<T, df64>::value, double, T>::type;  // elimination type
+  C A[9][10];
   for (int p = 0; p < 9; ++p) {
-    for (int q = 0; q < 10; ++q) A[p][q] = T(0);
+    for (int q = 0; q < 10; ++q) A[p][q] = C(0);
     const int ix = p % 3, iy = p / 3;
     if (outside_domain(ix, iy, 3, lshape)) {
-      A[p][p] = T(1);
+      A[p][p] = C(1);
       continue;
     }
-    A[p][p] = cf.c;
-    A[p][9] = cf.c * T(b[(int64_t)sl * 9 + p]);
+    A[p][p] = C(cf.c);
+    A[p][9] = C(cf.c) * C(b[(int64_t)sl * 9 + p]);
     const int nb[6][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}, {1, 1}, {-1, -1}};
     for (int t = 0; t < 6; ++t) {
       const int jx = ix + nb[t][0], jy = iy + nb[t][1];
       if (jx < 0 || jx > 2 || jy < 0 || jy > 2 || outside_domain(jx, jy, 3, lshape)) continue;
-      A[p][jy * 3 + jx] = t < 2 ? cf.ax : (t < 4 ? cf.ay : cf.dg);
+      A[p][jy * 3 + jx] = C(t < 2 ? cf.ax : (t < 4 ? cf.ay : cf.dg));
     }
   }
   for (int c = 0; c < 9; ++c) {
     for (int r = c + 1; r < 9; ++r) {
-      const T f = A[r][c] / A[c][c];
+      const C f = A[r][c] / A[c][c];
       for (int q = c; q < 10; ++q) A[r][q] -= f * A[c][q];
     }
   }
   for (int r = 8; r >= 0; --r) {
-    T v = A[r][9];
+    C v = A[r][9];
     for (int q = r + 1; q < 9; ++q) v -= A[r][q] * A[q][9];
     A[r][9] = v / A[r][r];
   }
@@ -292,12 +294,12 @@ __global__ void __launch_bounds__(128) k_gs_wave(G* __restrict__ x_out, const G*
     const int gx = cbase + m;
     const bool ok = cl >= s + 1 && cl < kWR - s - 1 && gx >= 0 && gx < n && !outside_domain(gx, j, n, lshape);
     // neighbours west, east, south, north, north-east, south-west (uniform branch on m)
-    const T up_c2 = __shfl_up_sync(0xffffffffu, xcr[2], 1);
-    const T dn_c0 = __shfl_down_sync(0xffffffffu, xcr[0], 1);
+    const T up_c2 = shfl_up(xcr[2], 1);
+    const T dn_c0 = shfl_down(xcr[0], 1);
     T up_s2 = T(0), dn_n0 = T(0);
     if (DIAG) {
-      up_s2 = __shfl_up_sync(0xffffffffu, xs[2], 1);
-      dn_n0 = __shfl_down_sync(0xffffffffu, xn[0], 1);
+      up_s2 = shfl_up(xs[2], 1);
+      dn_n0 = shfl_down(xn[0], 1);
     }
     if (m == 0) {
       T v = bc[0] - cf.axs * (up_c2 + xcr[1]);
@@ -352,8 +354,8 @@ __global__ void __launch_bounds__(128) k_gs_wave(G* __restrict__ x_out, const G*
 }
 
 // b' = b / c on the finest level (the multigrid's scaled right-hand side)
-template <typename T, typename G>
-__global__ void k_scale_rhs(G* __restrict__ bs, const T* __restrict__ b, int n, const Coef<T>* __restrict__ coef,
+template <typename T, typename G, typename Tin = T>
+__global__ void k_scale_rhs(G* __restrict__ bs, const Tin* __restrict__ b, int n, const Coef<T>* __restrict__ coef,
                             int coef_class, int J, int K) {
   const int N = n * n;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -361,7 +363,7 @@ __global__ void k_scale_rhs(G* __restrict__ bs, const T* __restrict__ b, int n, 
   const int slice = blockIdx.y;
   const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, K);
   const int64_t i = (int64_t)slice * N + p;
-  bs[i] = G(b[i] * cf.inv_c);
+  bs[i] = G(T(b[i]) * cf.inv_c);
 }
 
 // x += P xc (used when there is no post-smoothing to fuse the correction into)
@@ -461,6 +463,10 @@ template <>
 const Coef<float>* coef_table<float>(const st_handle_s* h) {
   return h->coef32;
 }
+template <>
+const Coef<df64>* coef_table<df64>(const st_handle_s* h) {
+  return h->coefdf;
+}
 
 // Tile shapes (chosen by measurement on GB300): binary64 is bound by the FP64 pipe, so one sweep
 // per launch keeps the halo recomputation small (3-point halo, 90 x 26 interior; 49 KB of shared
@@ -483,6 +489,10 @@ struct SweepShape;
 #endif
 template <>
 struct SweepShape<double> {
+  static constexpr int kFusedNSW = 1, kFusedHR = ST_GS_HR64, kSingleHR = ST_GS_HR64;
+};
+template <>
+struct SweepShape<df64> {  // 8-byte values like binary64; one sweep per launch
   static constexpr int kFusedNSW = 1, kFusedHR = ST_GS_HR64, kSingleHR = ST_GS_HR64;
 };
 template <>
@@ -541,8 +551,13 @@ cudaError_t wave_launch(const st_handle_s* h, int k, int nslices, int cls, G* x_
 // Which Gauss-Seidel kernel a launch uses: the handle's autotuned choice per element type,
 // coupling pattern and level (0: shared-memory tiles, the default; 1: register wavefront).
 template <typename T>
+constexpr int type_slot() {
+  return std::is_same<T, df64>::value ? 2 : (sizeof(T) == 4 ? 1 : 0);
+}
+
+template <typename T>
 int gs_kind(const st_handle_s* h, bool diag, int k) {
-  return h->gs_kind[sizeof(T) == 4 ? 1 : 0][diag ? 1 : 0][k];
+  return h->gs_kind[type_slot<T>()][diag ? 1 : 0][k];
 }
 
 template <typename T, typename G, bool DIAG>
@@ -624,17 +639,32 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, G* const x
   return cudaSuccess;
 }
 
-// x = the iterate, widened from the storage type (binary16 storage of binary32 work)
+// x = the iterate, widened from the storage type (bfloat16 storage of binary32 work; double-float
+// work into binary64)
 template <typename T, typename G>
 __global__ void k_widen(T* __restrict__ x, const G* __restrict__ g, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) x[i] = T(g[i]);
 }
 
+// the same in place: element i of a buffer of 8-byte double-float values becomes a double
+__global__ void k_widen_df_inplace(void* buf, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const df64 v = reinterpret_cast<const df64*>(buf)[i];
+    reinterpret_cast<double*>(buf)[i] = double(v);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, Phys ph, int dim, cudaStream_t s) {
   k_make_coef<double><<<1, 256, 0, s>>>(coef, K, J, alpha, ph, dim);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_make_coef_df(Coef<df64>* coef, int K, int J, double alpha, Phys ph, int dim, cudaStream_t s) {
+  k_make_coef<df64><<<1, 256, 0, s>>>(coef, K, J, alpha, ph, dim);
   return cudaGetLastError();
 }
 
@@ -663,6 +693,7 @@ cudaError_t mg_set_attributes() {
   if (e == cudaSuccess) e = set_smem_attr<float, float, 1, SF::kSingleHR>();
   if (e == cudaSuccess) e = set_smem_attr<float, __nv_bfloat16, SF::kFusedNSW, SF::kFusedHR>();
   if (e == cudaSuccess) e = set_smem_attr<float, __nv_bfloat16, 1, SF::kSingleHR>();
+  if (e == cudaSuccess) e = set_smem_attr<df64, df64, 1, SweepShape<df64>::kSingleHR>();
   return e;
 }
 
@@ -703,9 +734,42 @@ cudaError_t mg_run(const st_handle_s* h, int nslices, int coef_class, const T* b
   return cudaSuccess;
 }
 
+// binary64 in and out, the multigrid in double-float: the iterate lives in x's memory (8 bytes a
+// value either way) and the alternate buffer, and is widened to binary64 at the end
+cudaError_t mg_apply_df(const st_handle_s* h, int nslices, int coef_class, const double* b, double* x) {
+  using D = df64;
+  const bool diag = coef_class != 0 || h->diag0;
+  const size_t npts = (size_t)h->Nx * nslices;
+  D* const xb[2] = {reinterpret_cast<D*>(x), reinterpret_cast<D*>(h->Xalt)};
+  int cur = 0;
+  D* bs = reinterpret_cast<D*>(h->Bs);
+  const int n = h->n;
+  k_scale_rhs<D, D, double><<<dim3((n * n + 255) / 256, nslices), 256, 0, h->stream>>>(bs, b, n, coef_table<D>(h),
+                                                                                      coef_class, h->J, h->K);
+  count_launch(h);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int c = 0; c < h->cfg.n_vcycles; ++c) {
+    e = diag ? vcycle<D, D, true>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0)
+             : vcycle<D, D, false>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0);
+    if (e != cudaSuccess) return e;
+  }
+  if (h->cfg.n_vcycles == 0) return cudaMemsetAsync(x, 0, sizeof(double) * npts, h->stream);
+  const unsigned blocks = (unsigned)((npts + 255) / 256);
+  if (cur == 1)
+    k_widen<double, D><<<blocks, 256, 0, h->stream>>>(x, xb[1], (int64_t)npts);
+  else
+    k_widen_df_inplace<<<blocks, 256, 0, h->stream>>>(x, (int64_t)npts);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x) {
   if (h->domain == 2) return mg_apply3<T>(h, nslices, coef_class, b, x);
+  if constexpr (std::is_same<T, double>::value) {
+    if (h->mg_df) return mg_apply_df(h, nslices, coef_class, b, x);
+  }
   return mg_run<T, T>(h, nslices, coef_class, b, x);
 }
 
@@ -730,7 +794,7 @@ cudaError_t autotune_one(st_handle_s* h, int k, float* ms_tile, float* ms_wave) 
   float best[2] = {0.f, 0.f};
   cudaError_t err = cudaSuccess;
   for (int kind = 0; kind < 2 && err == cudaSuccess; ++kind) {
-    h->gs_kind[sizeof(T) == 4 ? 1 : 0][DIAG ? 1 : 0][k] = (unsigned char)kind;
+    h->gs_kind[type_slot<T>()][DIAG ? 1 : 0][k] = (unsigned char)kind;
     float t = 1e30f;
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
       cudaEventRecord(e0, h->stream);
@@ -745,7 +809,7 @@ cudaError_t autotune_one(st_handle_s* h, int k, float* ms_tile, float* ms_wave) 
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->gs_kind[sizeof(T) == 4 ? 1 : 0][DIAG ? 1 : 0][k] = best[1] < best[0] ? 1 : 0;
+  h->gs_kind[type_slot<T>()][DIAG ? 1 : 0][k] = best[1] < best[0] ? 1 : 0;
   *ms_tile = best[0];
   *ms_wave = best[1];
   return err;
@@ -764,6 +828,11 @@ cudaError_t mg_autotune(st_handle_s* h, float* table) {
     if (e == cudaSuccess) e = autotune_one<double, true>(h, k, row + 2, row + 3);
     if (e == cudaSuccess) e = autotune_one<float, false>(h, k, row + 4, row + 5);
     if (e == cudaSuccess) e = autotune_one<float, true>(h, k, row + 6, row + 7);
+    if (e == cudaSuccess && h->mg_df) {  // double-float kernels, recorded in their own slot only
+      float t0, t1;
+      e = autotune_one<df64, false>(h, k, &t0, &t1);
+      if (e == cudaSuccess) e = autotune_one<df64, true>(h, k, &t0, &t1);
+    }
   }
   h->prof_on = saved;
   return e;

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "../../include/st.h"
+#include "df64.cuh"
 
 namespace st {
 
@@ -138,12 +139,14 @@ struct st_handle_s {
   st_config cfg;
   st::Phys phys;     // D and c of the reaction-diffusion form (from cfg)
   bool diag0;        // K_x's operator couples the (1,1) diagonal (d12 != 0 or c != 0)
+  bool mg_df;        // ST_FP64_DF: the binary64 multigrid applications run in double-float
   cudaStream_t stream;
   int device;
 
   st::MGLevels mg;
   st::Coef<double>* coef;   // device, (J + 2) x (K + 1)
   st::Coef<float>* coef32;  // the same table rounded to binary32 (mixed precision)
+  st::Coef<st::df64>* coefdf;  // the same table in double-float (ST_FP64_DF)
 
   // workspace, each N_t x N_x doubles unless noted
   double* U;       // single-scale state
@@ -174,9 +177,9 @@ struct st_handle_s {
   bool use_guess;
   // handles of the coarser meshes (K - m, J - m), m = 1.., of st_nested_solve (created on first use)
   st_handle_s* nest[16];
-  // Gauss-Seidel kernel per [element type: 0 binary64, 1 binary32][mass couplings][level]:
-  // 0 shared-memory tiles (default), 1 register wavefront (chosen by st_autotune)
-  unsigned char gs_kind[2][2][16];
+  // Gauss-Seidel kernel per [element type: 0 binary64, 1 binary32, 2 double-float][mass
+  // couplings][level]: 0 shared-memory tiles (default), 1 register wavefront (st_autotune)
+  unsigned char gs_kind[3][2][16];
   // CUDA graphs of the PCG iteration bodies (0: binary64 PCG, 1: binary32 inner PCG,
   // 2: binary64 PCG with binary32 preconditioner), re-captured when `graph_key` changes
   cudaGraphExec_t graph_exec[3];
@@ -219,6 +222,7 @@ st_status cuda_fail(const char* where, cudaError_t e);
 // ---------------------------------------------------------------------------------------
 cudaError_t launch_make_coef(Coef<double>* coef, int K, int J, double alpha, Phys ph, int dim, cudaStream_t s);
 cudaError_t launch_make_coef32(Coef<float>* coef, int K, int J, double alpha, Phys ph, int dim, cudaStream_t s);
+cudaError_t launch_make_coef_df(Coef<df64>* coef, int K, int J, double alpha, Phys ph, int dim, cudaStream_t s);
 
 // The operator launchers below are instantiated for T = double and T = float; the float
 // versions reuse the handle's double workspace (half of each buffer).

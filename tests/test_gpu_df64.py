@@ -1,0 +1,94 @@
+"""ST_FP64_DF: the binary64 solver with every multigrid application in double-float arithmetic.
+
+Double-float carries about 48 significant bits: its sums and products are correctly rounded to
+within 2^-48 relative (twice binary32's 24 bits, from the error-free transformations), against
+2^-53 for binary64.  The parity tolerances of the binary64 tests (1e-12 for operators, derived
+from 2^-53) therefore scale by 2^5 = 32 for the operators that run the multigrid; solutions must
+meet the same 1e-10 target as binary64, the multigrid's rounding being far below it.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import schur  # noqa: E402
+from paper_2009_08875_gb300 import Solver, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL_OP = 32 * 1e-12
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("K,J,domain", [(2, 2, 0), (5, 3, 0), (7, 3, 0), (5, 3, 1)])
+def test_operators(K, J, domain):
+    p = schur.Problem(K, J, domain)
+    with Solver(K, J, domain=domain, precision="fp64_df") as s:
+        b = inputs.random_state(2 * p.Nt, p.Nx, 101)
+        x = torch.empty((2 * p.Nt, s.Nx), dtype=torch.float64, device="cuda")
+        s.apply_Kx(dev(inputs.to_grid(K, domain, b)), x)
+        assert rel(inputs.from_grid(K, domain, host(x)), p.Kx.apply(b.T).T) < TOL_OP
+        w = inputs.random_state(p.Nt, p.Nx, 102)
+        y = torch.empty(s.shape, dtype=torch.float64, device="cuda")
+        s.apply_S(dev(inputs.to_grid(K, domain, w)), y)
+        assert rel(inputs.from_grid(K, domain, host(y)), p.to_inplace(p.apply_Shat(p.from_inplace(w)))) < TOL_OP
+        s.apply_KX(dev(inputs.to_grid(K, domain, w)), y)
+        assert rel(inputs.from_grid(K, domain, host(y)), p.to_inplace(p.apply_KX(p.from_inplace(w)))) < TOL_OP
+
+
+@pytest.mark.parametrize("domain", [0, 1])
+def test_solve_meets_fp64_target(domain):
+    K, J = 5, 4
+    p = schur.Problem(K, J, domain)
+    g, u0, _ = inputs.manufactured(K, J, domain)
+    u_ref, _, _ = schur.solve(p, g, u0, tol=1e-13)
+    with Solver(K, J, domain=domain, precision="fp64_df", tol=1e-12) as s:
+        u = torch.zeros(s.shape, dtype=torch.float64).pin_memory()
+        s.solve_host(torch.from_numpy(inputs.to_grid(K, domain, g)).pin_memory(),
+                     torch.from_numpy(inputs.to_grid(K, domain, u0)).pin_memory(), u)
+    assert rel(inputs.from_grid(K, domain, u.numpy()), u_ref) < 1e-10
+
+
+def test_smoothers_and_batch_bitwise():
+    K, J, B = 6, 3, 3
+    rng = np.random.default_rng(3)
+    x = dev(rng.standard_normal((B, 2 ** J + 1, (2 ** K - 1) ** 2)))
+    with Solver(K, J, batch=B, precision="fp64_df") as s:
+        outs = []
+        for kind in ("tiles", "wavefront"):
+            s.set_smoother(kind)
+            y = torch.empty_like(x)
+            s.apply_KX(x, y)
+            outs.append(y)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[0], outs[1])
+        s.set_smoother("tiles")
+    with Solver(K, J, precision="fp64_df") as s1:
+        y1 = torch.empty_like(x[1])
+        s1.apply_KX(x[1].contiguous(), y1)
+        torch.cuda.synchronize()
+    assert torch.equal(outs[0][1], y1)
+
+
+def test_autotune_keeps_solution_bitwise():
+    K, J = 6, 4
+    g, u0, _ = inputs.manufactured(K, J)
+    with Solver(K, J, precision="fp64_df") as s:
+        u1 = torch.zeros(s.shape, dtype=torch.float64).pin_memory()
+        s.solve_host(torch.from_numpy(g).pin_memory(), torch.from_numpy(u0).pin_memory(), u1)
+        s.autotune()
+        u2 = torch.zeros_like(u1)
+        s.solve_host(torch.from_numpy(g).pin_memory(), torch.from_numpy(u0).pin_memory(), u2)
+    assert torch.equal(u1, u2)
