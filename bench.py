@@ -40,7 +40,14 @@ FP64_INST_PEAK = 1.25e12 / 2.0
 # DRAM traffic (bytes) per finest-level sweep launch from one ncu capture, valid only for the
 # kernel source it was taken on (keyed by the SHA-256 of k_mg.cu, then by (operator, kernel));
 # otherwise reported as null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --set full on K = 9, J = 5 (33 / 66 slices), mean of launches 2 and 3, read + write,
+    # scaled by slices to the full launch (513 / 1026 slices): profiles/k_gs_*_fp64_*_K9_J5.md
+    "a5f55f426cf2e60bc0344eb560a7de0d80f9af6268ca8c85fdb8fb567551f526": {
+        ("Kl", "wavefront"): (154.948e6 + 42.309e6) * 513 / 33,
+        ("Kx", "tiles"): (275.797e6 + 105.506e6) * 1026 / 66,
+    },
+}
 
 
 def parse():
