@@ -160,23 +160,31 @@ __global__ void __launch_bounds__(256) k_gs_sweep(G* __restrict__ x_out, const G
   const int gy0 = blockIdx.y * TY - H;
   const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, level);
 
-  for (int idx = threadIdx.x; idx < HR * kWR; idx += blockDim.x) {
-    int ry = idx / kWR, rx = idx - ry * kWR;
-    int gx = gx0 + rx, gy = gy0 + ry;
-    bool in = gx >= 0 && gx < n && gy >= 0 && gy < n && !outside_domain(gx, gy, n, lshape);
-    int64_t gi = (int64_t)gy * n + gx;
-    if (PROL) {
-      T v = (in && !zero_init) ? T(xin[gi]) : T(0);
-      if (in) v += prolong_value<T>(xcs, nc, gx + 1, gy + 1);
-      xs[idx] = v;
-    } else {
-      xs[idx] = (in && !zero_init) ? T(xin[gi]) : T(0);
+  // stage the region: warp w takes rows w, w + 8, ..., lane l the columns l, l + 32, l + 64
+  constexpr int kWarps = 8;  // launched with 256 threads
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int ry = warp; ry < HR; ry += kWarps) {
+    const int gy = gy0 + ry;
+    const bool row_in = gy >= 0 && gy < n;
+    const int64_t grow = (int64_t)gy * n;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int rx = lane + 32 * e, idx = ry * kWR + rx;
+      const int gx = gx0 + rx;
+      const bool in = row_in && gx >= 0 && gx < n && !outside_domain(gx, gy, n, lshape);
+      const int64_t gi = grow + gx;
+      if (PROL) {
+        T v = (in && !zero_init) ? T(xin[gi]) : T(0);
+        if (in) v += prolong_value<T>(xcs, nc, gx + 1, gy + 1);
+        xs[idx] = v;
+      } else {
+        xs[idx] = (in && !zero_init) ? T(xin[gi]) : T(0);
+      }
+      bs[idx] = in ? T(bsl[gi]) : T(0);
     }
-    bs[idx] = in ? T(bsl[gi]) : T(0);
   }
   __syncthreads();
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 #pragma unroll 1
   for (int t = 0; t < 3 * NSW; ++t) {
     const int tc = t % 3;
@@ -187,17 +195,21 @@ __global__ void __launch_bounds__(256) k_gs_sweep(G* __restrict__ x_out, const G
     // each warp updates R rows per pass: all operands are gathered before any result is
     // stored, so R independent FP64 chains are in flight (points of one colour never couple)
     constexpr int R = 2;
-    for (int ry0 = ry_lo + warp; ry0 < ry_hi; ry0 += R * nwarp) {
+    // colour (gx + gy + 2) mod 3 == colour  <=>  rx == colour - 2 - gy - gx0 (mod 3): the lane's
+    // active column in row ry is 3 lane + m(ry), and m(ry + 8) = m(ry) + 1, m(ry + 16) = m(ry) - 1
+    // (mod 3), so m is stepped instead of recomputed
+    int m0 = (colour - 2 - gy0 - (ry_lo + warp) - gx0) % 3;
+    m0 += (m0 < 0) ? 3 : 0;
+    for (int ry0 = ry_lo + warp; ry0 < ry_hi; ry0 += R * kWarps) {
       T sx[R], sy[R], sd[R], bv[R];
       int at[R];
+      const int mq[R] = {m0, m0 == 2 ? 0 : m0 + 1};
+      m0 = (m0 == 0) ? 2 : m0 - 1;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const int ry = ry0 + q * nwarp;
+        const int ry = ry0 + q * kWarps;
         const int gy = gy0 + ry;
-        // colour (gx + gy + 2) mod 3 == colour  <=>  rx == colour - 2 - gy - gx0 (mod 3)
-        int m = (colour - 2 - gy - gx0) % 3;
-        m += (m < 0) ? 3 : 0;
-        const int rx = 3 * lane + m;
+        const int rx = 3 * lane + mq[q];
         const bool ok = ry < ry_hi && rx >= rx_lo && rx < rx_hi && !outside_domain(gx0 + rx, gy, n, lshape);
         const int i = ok ? ry * kWR + rx : kWR + 1;  // a harmless interior address when idle
         at[q] = ok ? i : -1;
@@ -218,10 +230,16 @@ __global__ void __launch_bounds__(256) k_gs_sweep(G* __restrict__ x_out, const G
     __syncthreads();
   }
 
-  for (int idx = threadIdx.x; idx < TY * TX; idx += blockDim.x) {
-    int ty = idx / TX, tx = idx - ty * TX;
-    int gx = gx0 + H + tx, gy = gy0 + H + ty;
-    if (gx < n && gy < n) xsl[(int64_t)gy * n + gx] = G(xs[(ty + H) * kWR + tx + H]);
+  // write the tile interior
+  for (int ty = warp; ty < TY; ty += kWarps) {
+    const int gy = gy0 + H + ty;
+    if (gy >= n) break;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int tx = lane + 32 * e;
+      const int gx = gx0 + H + tx;
+      if (tx < TX && gx < n) xsl[(int64_t)gy * n + gx] = G(xs[(ty + H) * kWR + tx + H]);
+    }
   }
 }
 
