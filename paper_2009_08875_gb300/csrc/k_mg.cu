@@ -304,10 +304,8 @@ __global__ void __launch_bounds__(128) k_gs_wave(G* __restrict__ x_out, const G*
   };
 
   // one colour step on row j: xc = row j, xn = row j + 1, xs = row j - 1, bc = b of row j
-  auto update_row = [&](T (&xcr)[3], const T (&xn)[3], const T (&xs)[3], const T (&bc)[3], int j, int s,
-                        int colour) {
-    int m = (colour - 2 - j - gx0) % 3;  // the lane's element of this colour in row j
-    m += (m < 0) ? 3 : 0;
+  // m: the lane's element of the step's colour in row j
+  auto update_row = [&](T (&xcr)[3], const T (&xn)[3], const T (&xs)[3], const T (&bc)[3], int j, int s, int m) {
     const int cl = 3 * lane + m;
     const int gx = cbase + m;
     const bool ok = cl >= s + 1 && cl < kWR - s - 1 && gx >= 0 && gx < n && !outside_domain(gx, j, n, lshape);
@@ -341,7 +339,15 @@ __global__ void __launch_bounds__(128) k_gs_wave(G* __restrict__ x_out, const G*
   const int L = seg + 2 * S;      // rows walked
   const int tau_end = L + S - 1;  // the last row completes at tau = L + S - 2
   const int r1 = min(r0 + seg, n);
-  for (int tau0 = 0; tau0 < tau_end; tau0 += W) {
+  // Step s at time tau updates row j = ybase + tau - s in colour c_s (s mod 3, or 2 - s mod 3 in
+  // reverse); the lane's element of that colour is m = (c_s - 2 - j - gx0) mod 3
+  // = (z - tau + c_s + s) mod 3 with z = (-2 - ybase - gx0) mod 3, and c_s + s = 2 s (forward) or
+  // 2 (reverse) mod 3.  With tz = (z - tau0) mod 3 kept per block of W steps, m is tz plus a
+  // constant of (s, u) reduced once.
+  int tz = (-2 - ybase - gx0) % 3;
+  tz += (tz < 0) ? 3 : 0;
+  constexpr int kStepW = (3 - W % 3) % 3;  // (-W) mod 3: the change of tz per block
+  for (int tau0 = 0; tau0 < tau_end; tau0 += W, tz = (tz + kStepW >= 3) ? tz + kStepW - 3 : tz + kStepW) {
 #pragma unroll
     for (int u = 0; u < W; ++u) {
       const int tau = tau0 + u;
@@ -351,9 +357,11 @@ __global__ void __launch_bounds__(128) k_gs_wave(G* __restrict__ x_out, const G*
         for (int s = 0; s < S; ++s) {
           const int j = ybase + tau - s;
           if (tau - s >= 0 && tau - s < L && j >= 0 && j < n) {
-            const int tc = s % 3;
+            const int cf_ = ((2 * s - u) % 3 + 3) % 3, cr_ = ((2 - u) % 3 + 3) % 3;  // folded at compile time
+            int m = tz + (reverse ? cr_ : cf_);
+            m -= (m >= 3) ? 3 : 0;
             update_row(xw[(u - s + 4 * W) % W], xw[(u - s + 1 + 4 * W) % W], xw[(u - s - 1 + 4 * W) % W],
-                       bw[(u - s + 4 * W) % W], j, s, reverse ? 2 - tc : tc);
+                       bw[(u - s + 4 * W) % W], j, s, m);
           }
         }
         const int ro = ybase + tau - S + 1;
