@@ -43,9 +43,9 @@ FP64_INST_PEAK = 1.25e12 / 2.0
 NCU_TRAFFIC = {
     # ncu --set full on K = 9, J = 5 (33 / 66 slices), mean of launches 2 and 3, read + write,
     # scaled by slices to the full launch (513 / 1026 slices): profiles/k_gs_*_fp64_*_K9_J5.md
-    "a5f55f426cf2e60bc0344eb560a7de0d80f9af6268ca8c85fdb8fb567551f526": {
-        ("Kl", "wavefront"): (154.948e6 + 42.309e6) * 513 / 33,
-        ("Kx", "tiles"): (275.797e6 + 105.506e6) * 1026 / 66,
+    "8dade2f2e0b4f36253c88789feaceae9538fa327db1ef06ea4e12a20649b5cf0": {
+        ("Kl", "wavefront"): (154.960e6 + 42.238e6) * 513 / 33,
+        ("Kx", "tiles"): (275.785e6 + 105.391e6) * 1026 / 66,
     },
 }
 

@@ -432,26 +432,56 @@ __global__ void __launch_bounds__(256) k_residual_restrict(G* __restrict__ bc, c
   const int cx0 = blockIdx.x * kRCX, cy0 = blockIdx.y * kRCY;
   const int fx0 = 2 * cx0, fy0 = 2 * cy0;  // first residual point (fine interior index)
   const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, level);
-  for (int idx = threadIdx.x; idx < kRXY * kRXX; idx += blockDim.x) {
-    const int ry = idx / kRXX, rx = idx - ry * kRXX;
-    const int gx = fx0 - 1 + rx, gy = fy0 - 1 + ry;
-    const bool in = gx >= 0 && gx < n && gy >= 0 && gy < n && !outside_domain(gx, gy, n, lshape);
-    xs[idx] = in ? T(xsl[(int64_t)gy * n + gx]) : T(0);
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < kRFY * kRFX; idx += blockDim.x) {
-    const int ry = idx / kRFX, rx = idx - ry * kRFX;
-    const int gx = fx0 + rx, gy = fy0 + ry;
-    T r = T(0);
-    if (gx < n && gy < n && !outside_domain(gx, gy, n, lshape)) {
-      const int i = (ry + 1) * kRXX + (rx + 1);
-      // scaled residual r' = D^-1 (b - C x) = b' - x - (ax/c) sx - (ay/c) sy - (dg/c) sd
-      T v = T(bsl[(int64_t)gy * n + gx]) - cf.axs * (xs[i - 1] + xs[i + 1]);
-      v -= cf.ays * (xs[i - kRXX] + xs[i + kRXX]);
-      if (DIAG) v -= cf.dgs * (xs[i + kRXX + 1] + xs[i - kRXX - 1]);
-      r = v - xs[i];
+  // scaled residual r' = D^-1 (b - C x) = b' - x - (ax/c) sx - (ay/c) sy - (dg/c) sd at fine point
+  // (fx0 + rx, gy), 0 outside the grid or the domain
+  auto residual_at = [&](int rx, int ry, int gy) -> T {
+    const int gx = fx0 + rx;
+    if (gx >= n || gy >= n || outside_domain(gx, gy, n, lshape)) return T(0);
+    const int i = (ry + 1) * kRXX + (rx + 1);
+    T v = T(bsl[(int64_t)gy * n + gx]) - cf.axs * (xs[i - 1] + xs[i + 1]);
+    v -= cf.ays * (xs[i - kRXX] + xs[i + kRXX]);
+    if (DIAG) v -= cf.dgs * (xs[i + kRXX + 1] + xs[i - kRXX - 1]);
+    return v - xs[i];
+  };
+  if constexpr (sizeof(T) == 4) {
+    // binary32 is bound by instruction issue: rows by warp and columns by lane, no division
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarps = 8;  // launched with 256 threads
+    for (int ry = warp; ry < kRXY; ry += kWarps) {
+      const int gy = fy0 - 1 + ry;
+      const bool row_in = gy >= 0 && gy < n;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const int rx = lane + 32 * e;
+        if (rx >= kRXX) break;
+        const int gx = fx0 - 1 + rx;
+        const bool in = row_in && gx >= 0 && gx < n && !outside_domain(gx, gy, n, lshape);
+        xs[ry * kRXX + rx] = in ? T(xsl[(int64_t)gy * n + gx]) : T(0);
+      }
     }
-    rs[idx] = r;
+    __syncthreads();
+    for (int ry = warp; ry < kRFY; ry += kWarps) {
+      const int gy = fy0 + ry;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const int rx = lane + 32 * e;
+        if (rx >= kRFX) break;
+        rs[ry * kRFX + rx] = residual_at(rx, ry, gy);
+      }
+    }
+  } else {
+    // binary64 is bound by the FP64 pipe: flat loops keep every lane busy
+    for (int idx = threadIdx.x; idx < kRXY * kRXX; idx += blockDim.x) {
+      const int ry = idx / kRXX, rx = idx - ry * kRXX;
+      const int gx = fx0 - 1 + rx, gy = fy0 - 1 + ry;
+      const bool in = gx >= 0 && gx < n && gy >= 0 && gy < n && !outside_domain(gx, gy, n, lshape);
+      xs[idx] = in ? T(xsl[(int64_t)gy * n + gx]) : T(0);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kRFY * kRFX; idx += blockDim.x) {
+      const int ry = idx / kRFX, rx = idx - ry * kRFX;
+      rs[idx] = residual_at(rx, ry, fy0 + ry);
+    }
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < kRCX * kRCY; idx += blockDim.x) {
