@@ -58,7 +58,8 @@ struct Group {
   std::vector<Request*> slot;  // nullptr = free
   std::vector<int> joining;    // slots started this round
   Clock::time_point last_used;
-  bool stepped = false;
+  cudaEvent_t done = nullptr;  // recorded after the scalar readback of the iteration in flight
+  bool in_flight = false;
 };
 
 // Device bytes of a group (the allocation plan of st_setup_batch, rounded up).
@@ -112,6 +113,7 @@ Group* find_group(st_server_s* s, const Request* r) {
 }
 
 bool group_idle(const Group* g) {
+  if (g->in_flight) return false;
   for (Request* q : g->slot)
     if (q) return false;
   return true;
@@ -120,6 +122,7 @@ bool group_idle(const Group* g) {
 void release_group(st_server_s* s, size_t i) {
   Group* g = s->groups[i].get();
   st_destroy(g->h);
+  if (g->done) cudaEventDestroy(g->done);
   cudaStreamDestroy(g->stream);
   s->allocated -= g->bytes;
   s->groups.erase(s->groups.begin() + i);
@@ -150,7 +153,13 @@ Group* make_group(st_server_s* s, const Request* r) {
     cudaGetLastError();
     return nullptr;
   }
+  if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(g->stream);
+    return nullptr;
+  }
   if (st_setup_batch(&g->h, r->domain, r->K, r->J, slots, &s->cfg, g->stream) != ST_OK) {
+    cudaEventDestroy(g->done);
     cudaStreamDestroy(g->stream);
     return nullptr;
   }
@@ -205,6 +214,7 @@ void worker_loop(st_server_s* s) {
       if (s->error != ST_OK) return;
     }
     // 1-2. admission and start of the admitted problems
+    bool admitted = false;
     for (auto it = waiting.begin(); it != waiting.end();) {
       Request* r = *it;
       Group* g = find_group(s, r);
@@ -220,6 +230,10 @@ void worker_loop(st_server_s* s) {
           continue;
         }
         ++it;  // no room now: try again next round
+        continue;
+      }
+      if (g->in_flight) {  // joins when the group's current iteration has completed
+        ++it;
         continue;
       }
       int b = 0;
@@ -241,13 +255,18 @@ void worker_loop(st_server_s* s) {
         r->started = Clock::now();
         r->state = REQ_RUNNING;
       }
+      admitted = true;
       it = waiting.erase(it);
     }
-    // 3. one iteration of every group with an active slot
+    // 3. an iteration on every group that has occupied slots and none in flight; groups run
+    // independently on their own streams, so a large problem does not hold back small ones
+    bool progressed = admitted;
     for (auto& gp : s->groups) {
       Group* g = gp.get();
-      g->stepped = !group_idle(g);
-      if (!g->stepped) continue;
+      if (g->in_flight) continue;
+      bool occupied = false;
+      for (Request* q : g->slot) occupied = occupied || q != nullptr;
+      if (!occupied) continue;
       if (!g->joining.empty()) {
         st_status st = push_active(g->h);
         if (st != ST_OK) return fail_server(s, st, "active flags");
@@ -258,15 +277,22 @@ void worker_loop(st_server_s* s) {
       while (nb > 0 && !g->slot[nb - 1]) --nb;
       st_status st = step_enqueue(g->h, nb);
       if (st != ST_OK) return fail_server(s, st, "iteration");
+      cudaError_t e = cudaEventRecord(g->done, g->stream);
+      if (e != cudaSuccess) return fail_server(s, cuda_fail("event record", e), "iteration");
+      g->in_flight = true;
       g->last_used = Clock::now();
+      progressed = true;
     }
-    // 4. stop tests, results of finished problems
+    // 4. stop tests and results of every group whose iteration has completed
     for (auto& gp : s->groups) {
       Group* g = gp.get();
-      if (!g->stepped) continue;
+      if (!g->in_flight) continue;
+      cudaError_t e = cudaEventQuery(g->done);
+      if (e == cudaErrorNotReady) continue;
+      if (e != cudaSuccess) return fail_server(s, cuda_fail("iteration", e), "iteration");
+      g->in_flight = false;
+      progressed = true;
       st_handle h = g->h;
-      cudaError_t e = cudaStreamSynchronize(g->stream);
-      if (e != cudaSuccess) return fail_server(s, cuda_fail("stream synchronize", e), "iteration");
       bool changed = false;
       std::vector<int> done;
       std::vector<char> stop(g->slots, 0);  // 1 cancelled, 2 past the deadline
@@ -335,6 +361,7 @@ void worker_loop(st_server_s* s) {
       }
     }
     ++s->rounds;
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
 

@@ -122,7 +122,7 @@ def test_lanczos_estimate_matches_dense_kappa():
 
 
 def test_multigrid_preconditioned_kappa_stays_bounded():
-    # K_X optimal (Thm. 3.1): kappa does not grow with the levels (survey pin P-9, observed plateau)
+    # K_X optimal (Thm. 3.1): kappa does not grow with the levels (an observed plateau)
     ks = []
     for K, J in [(2, 2), (3, 3), (4, 4), (4, 6)]:
         p = schur.Problem(K, J)
