@@ -102,6 +102,8 @@ typedef struct {
                           positive definite and c >= 0 (else ST_ERR_ARG); D = Id, c = 0 is
                           the heat equation.  st_apply_Kx_static always uses the heat
                           equation's A_x.                                                 */
+  int initial_guess;   /* 1: st_pcg_solve starts from the content of w (r = f_hat - S_hat w);
+                          0 (default): from w = 0 as in Sec. 3.4                          */
 } st_config;
 
 /* Fills *cfg with the paper's settings (alpha 0.3, 2 V-cycles, 3+3 sweeps, Sec. 5.1),
@@ -163,7 +165,8 @@ st_status st_apply_KX(st_handle h, const double* r, double* z);
 st_status st_rhs(st_handle h, const double* g_nodal, const double* u0_nodal, double* fhat);
 
 /* PCG on S_hat w = f_hat with preconditioner K_X (Sec. 3.4), starting from w = 0 (the
- * input content of w is ignored and overwritten).  Stops by cfg.tol / cfg.tol_mode.
+ * input content of w is ignored and overwritten) or, with cfg.initial_guess = 1, from the
+ * content of w.  Stops by cfg.tol / cfg.tol_mode.
  * Synchronises the bound stream once per iteration (8 scalars read back).
  * *iters receives the iteration count; *relres sqrt(r^T K_X r / r_0^T K_X r_0).
  * With cfg.precision = ST_MIXED_FP32 (or ST_MIXED_BF16) the solve is iterative refinement: each outer step

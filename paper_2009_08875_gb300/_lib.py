@@ -19,7 +19,8 @@ class StConfig(ctypes.Structure):
                 ("n_post", ctypes.c_int), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("inner_maxit", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("diffusion", ctypes.c_double * 3), ("reaction", ctypes.c_double)]
+                ("diffusion", ctypes.c_double * 3), ("reaction", ctypes.c_double),
+                ("initial_guess", ctypes.c_int)]
 
 
 class StSolveInfo(ctypes.Structure):

@@ -655,6 +655,7 @@ void st_default_config(st_config* cfg) {
   cfg->diffusion[1] = 0.0;
   cfg->diffusion[2] = 1.0;
   cfg->reaction = 0.0;
+  cfg->initial_guess = 0;
 }
 
 const char* st_last_error(void) { return g_last_error.c_str(); }
@@ -905,7 +906,10 @@ st_status st_rhs(st_handle h, const double* g, const double* u0, double* fhat) {
 st_status st_pcg_solve(st_handle h, const double* fhat, double* w, int* iters, double* relres) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(fhat && w, "st_pcg_solve: null pointer");
-  return pcg_impl(h, fhat, w, iters, relres);
+  h->use_guess = h->cfg.initial_guess != 0;
+  const st_status s = pcg_impl(h, fhat, w, iters, relres);
+  h->use_guess = false;
+  return s;
 }
 
 st_status st_solve_info_get(st_handle h, st_solve_info* out) {

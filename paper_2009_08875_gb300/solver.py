@@ -31,7 +31,7 @@ class Solver:
 
     def __init__(self, K, J, domain=0, alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0,
                  maxit=200, precision="fp64", inner_tol=1e-5, inner_maxit=60, batch=1, use_graphs=True,
-                 stream=None, D=None, c=0.0):
+                 stream=None, D=None, c=0.0, initial_guess=False):
         import torch
         lib = _lib.load()
         cfg = _lib.StConfig()
@@ -43,6 +43,7 @@ class Solver:
                          "fp64_df": _lib.ST_FP64_DF}[precision]
         cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
         cfg.use_graphs = 1 if use_graphs else 0
+        cfg.initial_guess = 1 if initial_guess else 0
         _set_phys(cfg, D, c)
         if stream is None:
             stream = torch.cuda.current_stream()
