@@ -5,18 +5,20 @@
  * parabolic evolution equations", arXiv 2009.08875.  The library computes the paper's
  * hot path: PCG on  S_hat w = f_hat  (Sec. 3.4), S_hat = W^T S W, with S in the form of
  * Lemma 4.2 and the wavelet-in-time, multigrid-in-space preconditioner K_X (Thm. 3.1),
- * for u' - Laplace(u) = g on a uniformly refined P1 triangulation of the unit square,
- * P1 in time, three-point wavelets in time (Sec. 5).
+ * for u' - Laplace(u) = g (Sec. 5), or u' - div(D grad u) + c u = g (Sec. 4), on uniformly
+ * refined P1 meshes of the unit square, an L-shape and the unit cube, P1 in time, three-point
+ * wavelets in time; with reduced-precision variants, nested iteration, batches of problems, a
+ * solve server and the building blocks of a solve whose time axis is split over processes.
  *
  * ---------------------------------------------------------------------------------------
  * Conventions shared by every entry point
  * ---------------------------------------------------------------------------------------
- * Sizes.  Space level K >= 1: N_x = (2^K - 1)^2 interior nodes (Sec. 5.1).  Time level
- *   J >= 1: N_t = 2^J + 1 time nodes.
+ * Sizes.  Space level K >= 1: N_x = (2^K - 1)^2 interior nodes (Sec. 5.1; (2^K - 1)^3 on the
+ *   cube).  Time level J >= 1: N_t = 2^J + 1 time nodes.
  * Domains.  0: the unit square (Sec. 5.1).  1: the L-shape (0,1)^2 minus [1/2,1)^2 (not in the
  *   paper), K >= 2; it is stored on the same (2^K - 1)^2 grid, and the grid nodes with
  *   x >= 1/2 and y >= 1/2 (ix >= 2^(K-1) - 1 and iy >= 2^(K-1) - 1) are outside it: inputs must
- *   hold zeros there and outputs hold zeros there.
+ *   hold zeros there and outputs hold zeros there.  2: the unit cube (Sec. 5.2), see st_setup.
  * Layout.  A space-time vector is a dense row-major array of N_t x N_x doubles (time
  *   slowest).  Column p = iy * (2^K - 1) + ix is interior grid node (ix + 1, iy + 1) at
  *   (x, y) = ((ix+1) h, (iy+1) h), h = 2^-K.
@@ -90,8 +92,8 @@ typedef struct {
                        1: stop when sqrt(r^T K_X r) <= tol (Eq. 3.3, the paper's rule)      */
   int maxit;        /* PCG iteration limit                                                  */
   int precision;    /* st_precision                                                         */
-  double inner_tol; /* ST_MIXED_FP32: relative K_X-norm reduction of each inner solve        */
-  int inner_maxit;  /* ST_MIXED_FP32: iteration limit of each inner solve                    */
+  double inner_tol; /* ST_MIXED_FP32 / _BF16: relative K_X-norm reduction of each inner solve */
+  int inner_maxit;  /* ST_MIXED_FP32 / _BF16: iteration limit of each inner solve            */
   int use_graphs;   /* 1: capture each PCG iteration body once as a CUDA graph and replay it
                        (only on a stream other than the legacy/per-thread default streams
                        and outside st_profile_begin/end); 0: plain launches               */
@@ -108,7 +110,7 @@ typedef struct {
 
 /* Fills *cfg with the paper's settings (alpha 0.3, 2 V-cycles, 3+3 sweeps, Sec. 5.1),
  * tol 1e-10 relative, maxit 200, FP64; inner_tol 1e-5, inner_maxit 60, use_graphs 1;
- * D = Id, c = 0 (the heat equation of Sec. 5). */
+ * D = Id, c = 0 (the heat equation of Sec. 5); initial_guess 0. */
 void st_default_config(st_config* cfg);
 
 /* Creates a handle for `domain` at space level K and time level J (1..14), binds it to
@@ -118,7 +120,8 @@ void st_default_config(st_config* cfg);
  *   1  L-shape (0,1)^2 minus [1/2,1)^2 stored on the square's grid with zeros outside,
  *      K in 2..12;
  *   2  unit cube, K in 1..8, N_x = (2^K - 1)^3, P1 on the six Kuhn tetrahedra of every grid
- *      cube (the 3D problem of Sec. 5.2); D = Id only, c >= 0; not ST_MIXED_BF16;
+ *      cube (the 3D problem of Sec. 5.2); D = Id only, c >= 0; not ST_MIXED_BF16 nor
+ *      ST_FP64_DF;
  *      the column index is (iz (2^K - 1) + iy) (2^K - 1) + ix.
  * The multigrid's coarsest level is 1 (one unknown) on the square and the cube and 2 (five
  * unknowns, dense solve) on the L-shape.  cfg may be NULL (defaults).  Synchronous. */
@@ -237,8 +240,9 @@ typedef struct st_batch_s* st_batch;
 /* Creates an empty batch solved with *cfg (NULL: defaults) on the current device. */
 st_status st_batch_create(st_batch* out, const st_config* cfg);
 
-/* Registers one problem: g_host (N_t x N_x), u0_host (N_x), result u_host (N_t x N_x) in the
- * layout of st_solve_host.  *id (may be NULL) receives its index (0, 1, ...). */
+/* Registers one problem (domain 0, 1 or 2 with the levels st_setup accepts): g_host (N_t x N_x),
+ * u0_host (N_x), result u_host (N_t x N_x) in the layout of st_solve_host.  *id (may be NULL)
+ * receives its index (0, 1, ...). */
 st_status st_batch_add(st_batch b, int domain, int space_level, int time_level, const double* g_host,
                        const double* u0_host, double* u_host, int* id);
 

@@ -114,8 +114,8 @@ st_status st_batch_add(st_batch b, int domain, int space_level, int time_level, 
     set_error("st_batch_add: null pointer");
     return ST_ERR_ARG;
   }
-  if ((domain != 0 && domain != 1) || space_level < 1 || space_level > 12 || (domain == 1 && space_level < 2) ||
-      time_level < 1 || time_level > 14) {
+  if ((domain != 0 && domain != 1 && domain != 2) || space_level < 1 || space_level > 12 ||
+      (domain == 1 && space_level < 2) || (domain == 2 && space_level > 8) || time_level < 1 || time_level > 14) {
     set_error("st_batch_add: invalid domain or levels");
     return ST_ERR_ARG;
   }

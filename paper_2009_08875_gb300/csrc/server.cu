@@ -63,12 +63,13 @@ struct Group {
 };
 
 // Device bytes of a group (the allocation plan of st_setup_batch, rounded up).
-size_t group_bytes(int K, int J, int slots, int precision) {
+size_t group_bytes(int domain, int K, int J, int slots, int precision) {
+  const int dim = domain == 2 ? 3 : 2;
   const double n = (double)((1 << K) - 1);
   const double Nt = (double)((1 << J) + 1);
-  const double V = slots * Nt * n * n;
+  const double V = slots * Nt * std::pow(n, dim);
   double coarse = 0.0;
-  for (int k = 1; k < K; ++k) coarse += 3.0 * 2.0 * slots * Nt * ((1 << k) - 1) * ((1 << k) - 1);
+  for (int k = 1; k < K; ++k) coarse += 3.0 * 2.0 * slots * Nt * std::pow((double)((1 << k) - 1), dim);
   double floats = precision == ST_MIXED_PRECOND ? 2.0
                   : ((precision == ST_MIXED_FP32 || precision == ST_MIXED_BF16) ? 5.0 : 0.0);
   return (size_t)(8.0 * (26.0 * V + coarse) + 4.0 * floats * V + 64.0 * 1024 * 1024);
@@ -96,11 +97,11 @@ struct st_server_s {
 
 namespace {
 
-int slots_for(st_server_s* s, int K, int J) {
+int slots_for(st_server_s* s, int domain, int K, int J) {
   const int nt = (1 << J) + 1;
   int c = std::min(s->slots_per_group, 65535 / (2 * nt));
   // a group may use at most a quarter of the budget
-  while (c > 1 && group_bytes(K, J, c, s->cfg.precision) > s->budget / 4) c /= 2;
+  while (c > 1 && group_bytes(domain, K, J, c, s->cfg.precision) > s->budget / 4) c /= 2;
   return std::max(c, 1);
 }
 
@@ -131,8 +132,8 @@ void release_group(st_server_s* s, size_t i) {
 // Creates a group for r's shape if the budget allows, releasing idle groups (least recently
 // used first) to make room.  Returns nullptr if it cannot be made now.
 Group* make_group(st_server_s* s, const Request* r) {
-  const int slots = slots_for(s, r->K, r->J);
-  const size_t need = group_bytes(r->K, r->J, slots, s->cfg.precision);
+  const int slots = slots_for(s, r->domain, r->K, r->J);
+  const size_t need = group_bytes(r->domain, r->K, r->J, slots, s->cfg.precision);
   while (s->allocated + need > s->budget) {
     size_t victim = s->groups.size();
     for (size_t i = 0; i < s->groups.size(); ++i)
@@ -414,8 +415,8 @@ st_status st_server_submit_deadline(st_server s, int domain, int space_level, in
     set_error("st_server_submit: timeout must not be NaN");
     return ST_ERR_ARG;
   }
-  if ((domain != 0 && domain != 1) || space_level < 1 || space_level > 12 || (domain == 1 && space_level < 2) ||
-      time_level < 1 || time_level > 14) {
+  if ((domain != 0 && domain != 1 && domain != 2) || space_level < 1 || space_level > 12 ||
+      (domain == 1 && space_level < 2) || (domain == 2 && space_level > 8) || time_level < 1 || time_level > 14) {
     set_error("st_server_submit: invalid domain or levels");
     return ST_ERR_ARG;
   }

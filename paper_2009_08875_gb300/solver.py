@@ -224,7 +224,7 @@ class Batch:
 
     def add(self, domain, K, J, g, u0, u):
         n = 2 ** K - 1
-        Nt, Nx = 2 ** J + 1, n * n
+        Nt, Nx = 2 ** J + 1, (n ** 3 if domain == 2 else n * n)
         ids = ctypes.c_int()
         _lib.check(_lib.load().st_batch_add(self._h, domain, K, J, _ptr(g, (Nt, Nx), "g", False),
                                             _ptr(u0, (Nx,), "u0", False), _ptr(u, (Nt, Nx), "u", False),
@@ -279,7 +279,7 @@ class Server:
     def submit(self, domain, K, J, g, u0, u, timeout=None):
         """Queue a solve; with timeout (seconds) it fails with ST_ERR_TIMEOUT if not done by then."""
         n = 2 ** K - 1
-        Nt, Nx = 2 ** J + 1, n * n
+        Nt, Nx = 2 ** J + 1, (n ** 3 if domain == 2 else n * n)
         t = ctypes.c_int64()
         _lib.check(_lib.load().st_server_submit_deadline(self._h, domain, K, J, _ptr(g, (Nt, Nx), "g", False),
                                                          _ptr(u0, (Nx,), "u0", False),

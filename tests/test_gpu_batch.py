@@ -97,7 +97,7 @@ def test_batched_operators_equal_single():
 def test_multi_shape_runner_equals_alone(precision):
     from paper_2009_08875_gb300 import Batch
     rng = np.random.default_rng(7)
-    shapes = [(0, 4, 3), (0, 5, 4), (1, 4, 3), (0, 4, 3), (0, 5, 4), (1, 5, 3), (0, 4, 3)]
+    shapes = [(0, 4, 3), (0, 5, 4), (1, 4, 3), (0, 4, 3), (0, 5, 4), (1, 5, 3), (0, 4, 3), (2, 3, 3), (2, 3, 3)]
     bt = Batch(precision=precision, tol=1e-10)
     probs = []
     for i, (dom, K, J) in enumerate(shapes):
@@ -108,7 +108,7 @@ def test_multi_shape_runner_equals_alone(precision):
         assert bt.add(dom, K, J, g, u0, u) == i
         probs.append((dom, K, J, g, u0, u))
     assert bt.run() == 0
-    assert bt.buckets() == 4
+    assert bt.buckets() == 5
     for i, (dom, K, J, g, u0, u) in enumerate(probs):
         with Solver(K, J, domain=dom, precision=precision, tol=1e-10) as s:
             ua = torch.zeros_like(u)

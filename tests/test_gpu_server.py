@@ -44,7 +44,8 @@ def wait_all(srv, tickets, timeout=120):
 
 @pytest.mark.parametrize("precision", ["mixed_precond", "fp64"])
 def test_server_results_equal_alone(precision):
-    shapes = [(0, 4, 3), (0, 5, 4), (1, 4, 4), (0, 4, 3), (0, 5, 4), (0, 4, 3), (1, 4, 4), (0, 6, 3)]
+    shapes = [(0, 4, 3), (0, 5, 4), (1, 4, 4), (0, 4, 3), (2, 3, 3), (0, 5, 4), (0, 4, 3), (1, 4, 4), (0, 6, 3),
+              (2, 3, 3)]
     reqs = [make_request(d, K, J, 10 + i) for i, (d, K, J) in enumerate(shapes)]
     srv = Server(slots_per_group=2, memory_budget_gb=40.0, precision=precision, tol=1e-10)
     tickets = []
