@@ -349,10 +349,13 @@ st_status st_vec_dot(st_handle h, int64_t n, const double* a, const double* b, d
 st_status st_vec_axpby(st_handle h, int64_t n, double alpha, const double* x, double beta, double* y);
 
 /* Autotuner (not in the paper).  Two Gauss-Seidel kernels compute identical sweeps: shared-
- * memory tiles (the default) and a register wavefront.  For every multigrid level above the
- * coarsest, for binary64 and binary32 and for K_x (no mass couplings, 2 B N_t slices) and K_l
- * (mass couplings, B N_t slices), this times one pre-smoothing launch of each on the handle's
- * workspace and keeps the faster for later calls on this handle.  Synchronous.
+ * memory tiles (the default) and a register wavefront, whose strips of 90 columns are cut into
+ * row segments walked by separate warps.  For every multigrid level above the coarsest, for
+ * binary64 and binary32 and for K_x (no mass couplings, 2 B N_t slices) and K_l (mass
+ * couplings, B N_t slices), this times one pre-smoothing launch of the tiles and of the
+ * wavefront at ceil(n / q) rows per segment, q = 1 .. 12 (n = 2^k - 1 on level k), on the
+ * handle's workspace and keeps the fastest kernel and segment length for later calls on this
+ * handle.  Synchronous.
  * times_ms (may be NULL) receives 8 x 16 floats: times_ms[8 k + i] for level k and i = 0..7 in
  * the order (binary64 K_x: tiles, wavefront; binary64 K_l: tiles, wavefront; binary32 K_x:
  * tiles, wavefront; binary32 K_l: tiles, wavefront). */
@@ -362,6 +365,12 @@ st_status st_autotune(st_handle h, float* times_ms);
  * state after set-up), 1 register wavefront.  Both give bitwise the same sweeps.  Returns
  * ST_ERR_ARG for any other kind. */
 st_status st_set_smoother(st_handle h, int kind);
+
+/* Forces the register wavefront's rows per segment on every level of this handle (rows >= 1;
+ * values above a level's n = 2^k - 1 mean one segment per strip; 0 restores the compiled
+ * default of 64).  Any segment length gives bitwise the same sweeps.  Returns ST_ERR_ARG unless
+ * 0 <= rows <= 65535. */
+st_status st_set_wave_rows(st_handle h, int rows);
 
 /* Measurement hooks (not part of the method).  Between st_profile_begin and st_profile_end the
  * handle counts every kernel it launches and brackets each finest-level Gauss-Seidel sweep

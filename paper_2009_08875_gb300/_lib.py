@@ -80,6 +80,7 @@ _SIGS = {
     "st_nested_solve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P,
                                        ctypes.POINTER(ctypes.c_int)]),
     "st_set_smoother": (ctypes.c_int, [_P, ctypes.c_int]),
+    "st_set_wave_rows": (ctypes.c_int, [_P, ctypes.c_int]),
     "st_profile_begin": (ctypes.c_int, [_P]),
     "st_profile_end": (ctypes.c_int, [_P, ctypes.POINTER(StProfile)]),
     "st_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(StConfig)]),

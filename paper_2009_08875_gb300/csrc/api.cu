@@ -960,6 +960,22 @@ st_status st_autotune(st_handle h, float* times_ms) {
   return ST_OK;
 }
 
+st_status st_set_wave_rows(st_handle h, int rows) {
+  ST_CHECK(check_handle(h));
+  if (rows < 0 || rows > 65535) {
+    set_error("st_set_wave_rows: rows must be in 0 .. 65535");
+    return ST_ERR_ARG;
+  }
+  for (auto& a : h->gs_seg)
+    for (auto& b : a)
+      for (auto& c : b) c = (unsigned short)rows;
+  for (int i = 0; i < 3; ++i) {
+    if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
+    h->graph_exec[i] = nullptr;
+  }
+  return ST_OK;
+}
+
 st_status st_set_smoother(st_handle h, int kind) {
   ST_CHECK(check_handle(h));
   if (kind != 0 && kind != 1) {

@@ -200,17 +200,18 @@ __global__ void __launch_bounds__(256) k_gs_sweep(G* __restrict__ x_out, const G
     // (mod 3), so m is stepped instead of recomputed
     int m0 = (colour - 2 - gy0 - (ry_lo + warp) - gx0) % 3;
     m0 += (m0 < 0) ? 3 : 0;
-    for (int ry0 = ry_lo + warp; ry0 < ry_hi; ry0 += R * kWarps) {
-      T sx[R], sy[R], sd[R], bv[R];
-      int at[R];
-      const int mq[R] = {m0, m0 == 2 ? 0 : m0 + 1};
-      m0 = (m0 == 0) ? 2 : m0 - 1;
+    // one pass over RR rows ry0, ry0 + 8, ...; every row of it lies below ry_hi
+    auto pass = [&](auto rr, int ry0, int m_first) {
+      constexpr int RR = decltype(rr)::value;
+      T sx[RR], sy[RR], sd[RR], bv[RR];
+      int at[RR];
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
+      for (int q = 0; q < RR; ++q) {
         const int ry = ry0 + q * kWarps;
         const int gy = gy0 + ry;
-        const int rx = 3 * lane + mq[q];
-        const bool ok = ry < ry_hi && rx >= rx_lo && rx < rx_hi && !outside_domain(gx0 + rx, gy, n, lshape);
+        const int mq = q == 0 ? m_first : (m_first == 2 ? 0 : m_first + 1);
+        const int rx = 3 * lane + mq;
+        const bool ok = rx >= rx_lo && rx < rx_hi && !outside_domain(gx0 + rx, gy, n, lshape);
         const int i = ok ? ry * kWR + rx : kWR + 1;  // a harmless interior address when idle
         at[q] = ok ? i : -1;
         sx[q] = xs[i - 1] + xs[i + 1];
@@ -219,13 +220,31 @@ __global__ void __launch_bounds__(256) k_gs_sweep(G* __restrict__ x_out, const G
         bv[q] = bs[i];
       }
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
+      for (int q = 0; q < RR; ++q) {
         // scaled system: x = b' - (ax/c) sx - (ay/c) sy - (dg/c) sd with b' = b / c
         T v = bv[q] - cf.axs * sx[q];
         v -= cf.ays * sy[q];
         if (DIAG) v -= cf.dgs * sd[q];
         if (at[q] >= 0) xs[at[q]] = v;
       }
+    };
+    if (!PROL && zero_init && t == 0) {
+      // the first colour of a sweep from x = 0 sees only zero neighbours: x = b'
+      for (int ry = ry_lo + warp; ry < ry_hi; ry += kWarps, m0 = (m0 == 2) ? 0 : m0 + 1) {
+        const int rx = 3 * lane + m0;
+        if (rx >= rx_lo && rx < rx_hi && !outside_domain(gx0 + rx, gy0 + ry, n, lshape))
+          xs[ry * kWR + rx] = bs[ry * kWR + rx];
+      }
+      __syncthreads();
+      continue;
+    }
+    for (int ry0 = ry_lo + warp; ry0 < ry_hi; ry0 += R * kWarps) {
+      // the second row is skipped by the whole warp (a uniform branch) when it lies past ry_hi
+      if (ry0 + kWarps < ry_hi)
+        pass(std::integral_constant<int, 2>(), ry0, m0);
+      else
+        pass(std::integral_constant<int, 1>(), ry0, m0);
+      m0 = (m0 == 0) ? 2 : m0 - 1;
     }
     __syncthreads();
   }
@@ -316,6 +335,19 @@ __global__ void __launch_bounds__(128) k_gs_wave(G* __restrict__ x_out, const G*
     if (DIAG) {
       up_s2 = shfl_up(xs[2], 1);
       dn_n0 = shfl_down(xn[0], 1);
+    }
+    if (!PROL && zero_init && s == 0) {
+      // the first colour step of a sweep from x = 0 sees only zero neighbours: x = b'
+      // (m is warp-uniform; constant indices keep the rows in registers)
+      if (ok) {
+        if (m == 0)
+          xcr[0] = bc[0];
+        else if (m == 1)
+          xcr[1] = bc[1];
+        else
+          xcr[2] = bc[2];
+      }
+      return;
     }
     if (m == 0) {
       T v = bc[0] - cf.axs * (up_c2 + xcr[1]);
@@ -532,7 +564,7 @@ const Coef<df64>* coef_table<df64>(const st_handle_s* h) {
 template <typename T>
 struct SweepShape;
 #ifndef ST_GS_HR64
-#define ST_GS_HR64 32
+#define ST_GS_HR64 34
 #endif
 #ifndef ST_GS_HR32
 #define ST_GS_HR32 64
@@ -555,6 +587,12 @@ template <>
 struct SweepShape<float> {
   static constexpr int kFusedNSW = ST_GS_NSW32, kFusedHR = ST_GS_HR32, kSingleHR = 64;
 };
+
+// the autotuner's element-type index: 0 binary64, 1 binary32, 2 double-float
+template <typename T>
+constexpr int type_slot() {
+  return std::is_same<T, df64>::value ? 2 : (sizeof(T) == 4 ? 1 : 0);
+}
 
 template <typename T, typename G, int NSW, int HR, bool DIAG, bool PROL>
 cudaError_t gs_launch(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in, const G* b,
@@ -586,7 +624,9 @@ cudaError_t wave_launch(const st_handle_s* h, int k, int nslices, int cls, G* x_
   const int n = (1 << k) - 1;
   const int TXW = kWR - 2 * S;
   const int nstrips = (n + TXW - 1) / TXW;
-  const int seg = ST_GS_SEG;
+  // rows per segment: the autotuned or forced choice, else the compiled default; at most n
+  const int chosen = h->gs_seg[type_slot<T>()][DIAG ? 1 : 0][k];
+  const int seg = min(chosen > 0 ? chosen : ST_GS_SEG, n);
   const int nseg = (n + seg - 1) / seg;
   const int64_t warps = (int64_t)nstrips * nseg * nslices;
   const unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
@@ -606,11 +646,6 @@ cudaError_t wave_launch(const st_handle_s* h, int k, int nslices, int cls, G* x_
 // (x_in == x_out is not allowed)
 // Which Gauss-Seidel kernel a launch uses: the handle's autotuned choice per element type,
 // coupling pattern and level (0: shared-memory tiles, the default; 1: register wavefront).
-template <typename T>
-constexpr int type_slot() {
-  return std::is_same<T, df64>::value ? 2 : (sizeof(T) == 4 ? 1 : 0);
-}
-
 template <typename T>
 int gs_kind(const st_handle_s* h, bool diag, int k) {
   return h->gs_kind[type_slot<T>()][diag ? 1 : 0][k];
@@ -835,22 +870,26 @@ cudaError_t mg_apply_bf16(const st_handle_s* h, int nslices, int coef_class, con
 
 // Times both Gauss-Seidel kernels on every level of the handle's shapes (the pre-smoothing
 // launch of a V-cycle: K_x on 2 B N_t slices, K_l on B N_t slices) and keeps the faster per
-// element type, coupling pattern and level.  Uses the workspace as scratch.
+// element type, coupling pattern and level.  The wavefront is timed at several segment lengths,
+// ceil(n / q) rows for q = 1 .. 12 segments per strip: fewer segments recompute fewer overlap
+// rows (2 S per segment), more segments fill the GPU's last wave of warps better.  Uses the
+// workspace as scratch.
 template <typename T, bool DIAG>
 cudaError_t autotune_one(st_handle_s* h, int k, float* ms_tile, float* ms_wave) {
   const int nslices = (int)((DIAG ? 1 : 2) * h->B * h->Nt);
   const int cls = DIAG ? -1 : 0;
+  const int n = (1 << k) - 1;
   T* xo = reinterpret_cast<T*>(h->X);
   const T* xi = reinterpret_cast<const T*>(h->Xalt);
   const T* b = reinterpret_cast<const T*>(h->Bs);
   const int nsw = SweepShape<T>::kFusedNSW;
+  unsigned char& kind_sel = h->gs_kind[type_slot<T>()][DIAG ? 1 : 0][k];
+  unsigned short& seg_sel = h->gs_seg[type_slot<T>()][DIAG ? 1 : 0][k];
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best[2] = {0.f, 0.f};
   cudaError_t err = cudaSuccess;
-  for (int kind = 0; kind < 2 && err == cudaSuccess; ++kind) {
-    h->gs_kind[type_slot<T>()][DIAG ? 1 : 0][k] = (unsigned char)kind;
+  auto time_it = [&](float* out) {
     float t = 1e30f;
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
       cudaEventRecord(e0, h->stream);
@@ -861,13 +900,31 @@ cudaError_t autotune_one(st_handle_s* h, int k, float* ms_tile, float* ms_wave) 
       if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
       if (rep > 0) t = ms < t ? ms : t;  // the first run warms up
     }
-    best[kind] = t;
+    *out = t;
+  };
+  float t_tile = 1e30f, t_wave = 1e30f;
+  int best_seg = 0, last_seg = -1;
+  kind_sel = 0;
+  time_it(&t_tile);
+  kind_sel = 1;
+  for (int q = 1; q <= 12 && err == cudaSuccess; ++q) {
+    const int seg = (n + q - 1) / q;
+    if (seg == last_seg) continue;
+    last_seg = seg;
+    seg_sel = (unsigned short)seg;
+    float t;
+    time_it(&t);
+    if (t < t_wave) {
+      t_wave = t;
+      best_seg = seg;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->gs_kind[type_slot<T>()][DIAG ? 1 : 0][k] = best[1] < best[0] ? 1 : 0;
-  *ms_tile = best[0];
-  *ms_wave = best[1];
+  kind_sel = t_wave < t_tile ? 1 : 0;
+  seg_sel = (unsigned short)best_seg;
+  *ms_tile = t_tile;
+  *ms_wave = t_wave;
   return err;
 }
 

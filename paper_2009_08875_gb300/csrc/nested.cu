@@ -127,6 +127,7 @@ st_status st_nested_solve(st_handle h, int levels, double eps, double rate, cons
     st_status s = st_setup_batch(&h->nest[m], h->domain, h->K - m, h->J - m, h->B, &h->cfg, h->stream);
     if (s != ST_OK) return s;
     std::memcpy(h->nest[m]->gs_kind, h->gs_kind, sizeof(h->gs_kind));
+    std::memcpy(h->nest[m]->gs_seg, h->gs_seg, sizeof(h->gs_seg));
   }
   // data of every level by injection from the next finer one
   for (int m = 1; m < levels; ++m) {

@@ -180,6 +180,8 @@ struct st_handle_s {
   // Gauss-Seidel kernel per [element type: 0 binary64, 1 binary32, 2 double-float][mass
   // couplings][level]: 0 shared-memory tiles (default), 1 register wavefront (st_autotune)
   unsigned char gs_kind[3][2][16];
+  // rows per segment of the register wavefront, same indices (0: the compiled default)
+  unsigned short gs_seg[3][2][16];
   // CUDA graphs of the PCG iteration bodies (0: binary64 PCG, 1: binary32 inner PCG,
   // 2: binary64 PCG with binary32 preconditioner), re-captured when `graph_key` changes
   cudaGraphExec_t graph_exec[3];

@@ -175,6 +175,10 @@ class Solver:
         """Force the Gauss-Seidel kernel on every level: 'tiles' or 'wavefront' (st_set_smoother)."""
         _lib.check(_lib.load().st_set_smoother(self._h, {"tiles": 0, "wavefront": 1}[kind]))
 
+    def set_wave_rows(self, rows):
+        """Rows per segment of the wavefront kernel on every level, 0 for the default (st_set_wave_rows)."""
+        _lib.check(_lib.load().st_set_wave_rows(self._h, int(rows)))
+
     def profile_begin(self):
         """Start counting launches and timing finest-level sweeps (measurement hook)."""
         _lib.check(_lib.load().st_profile_begin(self._h))

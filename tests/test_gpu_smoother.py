@@ -3,8 +3,8 @@
 Both kernels perform the same three-colour sweeps with the same summation order per point, so
 every operator that runs the multigrid preconditioner (K_x, K_X, and the binary32 K_X) must give
 bitwise the same result with either, on the square and on the L-shape, for one problem and for a
-batch.  The autotuner only picks between them, so a solve after st_autotune must give bitwise the
-solve before it.
+batch, and the wavefront at any number of rows per segment.  The autotuner only picks among
+them, so a solve after st_autotune must give bitwise the solve before it.
 """
 import numpy as np
 import pytest
@@ -46,15 +46,20 @@ def test_tiles_and_wavefront_bitwise_equal(K, J, domain, B):
         s.set_smoother("tiles")
         a = run_ops(s, x)
         s.set_smoother("wavefront")
-        b = run_ops(s, x)
-        for name in a:
-            assert torch.equal(a[name], b[name]), name
+        # default segments, then one row per segment, a ragged length, and one segment per strip
+        for rows in (0, 1, 5, 73, 1000):
+            s.set_wave_rows(rows)
+            b = run_ops(s, x)
+            for name in a:
+                assert torch.equal(a[name], b[name]), (name, rows)
 
 
 def test_set_smoother_rejects_unknown_kind():
     from paper_2009_08875_gb300 import _lib
     with Solver(3, 2) as s:
         assert _lib.load().st_set_smoother(s._h, 2) == 1  # ST_ERR_ARG
+        assert _lib.load().st_set_wave_rows(s._h, -1) == 1
+        assert _lib.load().st_set_wave_rows(s._h, 65536) == 1
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed_precond"])
