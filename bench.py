@@ -43,9 +43,10 @@ FP64_INST_PEAK = 1.25e12 / 2.0
 NCU_TRAFFIC = {
     # ncu --set full on K = 9, J = 5 (33 / 66 slices), mean of launches 2 and 3, read + write,
     # scaled by slices to the full launch (513 / 1026 slices): profiles/k_gs_*_fp64_*_K9_J5.md
-    "8dade2f2e0b4f36253c88789feaceae9538fa327db1ef06ea4e12a20649b5cf0": {
-        ("Kl", "wavefront"): (154.960e6 + 42.238e6) * 513 / 33,
-        ("Kx", "tiles"): (275.785e6 + 105.391e6) * 1026 / 66,
+    "fbbb9feca2f5b908c1dd8cdc03a94637ac39987f9e2f2cb61535e684a608ac61": {
+        ("Kl", "tiles"): (137.904e6 + 36.602e6) * 513 / 33,
+        ("Kx", "tiles"): (275.811e6 + 105.295e6) * 1026 / 66,
+        ("Kl", "wavefront"): (154.946e6 + 42.377e6) * 513 / 33,
     },
 }
 
