@@ -557,8 +557,24 @@ def run_ours(args):
             t = torch.tensor([dt], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = t.item()
+        # the copies alone, timed on the solver's stream: what the host buffers add to a solve
+        gd = torch.empty_like(gh, device="cuda")
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k2 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(solver.stream):
+            k0.record()
+            gd.copy_(gh, non_blocking=True)
+            k1.record()
+            uh.copy_(gd, non_blocking=True)
+            k2.record()
+        torch.cuda.synchronize()
+        h2d_ms, d2h_ms = k0.elapsed_time(k1), k1.elapsed_time(k2)
+        del gd
         e2e = {"value": world * N * its_e / dt, "unit": "DoF-iter/s",
-               "h2d_bytes_per_step": (g_np.size + u0_np.size) * 8, "d2h_bytes_per_step": N * 8}
+               "h2d_bytes_per_step": (g_np.size + u0_np.size) * 8, "d2h_bytes_per_step": N * 8,
+               "ms_per_solve": dt * 1e3 / max(1, args.steps), "h2d_gbs": gh.numel() * 8 / h2d_ms / 1e6,
+               "d2h_gbs": uh.numel() * 8 / d2h_ms / 1e6}
 
     # mixed precision (binary32 inner PCG under binary64 refinement) on the same workload:
     # same tolerance, solution compared with the FP64 solution of the timed region
