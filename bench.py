@@ -43,10 +43,10 @@ FP64_INST_PEAK = 1.25e12 / 2.0
 NCU_TRAFFIC = {
     # ncu --set full on K = 9, J = 5 (33 / 66 slices), mean of launches 2 and 3, read + write,
     # scaled by slices to the full launch (513 / 1026 slices): profiles/k_gs_*_fp64_*_K9_J5.md
-    "fbbb9feca2f5b908c1dd8cdc03a94637ac39987f9e2f2cb61535e684a608ac61": {
-        ("Kl", "tiles"): (137.904e6 + 36.602e6) * 513 / 33,
-        ("Kx", "tiles"): (275.811e6 + 105.295e6) * 1026 / 66,
-        ("Kl", "wavefront"): (154.946e6 + 42.377e6) * 513 / 33,
+    "b694fb98c455126ba5435ca8313f1298e9652647f2ffc371902fd9db7298e6e2": {
+        ("Kl", "tiles"): (137.924e6 + 36.499e6) * 513 / 33,
+        ("Kx", "tiles"): (275.788e6 + 105.357e6) * 1026 / 66,
+        ("Kl", "wavefront"): (154.963e6 + 41.567e6) * 513 / 33,
     },
 }
 

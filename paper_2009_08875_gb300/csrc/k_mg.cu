@@ -173,14 +173,29 @@ __global__ void __launch_bounds__(256) k_gs_sweep(G* __restrict__ x_out, const G
       const int gx = gx0 + rx;
       const bool in = row_in && gx >= 0 && gx < n && !outside_domain(gx, gy, n, lshape);
       const int64_t gi = grow + gx;
-      if (PROL) {
-        T v = (in && !zero_init) ? T(xin[gi]) : T(0);
-        if (in) v += prolong_value<T>(xcs, nc, gx + 1, gy + 1);
-        xs[idx] = v;
-      } else {
-        xs[idx] = (in && !zero_init) ? T(xin[gi]) : T(0);
-      }
+      if (!PROL) xs[idx] = (in && !zero_init) ? T(xin[gi]) : T(0);
       bs[idx] = in ? T(bsl[gi]) : T(0);
+    }
+    if (PROL) {
+      // x + P xc, lane l taking the columns 3 l .. 3 l + 2, where the colour of element e is the
+      // same in every lane.  The points of the first colour step's colour c0 are overwritten by
+      // that step, which reads only other colours, and no earlier read touches them, so their
+      // old values and corrections are not formed (a warp-uniform branch; they hold 0).
+      // colour (gx + gy + 2) mod 3 == c0  <=>  e == c0 - 2 - gy - gx0 (mod 3)
+      int eskip = ((reverse ? 2 : 0) - 2 - gy - gx0) % 3;
+      eskip += (eskip < 0) ? 3 : 0;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const int rx = 3 * lane + e, idx = ry * kWR + rx;
+        const int gx = gx0 + rx;
+        T v = T(0);
+        if (e != eskip) {
+          const bool in = row_in && gx >= 0 && gx < n && !outside_domain(gx, gy, n, lshape);
+          if (in && !zero_init) v = T(xin[grow + gx]);
+          if (in) v += prolong_value<T>(xcs, nc, gx + 1, gy + 1);
+        }
+        xs[idx] = v;
+      }
     }
   }
   __syncthreads();
@@ -309,14 +324,23 @@ __global__ void __launch_bounds__(128) k_gs_wave(G* __restrict__ x_out, const G*
 #pragma unroll
     for (int e = 0; e < 3; ++e) xw[r][e] = bw[r][e] = T(0);
 
+  // Row r into registers.  The points of step 0's colour c0 are overwritten by step 0, which
+  // reads only other colours, before any read of them that matters (a row past the walked rows
+  // is never updated and counts among the missing neighbours above), so their old values and
+  // corrections are not loaded: element e has colour c0 in every lane for one e per row.
   auto load_row = [&](int r, T (&xr)[3], T (&br)[3]) {
+    int eskip = ((reverse ? 2 : 0) - 2 - r - gx0) % 3;  // colour (gx + r + 2) mod 3 == c0
+    eskip += (eskip < 0) ? 3 : 0;
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       const int gx = cbase + e;
       const bool in = r >= 0 && r < n && gx >= 0 && gx < n && !outside_domain(gx, r, n, lshape);
       const int64_t gi = (int64_t)r * n + gx;
-      T v = (in && !zero_init) ? T(xin[gi]) : T(0);
-      if (PROL && in) v += prolong_value<T>(xcs, nc, gx + 1, r + 1);
+      T v = T(0);
+      if (e != eskip) {
+        if (in && !zero_init) v = T(xin[gi]);
+        if (PROL && in) v += prolong_value<T>(xcs, nc, gx + 1, r + 1);
+      }
       xr[e] = v;
       br[e] = in ? T(bsl[gi]) : T(0);
     }
