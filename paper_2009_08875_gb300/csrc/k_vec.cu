@@ -2,6 +2,8 @@
 // same grid, the same partition and the same summation order on every call, so results are
 // bitwise reproducible), and the axpy updates of the Hestenes-Stiefel recurrences, which read
 // their scalars from device memory so the loop needs no host round trip except the stop test.
+#include <type_traits>
+
 #include "st_internal.cuh"
 
 namespace st {
@@ -28,7 +30,7 @@ __device__ double block_sum(double v) {
   return t;  // valid in thread 0
 }
 
-// inner products always accumulate in binary64, whatever the vectors' storage type.  Problem
+// inner products accumulate in binary64 partial sums, whatever the vectors' storage type.  Problem
 // blockIdx.y of a batch owns elements [y n, (y + 1) n); its partial sums go to
 // partials[y * gridDim.x + blockIdx.x].  The partition depends only on n, so a problem gives the
 // same bits alone and inside any batch.
@@ -37,15 +39,34 @@ __global__ void __launch_bounds__(256) k_dot_partial(const Ta* __restrict__ a, c
                                                      double* __restrict__ partials) {
   a += (int64_t)blockIdx.y * n;
   b += (int64_t)blockIdx.y * n;
-  double acc0 = 0.0, acc1 = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (; i + stride < n; i += 2 * stride) {
-    acc0 = fma((double)a[i], (double)b[i], acc0);
-    acc1 = fma((double)a[i + stride], (double)b[i + stride], acc1);
+  double t;
+  if constexpr (std::is_same<Ta, float>::value && std::is_same<Tb, float>::value) {
+    // binary32 vectors: a product of two floats is exactly p + e (p = fl(a b), e = fma(a, b, -p)),
+    // summed in double-float (about 48 bits, well inside the binary64 partial sums it feeds) and
+    // converted once per thread.  This keeps the loop off the binary64 pipe, which GB300 runs at
+    // 1/58 of the binary32 rate: widening and a binary64 fma per element made the dot bound by it.
+    df64 acc0(0.0f), acc1(0.0f);
+    auto prod = [](float x, float y) {
+      const float p = __fmul_rn(x, y);
+      return df64(p, __fmaf_rn(x, y, -p), 0);
+    };
+    for (; i + stride < n; i += 2 * stride) {
+      acc0 += prod(a[i], b[i]);
+      acc1 += prod(a[i + stride], b[i + stride]);
+    }
+    if (i < n) acc0 += prod(a[i], b[i]);
+    t = block_sum(double(acc0) + double(acc1));
+  } else {
+    double acc0 = 0.0, acc1 = 0.0;
+    for (; i + stride < n; i += 2 * stride) {
+      acc0 = fma((double)a[i], (double)b[i], acc0);
+      acc1 = fma((double)a[i + stride], (double)b[i + stride], acc1);
+    }
+    if (i < n) acc0 = fma((double)a[i], (double)b[i], acc0);
+    t = block_sum(acc0 + acc1);
   }
-  if (i < n) acc0 = fma((double)a[i], (double)b[i], acc0);
-  double t = block_sum(acc0 + acc1);
   if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
