@@ -116,3 +116,18 @@ def test_multi_shape_runner_equals_alone(precision):
         assert torch.equal(u, ua), i
         assert bt.info(i)["iterations"] == its
     bt.close()
+
+
+def test_empty_batch_and_rejected_shapes():
+    # a batch without problems runs no bucket; shapes outside the accepted levels (the cube above
+    # K = 8, the L-shape at K = 1, domain 3, K = 13, J = 15, J = 0) are rejected before any copy
+    from paper_2009_08875_gb300 import Batch, _lib
+    bt = Batch(precision="fp64")
+    assert bt.run() == _lib.ST_OK and bt.buckets() == 0
+    buf = torch.zeros(4, dtype=torch.float64)
+    p = buf.data_ptr()
+    lib = _lib.load()
+    for dom, K, J in ((2, 9, 3), (1, 1, 3), (3, 4, 3), (0, 13, 3), (0, 4, 15), (0, 4, 0)):
+        assert lib.st_batch_add(bt._h, dom, K, J, p, p, p, None) == _lib.ST_ERR_ARG, (dom, K, J)
+    assert bt.run() == _lib.ST_OK and bt.buckets() == 0
+    bt.close()

@@ -116,3 +116,24 @@ def test_cancel_and_deadline():
     assert res[t_ok]["state"] == Server.DONE and res[t_ok]["status"] == _lib.ST_OK
     u_alone, its = alone(*big[3][:5], "mixed_precond")
     assert torch.equal(big[3][5], u_alone) and res[t_ok]["iterations"] == its
+
+
+def test_server_rejects_bad_requests_and_stops_empty():
+    # invalid shapes and a NaN timeout are rejected at submission; unknown tickets at poll and
+    # cancel; a server that never got a request stops cleanly
+    import ctypes
+
+    from paper_2009_08875_gb300 import _lib
+    lib = _lib.load()
+    srv = Server(slots_per_group=1, memory_budget_gb=1.0, tol=1e-10)
+    buf = torch.zeros(4, dtype=torch.float64)
+    p = buf.data_ptr()
+    t = ctypes.c_int64(-1)
+    for dom, K, J in ((2, 9, 3), (1, 1, 3), (3, 4, 3), (0, 13, 3), (0, 4, 15), (0, 4, 0)):
+        assert lib.st_server_submit_deadline(srv._h, dom, K, J, p, p, p, 0.0, ctypes.byref(t)) == _lib.ST_ERR_ARG
+    assert lib.st_server_submit_deadline(srv._h, 0, 4, 3, p, p, p, float("nan"), ctypes.byref(t)) == _lib.ST_ERR_ARG
+    assert t.value == -1
+    state = ctypes.c_int()
+    assert lib.st_server_poll(srv._h, 0, ctypes.byref(state), None, None, None) == _lib.ST_ERR_ARG
+    assert lib.st_server_cancel(srv._h, 5) == _lib.ST_ERR_ARG
+    srv.stop()
