@@ -40,7 +40,7 @@ class Solver:
         cfg.tol, cfg.tol_mode, cfg.maxit = tol, tol_mode, maxit
         cfg.precision = {"fp64": _lib.ST_FP64, "mixed": _lib.ST_MIXED_FP32,
                          "mixed_precond": _lib.ST_MIXED_PRECOND, "mixed_bf16": _lib.ST_MIXED_BF16,
-                         "fp64_df": _lib.ST_FP64_DF}[precision]
+                     "fp64_df": _lib.ST_FP64_DF}[precision]
         cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
         cfg.use_graphs = 1 if use_graphs else 0
         cfg.initial_guess = 1 if initial_guess else 0
@@ -208,7 +208,7 @@ def _config(alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0, ma
     cfg.tol, cfg.tol_mode, cfg.maxit = tol, tol_mode, maxit
     cfg.precision = {"fp64": _lib.ST_FP64, "mixed": _lib.ST_MIXED_FP32,
                      "mixed_precond": _lib.ST_MIXED_PRECOND, "mixed_bf16": _lib.ST_MIXED_BF16,
-                         "fp64_df": _lib.ST_FP64_DF}[precision]
+                     "fp64_df": _lib.ST_FP64_DF}[precision]
     cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
     cfg.use_graphs = 1 if use_graphs else 0
     _set_phys(cfg, D, c)
