@@ -375,7 +375,7 @@ st_status st_set_wave_rows(st_handle h, int rows);
 /* Measurement hooks (not part of the method).  Between st_profile_begin and st_profile_end the
  * handle counts every kernel it launches and brackets each finest-level Gauss-Seidel sweep
  * launch (the dominant kernel) with a pair of CUDA events on the bound stream, adding up the
- * launch's algorithmic work: per point and sweep 4 FP64 operations for K_x (3 adds, 1 fma; 6
+ * launch's algorithmic work: per point and sweep 4 FP64 operations for K_x (2 adds, 2 fmas; 6
  * with the mass couplings of K_l: 1 more add and fma), and 3 values moved (read x and b, write
  * x; 2 on a sweep that starts from x = 0) of the element type.  st_profile_end synchronises
  * the stream and reports the sums, in total and for the sweeps with mass couplings alone. */
