@@ -4,9 +4,11 @@ Tolerances as in test_gpu_parity: operators 1e-12 of their largest entry (the sa
 formulas, summation order and the Jacobi-scaled Gauss-Seidel form differ), solutions 1e-10,
 mixed-precision solutions 1e-8.  K = 4 has 15^3 points per slice, K = 1 the single-unknown
 degenerate case.  The paper's 3D weak-scaling runs (Table 5.5, N_x = 250047, eps = 1e-6,
-u = exp(-3 pi^2 t) sin sin sin) give the iteration counts checked at the end, within the margin
-that the multigrid reading costs in 2D as well (a few iterations, see the 2D Table 5.3 test).
+u = exp(-3 pi^2 t) sin sin sin, tests/golden/table_5_5_iterations.txt) give the iteration counts
+checked at the end, within one iteration.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -94,12 +96,26 @@ def test_cube_nested_matches_oracle():
     assert rel(w.cpu().numpy(), p.to_inplace(w_ref)) < 1e-10
 
 
-# Table 5.5 (3D weak scaling): N_x = 250047 (K = 6); N_t = 129 -> 15 iterations, 257 -> 16
-@pytest.mark.parametrize("J,paper_its", [(7, 15), (8, 16)])
-def test_cube_table_5_5_iterations(J, paper_its):
+def _table_5_5():
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table_5_5_iterations.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                a, b = line.split()
+                rows.append((int(a), int(b)))
+    return rows
+
+
+# Table 5.5 (3D weak scaling) at N_x = 250047 (K = 6), the rows up to N_t = 513: the count must
+# be the paper's within one iteration (the paper's smoother ordering is not stated; measured:
+# 15, 16, 16, the paper's counts)
+@pytest.mark.parametrize("Nt,paper_its", [r for r in _table_5_5() if r[0] <= 513])
+def test_cube_table_5_5_iterations(Nt, paper_its):
     K = 6
+    J = Nt.bit_length() - 1
+    assert 2 ** J + 1 == Nt
     g, u0, _ = inputs.decaying(K, J, CUBE)
     with Solver(K, J, domain=CUBE, tol=1e-6, tol_mode=1, maxit=100) as s:
         u = torch.zeros(s.shape, dtype=torch.float64).pin_memory()
         its, _ = s.solve_host(torch.from_numpy(g).pin_memory(), torch.from_numpy(u0).pin_memory(), u)
-    assert paper_its - 1 <= its <= paper_its + 6, its
+    assert abs(its - paper_its) <= 1, its
