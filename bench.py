@@ -283,6 +283,24 @@ def run_batch_workload(args):
     return res
 
 
+def serve_arrivals(rate, seconds, seed=0):
+    """(time, domain, K, J) of seeded Poisson arrivals at `rate` per second over `seconds`: domain 0
+    (square) or 1 (L-shape) with probability 1/2, K and J independent with P(4 + k) proportional
+    to 2^-k, k = 0..5."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    pk = 2.0 ** -np.arange(6)
+    pk /= pk.sum()
+    t, arrivals = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        dom = int(rng.integers(0, 2))
+        arrivals.append((t, dom, 4 + int(rng.choice(6, p=pk)), 4 + int(rng.choice(6, p=pk))))
+    return arrivals
+
+
 def run_serve_workload(args, seed=0):
     """Seeded Poisson arrivals of solves: domain square / L-shape with probability 1/2 each,
     K and J independent with P(4 + k) proportional to 2^-k (k = 0..5), forcing a random smooth
@@ -292,16 +310,7 @@ def run_serve_workload(args, seed=0):
     import torch
 
     from paper_2009_08875_gb300 import Server, inputs
-    rng = np.random.default_rng(seed)
-    pk = 2.0 ** -np.arange(6)
-    pk /= pk.sum()
-    t, arrivals = 0.0, []
-    while True:
-        t += rng.exponential(1.0 / args.serve_rate)
-        if t > args.serve_seconds:
-            break
-        dom = int(rng.integers(0, 2))
-        arrivals.append((t, dom, 4 + int(rng.choice(6, p=pk)), 4 + int(rng.choice(6, p=pk))))
+    arrivals = serve_arrivals(args.serve_rate, args.serve_seconds, seed)
     # one forcing per shape (the requests' data repeat; outputs of one shape share a buffer,
     # so this measures timing only: correctness of served results is covered by the tests)
     data = {}
