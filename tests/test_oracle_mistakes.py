@@ -1,0 +1,101 @@
+"""Planted mistakes: each test breaks one piece of the oracle the way an implementation plausibly
+could (a transposed or negated term, a dropped term, a wrong shift or level), on CPU, and checks
+that one of the pins that guard the oracle rejects it.  The unbroken oracle passes the same pins
+in test_oracle_schur.py.
+"""
+import numpy as np
+
+from oracle import schur, space
+
+KAPPA_65_49 = 6.34  # Sec. 5.1, Table 5.1: N_t = 65, N_x = 49, direct inverses, alpha = 0.3
+
+
+def _rand(p, seed):
+    return np.random.default_rng(seed).standard_normal((p.Nt, p.Nx))
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _kappa(p):
+    _, info = schur.pcg(p.apply_Shat, p.apply_KX, _rand(p, 1), tol=1e-15, maxit=150)
+    return schur.lanczos_kappa(info["alpha"], info["beta"])[0]
+
+
+def test_transposed_or_negated_L_breaks_lemma_4_1_equals_4_2():
+    # Lemma 4.2's cross terms are L^T kron M K A and L kron A K M; route (i) does not use L.
+    # Transposing L changes S by (L^T - L) kron (M K A - A K M), which vanishes for K = A^-1 and is
+    # of the size of the multigrid's error otherwise: far above the pin's 1e-13, as is a sign error
+    for mutate, floor in ((lambda L: L.T.copy(), 1e-6), (lambda L: -L, 1e-3)):
+        p = schur.Problem(3, 3)
+        U = _rand(p, 7)
+        s1 = p.apply_S_route1(U)
+        assert _rel(p.apply_S_route2(U), s1) <= 1e-13
+        p.L = mutate(p.L)
+        assert _rel(p.apply_S_route2(U), s1) > floor
+
+
+def test_dropped_initial_trace_term_breaks_the_closed_form():
+    # without Gamma_0 = e_0 e_0^T (kron M) the Gram-matrix closed form of S no longer holds
+    p = schur.Problem(3, 3, inverses="direct")
+    M, A = p.Mx.toarray(), p.Ax.toarray()
+    eN = np.zeros((p.Nt, p.Nt))
+    eN[-1, -1] = 1.0
+    S_closed = np.kron(p.At, M @ np.linalg.solve(A, M)) + np.kron(p.Mt, A) + np.kron(eN, M)
+    assert _rel(schur.dense(p.apply_S, (p.Nt, p.Nx)), S_closed) <= 1e-13
+    p.Gamma0 = 0.0 * p.Gamma0
+    assert _rel(schur.dense(p.apply_S, (p.Nt, p.Nx)), S_closed) > 1e-3
+
+
+def test_wrong_shift_or_level_offset_in_K_X_misses_table_5_1():
+    # K_l ~ (alpha A + 2^l M)^-1 with the detail d_j on level j + 1 reproduces Table 5.1; 4^l
+    # instead of 2^l, or d_j on level j, does not
+    p = schur.Problem(3, 6, inverses="direct")
+    assert abs(_kappa(p) - KAPPA_65_49) <= 0.01 * KAPPA_65_49
+    q = schur.Problem(3, 6, inverses="direct")
+    q.Kl = {l: space.DirectInverse(3, space.SQUARE, 0.3, 4.0 ** l) for l in q.Kl}
+    assert abs(_kappa(q) - KAPPA_65_49) > 0.05 * KAPPA_65_49
+    r = schur.Problem(3, 6, inverses="direct")
+    r.levels = np.maximum(r.levels - 1, 0)
+    assert abs(_kappa(r) - KAPPA_65_49) > 0.05 * KAPPA_65_49
+
+
+def test_unscaled_wavelets_miss_table_5_1():
+    # the detail functions carry the factor 2^((j+1)/2) of Eq. 3.1 (L2 normalisation); dropping it
+    # (W's columns of level l divided by 2^(l/2)) leaves K_X mis-scaled against S_hat
+    p = schur.Problem(3, 6, inverses="direct")
+    scale = 2.0 ** (-0.5 * p.levels.astype(float))
+    p.W = p.W @ np.diag(scale)
+    assert abs(_kappa(p) - KAPPA_65_49) > 0.05 * KAPPA_65_49
+
+
+class _MirroredMesh(space.Mesh):
+    """The same grid with every cell cut along the other diagonal, (I+1, J)-(I, J+1)."""
+
+    def __init__(self, level):
+        super().__init__(level)
+        m = self.m
+        I, J = np.meshgrid(np.arange(m), np.arange(m), indexing="xy")
+        I, J = I.ravel(), J.ravel()
+        a = np.stack([np.stack([I, J], 1), np.stack([I + 1, J], 1), np.stack([I, J + 1], 1)], 1)
+        b = np.stack([np.stack([I + 1, J], 1), np.stack([I + 1, J + 1], 1), np.stack([I, J + 1], 1)], 1)
+        self.tri = np.concatenate([a, b], 0)
+
+
+def test_other_diagonal_breaks_the_three_colouring():
+    # the colouring (i + j) mod 3 decouples the 7-point pattern of the (1,1)-diagonal mesh (the
+    # pin in test_oracle_space.py); assembled on the mirrored mesh, mass and stiffness couple
+    # (i, j) with (i + 1, j - 1), which has the same colour
+    for make in (lambda k: space.Mesh(k), _MirroredMesh):
+        m = make(4)
+        col = m.colour()
+        same = []
+        for Mat in (space.mass_matrix(m), space.stiffness_matrix(m)):
+            C = Mat.tocoo()
+            off = (C.row != C.col) & (np.abs(C.data) > 0)
+            same.append(bool(np.any(col[C.row[off]] == col[C.col[off]])))
+        if isinstance(m, _MirroredMesh):
+            assert same[0]        # the mass matrix couples the new diagonal
+        else:
+            assert not any(same)
