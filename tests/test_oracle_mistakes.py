@@ -99,3 +99,31 @@ def test_other_diagonal_breaks_the_three_colouring():
             assert same[0]        # the mass matrix couples the new diagonal
         else:
             assert not any(same)
+
+
+def _bilinear_prolongation(coarse, fine):
+    # Q1 interpolation: a cell-centre node takes the mean of the four cell corners instead of the
+    # two end points of the cell's (1,1) diagonal
+    P = np.zeros((fine.N, coarse.N))
+    for f, (i, j) in enumerate(zip(fine.node_i, fine.node_j)):
+        x, y = i / 2.0, j / 2.0
+        I, J = int(np.floor(x)), int(np.floor(y))
+        for di in (0, 1):
+            for dj in (0, 1):
+                w = (1 - abs(x - (I + di))) * (1 - abs(y - (J + dj)))
+                ci, cj = I + di, J + dj
+                if w > 0 and 0 <= ci <= coarse.m and 0 <= cj <= coarse.m and coarse.dof[cj, ci] >= 0:
+                    P[f, coarse.dof[cj, ci]] += w
+    return P
+
+
+def test_bilinear_prolongation_breaks_galerkin_exactness():
+    # nested P1 spaces make P^T A_f P = A_c exact (the pin in test_oracle_space.py); Q1 weights at
+    # the cell centres do not, although their column sums are the same
+    c, f = space.Mesh(3), space.Mesh(4)
+    Af, Ac = space.stiffness_matrix(f).toarray(), space.stiffness_matrix(c).toarray()
+    P = space.prolongation(c, f).toarray()
+    assert np.abs(P.T @ Af @ P - Ac).max() < 1e-13
+    Q = _bilinear_prolongation(c, f)
+    assert np.allclose(Q.sum(0).max(), P.sum(0).max())
+    assert np.abs(Q.T @ Af @ Q - Ac).max() > 1e-2
