@@ -127,3 +127,22 @@ def test_bilinear_prolongation_breaks_galerkin_exactness():
     Q = _bilinear_prolongation(c, f)
     assert np.allclose(Q.sum(0).max(), P.sum(0).max())
     assert np.abs(Q.T @ Af @ Q - Ac).max() > 1e-2
+
+
+def test_time_matrix_slips_break_the_lemma_4_2_identities():
+    # M_t, A_t and L are assembled independently of the DG test-space matrices T, N, O; the proof
+    # identities N^T O^-1 N = M_t, T^T O^-1 T = A_t, T^T O^-1 N = L^T tie them together.  A corner
+    # of M_t at h/6 instead of h/3, A_t without its corner, or L with the wrong end sign fails them.
+    from oracle import time as tm
+    J = 3
+    t = tm.time_matrices(J)
+    Oi = np.linalg.inv(t["O"])
+    h = 2.0 ** -J
+    Mt, At, L = t["Mt"].copy(), t["At"].copy(), t["L"].copy()
+    assert np.abs(t["N"].T @ Oi @ t["N"] - Mt).max() < 1e-15
+    Mt[0, 0] = h / 6
+    assert np.abs(t["N"].T @ Oi @ t["N"] - Mt).max() > 1e-3
+    At[-1, -1] = 2.0 / h
+    assert np.abs(t["T"].T @ Oi @ t["T"] - At).max() > 1.0
+    L[0, 0] = +0.5
+    assert np.abs(t["T"].T @ Oi @ t["N"] - L.T).max() > 0.5
