@@ -146,3 +146,14 @@ def test_time_matrix_slips_break_the_lemma_4_2_identities():
     assert np.abs(t["T"].T @ Oi @ t["T"] - At).max() > 1.0
     L[0, 0] = +0.5
     assert np.abs(t["T"].T @ Oi @ t["N"] - L.T).max() > 0.5
+
+
+def test_three_colours_do_not_decouple_the_cube():
+    # the Kuhn mesh couples a node with index-sum offsets +-1, +-2 and +-3 (the body diagonal), so
+    # (i + j + k) mod 4 separates every coupled pair and (i + j + k) mod 3 does not
+    m = space.Mesh3(3)
+    C = space.mass_matrix(m).tocoo()
+    off = C.row != C.col
+    s = m.node_i + m.node_j + m.node_k
+    assert np.all(m.colour()[C.row[off]] != m.colour()[C.col[off]])
+    assert np.any((s % 3)[C.row[off]] == (s % 3)[C.col[off]])
