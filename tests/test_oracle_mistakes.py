@@ -157,3 +157,26 @@ def test_three_colours_do_not_decouple_the_cube():
     s = m.node_i + m.node_j + m.node_k
     assert np.all(m.colour()[C.row[off]] != m.colour()[C.col[off]])
     assert np.any((s % 3)[C.row[off]] == (s % 3)[C.col[off]])
+
+
+def test_shifted_injection_or_detail_placement_fail_the_nested_pins():
+    # injection takes coarse time node i from fine node 2i and grid node (i, j) from (2i, 2j): the
+    # odd fine nodes instead give values that are not the coarse mesh's samples; the coarse
+    # solution enters the fine level as its first 2^(J-1) + 1 wavelet rows, and placing it in the
+    # last rows instead is not the space-time P1 interpolation
+    from paper_2009_08875_gb300 import inputs
+    K, J = 5, 4
+    fine, coarse = schur.Problem(K, J), schur.Problem(K - 1, J - 1)
+    g_f = inputs.manufactured(K, J)[0]
+    g_c = inputs.manufactured(K - 1, J - 1)[0]
+    assert np.array_equal(schur.inject_nodal(fine, coarse, g_f), g_c)
+    fi = fine.mesh.dof[2 * coarse.mesh.node_j, 2 * coarse.mesh.node_i]
+    assert np.abs(g_f[1::2][:, fi] - g_c[:-1]).max() > 1e-2       # odd time nodes
+    fi_odd = fine.mesh.dof[2 * coarse.mesh.node_j - 1, 2 * coarse.mesh.node_i - 1]
+    assert np.abs(g_f[::2][:, fi_odd] - g_c).max() > 1e-2          # odd grid nodes
+    # detail placement: the coarse rows go first; moving them to the end changes the function
+    Wc = np.random.default_rng(2).standard_normal((coarse.Nt, coarse.Nx))
+    right = fine.synth(schur.prolong_wavelet(coarse, fine, Wc))
+    wrong = np.zeros((fine.Nt, fine.Nx))
+    wrong[-coarse.Nt:] = schur.prolong_wavelet(coarse, fine, Wc)[:coarse.Nt]
+    assert np.abs(fine.synth(wrong) - right).max() > 1e-2 * np.abs(right).max()
