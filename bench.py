@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=0.25, help="seconds of Poisson arrivals replayed")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate (requests/s)")
+    ap.add_argument("--serve-sweep-requests", type=int, default=150,
+                    help="requests per point of the offered-load sweep (25/50/90%% of capacity)")
     ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--smoother", choices=["auto", "tiles", "wavefront"], default="auto",
                     help="Gauss-Seidel kernel: autotuned per level (default) or one kernel on every level")
@@ -252,35 +254,46 @@ def batch_workload(nprob, seed=0):
 
 
 def run_batch_workload(args):
-    """Many uneven solves through st_batch_* (binary64 PCG with the binary32 preconditioner),
-    host buffers in and out, timed end to end (workspace set-up, copies, solves)."""
+    """Many uneven solves through st_batch_* (config 4), host buffers in and out, timed end to end
+    (workspace set-up, copies, solves), once per precision on the same problems: binary64 PCG
+    (ST_FP64), binary64 refinement around a binary32 inner PCG (ST_MIXED_FP32) and binary64 PCG
+    with the binary32 preconditioner (ST_MIXED_PRECOND).  Each mixed result is compared with the
+    binary64 one of the same problem (max over the problems of max|u - u64| / max|u64|)."""
     import torch
 
     from paper_2009_08875_gb300 import Batch
     probs = batch_workload(args.batch_problems)
-    host = []
-    for K, J, g, u0 in probs:
-        host.append((K, J, torch.from_numpy(g).pin_memory(), torch.from_numpy(u0).pin_memory(),
-                     torch.empty(g.shape, dtype=torch.float64).pin_memory()))
-    res = None
-    for rep in range(2):  # the first run warms up
-        bt = Batch(precision="mixed_precond", tol=TOL, maxit=500)
-        for K, J, g, u0, u in host:
-            bt.add(0, K, J, g, u0, u)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st = bt.run()
-        dt = time.perf_counter() - t0
-        its = [bt.info(i)["iterations"] for i in range(len(host))]
-        dofs = sum(g.numel() for _, _, g, _, _ in host)
-        dof_its = sum(g.numel() * it for (_, _, g, _, _), it in zip(host, its))
-        res = {"problems": len(host), "groups": bt.buckets(), "status": st, "seconds": dt,
-               "solves_per_s": len(host) / dt, "dof_total": dofs, "dof_iters_per_s": dof_its / dt,
-               "iterations_mean": sum(its) / len(its), "iterations_max": max(its),
-               "precision": "f64 PCG, f32 preconditioner", "tol": TOL,
-               "timed": "st_batch_run end to end: workspace set-up, host<->device copies, all solves"}
-        bt.close()
-    return res
+    ins = [(K, J, torch.from_numpy(g).pin_memory(), torch.from_numpy(u0).pin_memory()) for K, J, g, u0 in probs]
+    dofs = sum(g.numel() for _, _, g, _ in ins)
+    arms, ref = {}, None
+    for prec in ("fp64", "mixed", "mixed_precond"):
+        outs = [torch.empty(g.shape, dtype=torch.float64).pin_memory() for _, _, g, _ in ins]
+        res = None
+        for rep in range(2):  # the first run warms up
+            bt = Batch(precision=prec, tol=TOL, maxit=500)
+            for (K, J, g, u0), u in zip(ins, outs):
+                bt.add(0, K, J, g, u0, u)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = bt.run()
+            dt = time.perf_counter() - t0
+            its = [bt.info(i)["iterations"] for i in range(len(ins))]
+            dof_its = sum(g.numel() * it for (_, _, g, _), it in zip(ins, its))
+            res = {"status": st, "seconds": dt, "solves_per_s": len(ins) / dt, "dof_iters_per_s": dof_its / dt,
+                   "iterations_mean": sum(its) / len(its), "iterations_max": max(its), "groups": bt.buckets()}
+            bt.close()
+        if prec == "fp64":
+            ref = outs
+        else:
+            res["max_rel_err_vs_fp64"] = max(((u - r).abs().max() / r.abs().max()).item() for u, r in zip(outs, ref))
+        arms[prec] = res
+    best = max(("mixed", "mixed_precond"), key=lambda k: arms[k]["solves_per_s"])
+    return {"problems": len(ins), "dof_total": dofs, "tol": TOL, "fp64": arms["fp64"], "mixed": arms["mixed"],
+            "mixed_precond": arms["mixed_precond"],
+            "mixed_speedup_vs_fp64": arms[best]["solves_per_s"] / arms["fp64"]["solves_per_s"], "mixed_best": best,
+            "precisions": {"fp64": "f64 PCG", "mixed": "f32 inner PCG under f64 refinement",
+                           "mixed_precond": "f64 PCG, f32 preconditioner"},
+            "timed": "st_batch_run end to end: workspace set-up, host<->device copies, all solves"}
 
 
 def serve_arrivals(rate, seconds, seed=0):
@@ -301,35 +314,44 @@ def serve_arrivals(rate, seconds, seed=0):
     return arrivals
 
 
-def run_serve_workload(args, seed=0):
-    """Seeded Poisson arrivals of solves: domain square / L-shape with probability 1/2 each,
-    K and J independent with P(4 + k) proportional to 2^-k (k = 0..5), forcing a random smooth
-    sum of 8 modes, u0 = 0.  Served by st_server_* (binary64 PCG, binary32 preconditioner,
-    continuous batching); latency = submission to result in host memory."""
-    import numpy as np
+def serve_shapes_data(arrivals):
+    """One forcing per shape (requests of a shape share it and its output buffer: the served runs
+    measure timing; a result is checked per shape, see run_serve_once), pinned host tensors."""
     import torch
 
-    from paper_2009_08875_gb300 import Server, inputs
-    arrivals = serve_arrivals(args.serve_rate, args.serve_seconds, seed)
-    # one forcing per shape (the requests' data repeat; outputs of one shape share a buffer,
-    # so this measures timing only: correctness of served results is covered by the tests)
+    from paper_2009_08875_gb300 import inputs
     data = {}
     for _, dom, K, J in arrivals:
         if (dom, K, J) not in data:
             g, u0 = inputs.smooth_forcing(K, J, seed=K * 16 + J, domain=dom)
             g = torch.from_numpy(inputs.to_grid(K, dom, g)).pin_memory()
             u0 = torch.from_numpy(inputs.to_grid(K, dom, u0)).pin_memory()
-            data[(dom, K, J)] = (g, u0, torch.empty(g.shape, dtype=torch.float64).pin_memory())
-    srv = Server(slots_per_group=8, memory_budget_gb=160.0, tol=TOL, maxit=500)
+            data[(dom, K, J)] = (g, u0, torch.empty(g.shape, dtype=torch.float64).pin_memory(),
+                                 torch.empty(g.shape, dtype=torch.float64).pin_memory())
+    return data
+
+
+def run_serve_once(arrivals, data, precision):
+    """Replays `arrivals` (time, domain, K, J) into a fresh server; latency = submission to result
+    in host memory.  The first request of every shape writes its own buffer (the 4th tensor of
+    data[shape]), which the caller compares across precisions."""
+    import numpy as np
+    import torch
+
+    from paper_2009_08875_gb300 import Server
+    srv = Server(slots_per_group=8, memory_budget_gb=160.0, tol=TOL, maxit=500, precision=precision)
     torch.cuda.synchronize()
+    seen = set()
     t0 = time.perf_counter()
     tickets = []
     for ta, dom, K, J in arrivals:
         now = time.perf_counter() - t0
         if ta > now:
             time.sleep(ta - now)
-        g, u0, u = data[(dom, K, J)]
-        tickets.append((srv.submit(dom, K, J, g, u0, u), dom, K, J))
+        g, u0, u, ufirst = data[(dom, K, J)]
+        out = u if (dom, K, J) in seen else ufirst
+        seen.add((dom, K, J))
+        tickets.append((srv.submit(dom, K, J, g, u0, out), dom, K, J))
     lat, its, failed, pending = [], [], 0, list(tickets)
     while pending:
         rest = []
@@ -348,13 +370,72 @@ def run_serve_workload(args, seed=0):
     srv.stop()
     dof = sum(data[(d, K, J)][0].numel() for _, d, K, J in tickets)
     lat_ms = np.array(lat) * 1e3
-    return {"offered_rate_per_s": args.serve_rate, "arrival_window_s": args.serve_seconds, "requests": len(tickets),
-            "failed": failed, "makespan_s": makespan, "served_per_s": len(lat) / makespan,
+    return {"requests": len(tickets), "failed": failed, "makespan_s": makespan, "served_per_s": len(lat) / makespan,
+            "offered_per_s": len(tickets) / max(arrivals[-1][0], 1e-9) if arrivals else 0.0,
             "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat) else None,
             "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat) else None,
-            "iterations_mean": float(np.mean(its)) if its else None, "dof_total": dof,
-            "precision": "f64 PCG, f32 preconditioner", "tol": TOL,
-            "note": "offered load exceeds capacity: latency includes queueing behind the backlog"}
+            "iterations_mean": float(np.mean(its)) if its else None, "dof_total": dof}
+
+
+def run_serve_workload(args, seed=0):
+    """Config 5: seeded Poisson arrivals of solves (domain square / L-shape with probability 1/2,
+    K and J independent with P(4 + k) proportional to 2^-k, k = 0..5, forcing a random smooth sum
+    of 8 modes, u0 = 0) served by st_server_* (continuous batching), for binary64 PCG and for the
+    binary64 PCG with the binary32 preconditioner.  First at the offered 2000/s (far above
+    capacity: latency is queueing behind the backlog), then at 25 / 50 / 90 % of the capacity that
+    run measured, with a fixed number of requests each."""
+    out = {"offered_rate_per_s": args.serve_rate, "arrival_window_s": args.serve_seconds, "tol": TOL,
+           "precisions": {"fp64": "f64 PCG", "mixed_precond": "f64 PCG, f32 preconditioner"}}
+    arrivals = serve_arrivals(args.serve_rate, args.serve_seconds, seed)
+    data = serve_shapes_data(arrivals)
+    firsts = {}
+    for prec in ("fp64", "mixed_precond"):
+        r = run_serve_once(arrivals, data, prec)
+        firsts[prec] = {k: v[3].clone() for k, v in data.items()}
+        sweep = []
+        for frac in (0.25, 0.5, 0.9):
+            rate = frac * r["served_per_s"]
+            arr = serve_arrivals(rate, args.serve_sweep_requests / rate, seed + 1)
+            sweep.append(dict(run_serve_once(arr, serve_shapes_data(arr), prec), load_fraction=frac,
+                              target_rate_per_s=rate))
+        out[prec] = dict(r, sweep=sweep)
+    out["max_rel_err_mixed_precond_vs_fp64"] = max(
+        ((firsts["mixed_precond"][k] - firsts["fp64"][k]).abs().max() / firsts["fp64"][k].abs().max()).item()
+        for k in firsts["fp64"])
+    out["mixed_speedup_vs_fp64"] = out["mixed_precond"]["served_per_s"] / out["fp64"]["served_per_s"]
+    out["note"] = ("overload point: offered load far above capacity, latency is queueing; sweep: arrivals at "
+                   "25/50/90% of the capacity measured at the overload point")
+    return out
+
+
+def f32_sweep_roof(prof, step_ms, hbm_peak, hbm_src):
+    """HBM roofline of the binary32 finest-level Gauss-Seidel launches of a mixed solve (three
+    sweeps per launch; algorithmic bytes: read x and b, write x, plus the coarse iterate of a
+    launch that adds the prolongated correction), from the CUDA events st_profile put around them."""
+    n, ms_sum, nbytes = prof["f32_launches"], prof["f32_ms"], prof["f32_bytes"]
+    if n == 0 or ms_sum <= 0:
+        return None
+    gbs = nbytes / (ms_sum / 1e3) / 1e9
+    nd, msd, bd = prof["f32_diag_launches"], prof["f32_diag_ms"], prof["f32_diag_bytes"]
+    return {"kernel": "finest-level binary32 Gauss-Seidel launches (3 fused sweeps), K_x and K_l", "bound": "hbm",
+            "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "peak_source": hbm_src,
+            "launches": n, "avg_launch_ms": ms_sum / n, "algorithmic_bytes_per_launch": nbytes / n,
+            "share_of_step": ms_sum / step_ms if step_ms > 0 else None,
+            "K_l_only": {"launches": nd, "achieved": (bd / (msd / 1e3) / 1e9) if msd > 0 else None,
+                         "avg_launch_ms": msd / nd if nd else None},
+            "K_x_only": {"launches": n - nd,
+                         "achieved": ((nbytes - bd) / ((ms_sum - msd) / 1e3) / 1e9) if ms_sum > msd else None,
+                         "avg_launch_ms": (ms_sum - msd) / (n - nd) if n > nd else None},
+            "traffic": None}
+
+
+def measured_hbm_peak():
+    """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s of the profiling recipe"
 
 
 def kernel_source_hash():
@@ -375,7 +456,9 @@ def smoother_choice(tune):
         return f"{tune} on every level"
     out = {}
     for k, row in sorted(tune.items()):
-        out[str(k)] = {op: ("wavefront" if row[f"f64_{op}"][1] < row[f"f64_{op}"][0] else "tiles") for op in ("Kx", "Kl")}
+        out[str(k)] = {f"{p}_{op}": ("wavefront" if row[f"{p}_{op}"][1] < row[f"{p}_{op}"][0] else "tiles")
+                       for p in ("f64", "f32") for op in ("Kx", "Kl")}
+        out[str(k)]["ms"] = {key: [round(v[0], 4), round(v[1], 4)] for key, v in row.items()}
     return out
 
 
@@ -415,6 +498,10 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # the device's fma rates, measured on the solver's stream just before the timed region
+    from paper_2009_08875_gb300 import probe_fma_rates
+    fp64_probe, fp32_probe = probe_fma_rates(stream)
+    hbm_peak, hbm_src = measured_hbm_peak()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -613,6 +700,7 @@ def run_ours(args):
             m0 = torch.cuda.Event(enable_timing=True)
             m1 = torch.cuda.Event(enable_timing=True)
             inner = outer = 0
+            ms_solver.profile_begin()
             m0.record(ms_solver.stream)
             for _ in range(args.steps):
                 info = mstep()
@@ -620,6 +708,7 @@ def run_ours(args):
                 outer += info["outer_iterations"]
             m1.record(ms_solver.stream)
             torch.cuda.synchronize()
+            mprof = ms_solver.profile_end()
             mms = m0.elapsed_time(m1)
             if dist:
                 t = torch.tensor([mms], device="cuda")
@@ -632,7 +721,8 @@ def run_ours(args):
                            "unit": "DoF-iter/s (binary32 inner iterations)",
                            "inner_iterations_per_solve": inner / args.steps,
                            "outer_iterations_per_solve": outer / args.steps,
-                           "rel_err_vs_fp64_solution": err, "dtype": dtype}
+                           "rel_err_vs_fp64_solution": err, "dtype": dtype,
+                           "roofline": f32_sweep_roof(mprof, mms, hbm_peak, hbm_src)}
             solver = ms_solver
 
     batch = None
@@ -651,25 +741,33 @@ def run_ours(args):
         return
 
     # roofline of the dominant kernel, timed live: the finest-level Gauss-Seidel sweep of K_l
-    # (mass couplings; the K_X half of the iteration); the K_x sweep (inside S) beside it
+    # (mass couplings; the K_X half of the iteration); the K_x sweep (inside S) beside it.  The
+    # FP64 instruction peak is the recipe's nominal rate; the same device's fma rate, measured
+    # by st_probe_fma_rates in this run, and the HBM fraction stand beside it.
+
     def sweep_roof(n, ms_sum, ops, nbytes, name, traffic):
         sec = ms_sum / 1e3
         achieved = ops / sec / 1e9 if sec > 0 else None
         n = max(n, 1)
+        gbs = nbytes / sec / 1e9 if sec > 0 else None
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_INST_PEAK / 1e9,
                 "unit": "G FP64 inst/s (add, mul, fma = 1)",
                 "frac": (achieved / (FP64_INST_PEAK / 1e9)) if achieved else None,
-                "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe (the box measured 1.198 by "
-                               "a DFMA loop), / 2 flops per fma",
+                "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe, / 2 flops per fma",
+                "peak_probe": fp64_probe / 1e9, "frac_of_probe": (achieved / (fp64_probe / 1e9)) if achieved else None,
+                "peak_probe_source": "st_probe_fma_rates in this run (binary64 fma throughput kernel, same device "
+                                     "and clocks)",
+                "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak if gbs else None,
+                        "peak_source": hbm_src},
                 "traffic": traffic, "algorithmic_bytes_per_launch": nbytes / n, "fp64_inst_per_launch": ops / n,
                 "avg_launch_ms": ms_sum / n, "launches": n,
-                "hbm_gbs": nbytes / sec / 1e9 if sec > 0 else None,
+                "hbm_gbs": gbs,
                 "share_of_step": ms_sum / ms if ms > 0 else None}
 
     kinds = smoother_choice(tune)
     top = str(K)
-    kind_l = kinds[top]["Kl"] if isinstance(kinds, dict) else args.smoother
-    kind_x = kinds[top]["Kx"] if isinstance(kinds, dict) else args.smoother
+    kind_l = kinds[top]["f64_Kl"] if isinstance(kinds, dict) else args.smoother
+    kind_x = kinds[top]["f64_Kx"] if isinstance(kinds, dict) else args.smoother
     traffic = NCU_TRAFFIC.get(kernel_source_hash(), {})
     roofline = sweep_roof(prof["diag_launches"], prof["diag_ms"], prof["diag_fp64_ops"], prof["diag_bytes"],
                           f"finest-level K_l Gauss-Seidel sweep, FP64 ({kind_l})", traffic.get(("Kl", kind_l)))
@@ -716,6 +814,8 @@ def run_ours(args):
         "mixed_bf16": mixed.get("mixed_bf16"),
         "batch": batch,
         "serve": serve,
+        "fma_rates": {"fp64_per_s": fp64_probe, "fp32_per_s": fp32_probe,
+                      "source": "st_probe_fma_rates on the solver's stream before the timed region"},
         "gpu_launches": prof["launches"],
         "clocks": clk,
     }

@@ -217,10 +217,13 @@ st_status st_solve_host(st_handle h, const double* g_nodal_host, const double* u
  * with the default multigrid settings (2 V-cycles, 3 + 3 sweeps), enqueued on cuda_stream.
  * Needs no handle and allocates nothing: its scratch is one static device array of 32 MiB,
  * held by every device that loads the library until the process exits.  Sizes whose scratch
- * (about nslices * N_x * 3 doubles) exceeds 32 MiB are rejected with ST_ERR_ARG before any
- * work is enqueued; for example K = 9 allows 5 slices, K = 7 allows 87.
+ * (about nslices * N_x * 3 doubles) exceeds 32 MiB, and nslices above 65535 (a launch grid
+ * dimension), are rejected with ST_ERR_ARG before any work is enqueued; for example K = 9
+ * allows 5 slices, K = 7 allows 87.
  * The first call on each device looks up the array's device address and sets kernel
- * attributes; make that first call before any stream capture on that device.
+ * attributes; make that first call before any stream capture on that device.  The address is
+ * kept for the life of the process: calls after cudaDeviceReset on that device are not
+ * supported (the reset reloads the module, and the kept address would be stale).
  * Every call on a device shares the one array, which keeps the last call's contents (nothing
  * in it needs to start at zero), so calls whose work overlaps on the GPU (other streams, other
  * host threads) race and must be serialised by the caller.  b and x are device pointers to
@@ -376,12 +379,15 @@ st_status st_set_wave_rows(st_handle h, int rows);
  * handle counts every kernel it launches and brackets each finest-level Gauss-Seidel sweep
  * launch (the dominant kernel) with a pair of CUDA events on the bound stream, adding up the
  * launch's algorithmic work: per point and sweep 4 FP64 operations for K_x (2 adds, 2 fmas; 6
- * with the mass couplings of K_l: 1 more add and fma), and 3 values moved (read x and b, write
- * x; 2 on a sweep that starts from x = 0) of the element type.  st_profile_end synchronises
- * the stream and reports the sums, in total and for the sweeps with mass couplings alone. */
+ * with the mass couplings of K_l: 1 more add and fma), and per point and launch 3 values moved
+ * (read x and b, write x; 2 on a launch that starts from x = 0) of the storage type, plus the
+ * coarse iterate read by a launch that adds the prolongated correction.  Launches computing in
+ * binary64 or double-float and launches computing in binary32 (binary32 or bfloat16 storage)
+ * are summed separately.  st_profile_end synchronises the stream and reports the sums, in total
+ * and for the sweeps with mass couplings alone. */
 typedef struct {
   int64_t launches;        /* kernels launched by the handle                        */
-  int64_t sweep_launches;  /* finest-level Gauss-Seidel sweep launches timed        */
+  int64_t sweep_launches;  /* finest-level binary64 Gauss-Seidel sweep launches     */
   double sweep_ms;         /* their summed CUDA-event durations                     */
   double sweep_fp64_ops;   /* their algorithmic FP64 operations (add, mul, fma = 1) */
   double sweep_bytes;      /* their algorithmic DRAM bytes                          */
@@ -389,10 +395,24 @@ typedef struct {
   double diag_ms;          /*   CUDA-event time                                     */
   double diag_fp64_ops;    /*   FP64 operations                                     */
   double diag_bytes;       /*   DRAM bytes                                          */
+  int64_t f32_launches;    /* finest-level binary32 sweep launches                  */
+  double f32_ms;           /*   CUDA-event time                                     */
+  double f32_bytes;        /*   algorithmic DRAM bytes                              */
+  int64_t f32_diag_launches; /* the binary32 subset with mass couplings (K_l)       */
+  double f32_diag_ms;
+  double f32_diag_bytes;
 } st_profile;
 
 st_status st_profile_begin(st_handle h);
 st_status st_profile_end(st_handle h, st_profile* out);
+
+/* Measurement hook (not part of the method): the device's sustained fused multiply-add rates,
+ * from a throughput kernel of 8 independent x <- x a + c chains per thread and 8 blocks of 256
+ * threads per SM, in binary64 (about 2.5e9 fmas) and binary32 (32 times as many), each the best
+ * of 3 launches timed with CUDA events on cuda_stream after one warm-up launch, on the current
+ * device.  *fp64_fma_per_s and *fp32_fma_per_s receive fmas per second (2 flops each).  Allocates
+ * nothing (its results are folded into a file-scope device array).  Synchronous. */
+st_status st_probe_fma_rates(void* cuda_stream, double* fp64_fma_per_s, double* fp32_fma_per_s);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* st_last_error(void);

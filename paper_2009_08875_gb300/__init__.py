@@ -4,4 +4,4 @@ The solver lives in the CUDA library libst.so (C ABI in include/st.h).  `Solver`
 ctypes wrapper whose methods take torch CUDA float64 tensors; it never computes anything
 itself and raises if the library has not been built.
 """
-from .solver import Batch, Server, Solver, STError  # noqa: F401
+from .solver import Batch, Server, Solver, STError, probe_fma_rates  # noqa: F401

@@ -34,7 +34,10 @@ class StProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("sweep_launches", ctypes.c_int64), ("sweep_ms", ctypes.c_double),
                 ("sweep_fp64_ops", ctypes.c_double), ("sweep_bytes", ctypes.c_double),
                 ("diag_launches", ctypes.c_int64), ("diag_ms", ctypes.c_double),
-                ("diag_fp64_ops", ctypes.c_double), ("diag_bytes", ctypes.c_double)]
+                ("diag_fp64_ops", ctypes.c_double), ("diag_bytes", ctypes.c_double),
+                ("f32_launches", ctypes.c_int64), ("f32_ms", ctypes.c_double), ("f32_bytes", ctypes.c_double),
+                ("f32_diag_launches", ctypes.c_int64), ("f32_diag_ms", ctypes.c_double),
+                ("f32_diag_bytes", ctypes.c_double)]
 
 
 class STError(RuntimeError):
@@ -100,6 +103,7 @@ _SIGS = {
                                                  ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
     "st_server_cancel": (ctypes.c_int, [_P, ctypes.c_int64]),
     "st_server_stop": (ctypes.c_int, [_P]),
+    "st_probe_fma_rates": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "st_last_error": (ctypes.c_char_p, []),
 }
 

@@ -994,7 +994,7 @@ st_status st_profile_begin(st_handle h) {
   ST_CHECK(check_handle(h));
   h->launches = 0;
   h->prof_n = 0;
-  h->prof_ops[0] = h->prof_ops[1] = h->prof_bytes[0] = h->prof_bytes[1] = 0.0;
+  for (int c = 0; c < 4; ++c) h->prof_ops[c] = h->prof_bytes[c] = 0.0;
   h->prof_on = true;
   // preallocate events so that recording inside the timed region never creates them
   if (h->prof_cap < 16384 && prof_start(h)) {
@@ -1013,8 +1013,8 @@ st_status st_profile_end(st_handle h, st_profile* out) {
   ST_CHECK(check_handle(h));
   ST_REQUIRE(out != nullptr, "st_profile_end: null output");
   ST_CHECK_CUDA(cudaStreamSynchronize(h->stream), "st_profile_end");
-  double ms[2] = {0.0, 0.0};
-  int64_t n[2] = {0, 0};
+  double ms[4] = {0.0, 0.0, 0.0, 0.0};
+  int64_t n[4] = {0, 0, 0, 0};
   for (int i = 0; i + 1 < h->prof_n; i += 2) {
     float t = 0.f;
     ST_CHECK_CUDA(cudaEventElapsedTime(&t, h->prof_ev[i], h->prof_ev[i + 1]), "cudaEventElapsedTime");
@@ -1030,6 +1030,12 @@ st_status st_profile_end(st_handle h, st_profile* out) {
   out->diag_ms = ms[1];
   out->diag_fp64_ops = h->prof_ops[1];
   out->diag_bytes = h->prof_bytes[1];
+  out->f32_launches = n[2] + n[3];
+  out->f32_ms = ms[2] + ms[3];
+  out->f32_bytes = h->prof_bytes[2] + h->prof_bytes[3];
+  out->f32_diag_launches = n[3];
+  out->f32_diag_ms = ms[3];
+  out->f32_diag_bytes = h->prof_bytes[3];
   h->prof_on = false;
   h->prof_n = 0;
   return ST_OK;

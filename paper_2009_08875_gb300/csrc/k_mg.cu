@@ -634,9 +634,12 @@ cudaError_t gs_launch(const st_handle_s* h, int k, int nslices, int cls, G* x_ou
   count_launch(h);
   if (prof) {
     // per point and sweep: 3 adds + 1 fma (+ 1 add + 1 fma with diagonal couplings);
-    // bytes: read x and b, write x (x is not read when the launch starts from x = 0)
+    // bytes: read x and b, write x (x is not read when the launch starts from x = 0), and the
+    // coarse iterate when the launch adds the prolongated correction
     const double pts = (double)n * n * nslices;
-    prof_stop(h, DIAG ? 1 : 0, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(G) * (zero_init ? 2.0 : 3.0));
+    const double nc = (double)((n - 1) / 2);
+    prof_stop(h, (DIAG ? 1 : 0) + (sizeof(T) == 4 ? 2 : 0), pts * NSW * (DIAG ? 6.0 : 4.0),
+              sizeof(G) * (pts * (zero_init ? 2.0 : 3.0) + (PROL ? nc * nc * nslices : 0.0)));
   }
   return cudaGetLastError();
 }
@@ -661,7 +664,9 @@ cudaError_t wave_launch(const st_handle_s* h, int k, int nslices, int cls, G* x_
   count_launch(h);
   if (prof) {
     const double pts = (double)n * n * nslices;
-    prof_stop(h, DIAG ? 1 : 0, pts * NSW * (DIAG ? 6.0 : 4.0), pts * sizeof(G) * (zero_init ? 2.0 : 3.0));
+    const double nc = (double)((n - 1) / 2);
+    prof_stop(h, (DIAG ? 1 : 0) + (sizeof(T) == 4 ? 2 : 0), pts * NSW * (DIAG ? 6.0 : 4.0),
+              sizeof(G) * (pts * (zero_init ? 2.0 : 3.0) + (PROL ? nc * nc * nslices : 0.0)));
   }
   return cudaGetLastError();
 }

@@ -177,7 +177,7 @@ cudaError_t colour_sweep(const st_handle_s* h, int k, int nslices, int cls, T* x
   if (prof) {
     // one colour of the sweep is timed; its work is a quarter of the sweep's
     const double pts = (double)n * n * n * nslices / 4.0;
-    prof_stop(h, DIAG ? 1 : 0, pts * (DIAG ? 16.0 : 6.0), pts * sizeof(T) * 3.0);
+    prof_stop(h, (DIAG ? 1 : 0) + (sizeof(T) == 4 ? 2 : 0), pts * (DIAG ? 16.0 : 6.0), pts * sizeof(T) * 3.0);
   }
   return cudaGetLastError();
 }

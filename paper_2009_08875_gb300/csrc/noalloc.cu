@@ -83,8 +83,9 @@ using namespace st;
 
 extern "C" st_status st_apply_Kx_static(int space_level, int nslices, const double* b, double* x,
                                         void* cuda_stream) {
-  if (space_level < 1 || space_level > 12 || nslices < 1) {
-    set_error("st_apply_Kx_static: space level must be in 1..12 and nslices >= 1");
+  // nslices is a grid dimension of the multigrid launches (65535 at most), as in st_setup
+  if (space_level < 1 || space_level > 12 || nslices < 1 || nslices > 65535) {
+    set_error("st_apply_Kx_static: space level must be in 1..12 and nslices in 1..65535");
     return ST_ERR_ARG;
   }
   if (!b || !x) {

@@ -203,8 +203,10 @@ struct st_handle_s {
   mutable bool prof_on;
   mutable int prof_cap, prof_n;
   mutable cudaEvent_t* prof_ev;
-  mutable unsigned char* prof_cat;  // per event pair: 0 sweep without, 1 with mass couplings
-  mutable double prof_ops[2], prof_bytes[2];
+  // per event pair: 0 / 1 sweep of 8-byte values (binary64, double-float) without / with mass
+  // couplings, 2 / 3 the same for binary32 arithmetic (binary32 or bfloat16 storage)
+  mutable unsigned char* prof_cat;
+  mutable double prof_ops[4], prof_bytes[4];
 };
 
 namespace st {

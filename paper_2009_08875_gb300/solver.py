@@ -314,3 +314,13 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+def probe_fma_rates(stream=None):
+    """The device's sustained fused multiply-add rates (st_probe_fma_rates): (binary64, binary32)
+    fmas per second, measured on `stream` (default: torch's current stream)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _lib.check(_lib.load().st_probe_fma_rates(ctypes.c_void_p(st.cuda_stream), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

@@ -41,6 +41,9 @@ def test_static_scratch_variant_matches_st_apply_Kx(K, ns):
             torch.cuda.synchronize()
             err = ((out - ref).abs().max() / ref.abs().max()).item()
             assert err <= TOL, (seed, err)
+            # the handle is not autotuned, so both run the same kernels on the same coefficient
+            # table: the header promises the same bits
+            assert torch.equal(out, ref), (seed, err)
 
 
 def test_sizes_beyond_the_static_maximum_are_rejected():
@@ -50,3 +53,7 @@ def test_sizes_beyond_the_static_maximum_are_rejected():
     st = _static_kx(lib, 9, 6, b, b)
     assert st == _lib.ST_ERR_ARG
     assert "static maximum" in lib.st_last_error().decode()
+    # K = 2 would fit about a million slices in the array, but a launch grid holds 65535
+    st = _static_kx(lib, 2, 65536, b, b)
+    assert st == _lib.ST_ERR_ARG
+    assert "65535" in lib.st_last_error().decode()
