@@ -180,17 +180,35 @@ def _golden_table_5_3():
     return dict(rows)
 
 
-@pytest.mark.parametrize("J", [3, 4, 5])
+@pytest.mark.parametrize("J", [3, 4])
 def test_table_5_3_iterations_with_direct_inverses(J):
     # Sec. 5.2, Table 5.3 (N_x = 261121): PCG iterations to eps = 1e-6 in the K_X-norm, absolute,
-    # for u = exp(-2 pi^2 t) sin(pi x) sin(pi y), g = 0.  With direct inverses in place of the
-    # multigrid (whose smoother the paper does not define) the oracle needs at most two more
-    # iterations than printed at a coarser space level (the counts barely depend on N_x).
+    # for u = exp(-2 pi^2 t) sin(pi x) sin(pi y), g = 0.  With the direct inverses of Sec. 5.1 in
+    # place of the multigrid (whose smoother the paper does not define) the oracle takes the
+    # printed 8 and 11 iterations at N_t = 9 and 17 at K = 7, 8 and 9 (tests/golden/
+    # table_5_3_oracle.txt holds K = 9); the window allows one more.  At K <= 6 the last iterate
+    # misses 1e-6 by a small factor (9 at K = 6, N_t = 9).
     paper = _golden_table_5_3()[2 ** J + 1]
-    p = schur.Problem(4, J, inverses="direct")
-    g, u0, _ = inputs.decaying(4, J)
+    p = schur.Problem(7, J, inverses="direct")
+    g, u0, _ = inputs.decaying(7, J)
     _, _, info = schur.solve(p, g, u0, tol=1e-6, tol_mode="abs")
-    assert paper <= info["iters"] <= paper + 2, (J, info["iters"], paper)
+    assert paper <= info["iters"] <= paper + 1, (J, info["iters"], paper)
+
+
+def test_table_5_3_direct_inverses_at_the_papers_space_level():
+    # the stored K = 9 oracle counts (tests/golden/make_table_5_3_oracle.py): direct inverses within
+    # one of Table 5.3 at every stored N_t, equal at N_t = 9 and 17
+    paper = _golden_table_5_3()
+    path = os.path.join(GOLDEN, "table_5_3_oracle.txt")
+    if not os.path.exists(path):
+        pytest.skip("table_5_3_oracle.txt not generated")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            Nt, direct = int(f[0]), int(f[4])
+            assert paper[Nt] <= direct <= paper[Nt] + 1, (Nt, direct, paper[Nt])
+            if Nt in (9, 17):
+                assert direct == paper[Nt], (Nt, direct)
 
 
 def test_inplace_layout_roundtrip():
