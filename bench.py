@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--serve-sweep-requests", type=int, default=150,
                     help="requests per point of the offered-load sweep (25/50/90%% of capacity)")
     ap.add_argument("--batch-problems", type=int, default=256)
-    ap.add_argument("--smoother", choices=["auto", "tiles", "wavefront"], default="auto",
+    ap.add_argument("--smoother", choices=["auto", "tiles", "wavefront", "registers"], default="auto",
                     help="Gauss-Seidel kernel: autotuned per level (default) or one kernel on every level")
     ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_precond", "mixed_bf16", "fp64_df"], default="fp64",
                     help="precision of the main timed solve (profiling aid; the bench line uses fp64)")
@@ -429,6 +429,41 @@ def f32_sweep_roof(prof, step_ms, hbm_peak, hbm_src):
             "traffic": None}
 
 
+def gpu_local_cpus(device_index):
+    """CPUs local to the GPU (sysfs local_cpulist of its PCI device), or None."""
+    try:
+        import torch
+        ident = str(torch.cuda.get_device_properties(device_index).uuid)
+        ident = ident if ident.startswith("GPU-") else "GPU-" + ident
+        out = subprocess.run(["nvidia-smi", f"--id={ident}", "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout.strip()
+        dom, bus = out.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{bus.lower()}/local_cpulist"
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return cpus & os.sched_getaffinity(0) or None
+    except Exception:
+        return None
+
+
+def pinned_near_gpu(device_index, *arrays):
+    """Page-locked copies of `arrays`, allocated (and first touched) from the CPUs local to the
+    GPU so that the pages sit on its NUMA node; the thread's affinity is restored afterwards.
+    Returns (tensors, cpus used or None)."""
+    import torch
+    cpus = gpu_local_cpus(device_index)
+    old = os.sched_getaffinity(0)
+    try:
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+        out = [torch.from_numpy(a).pin_memory() if a is not None else None for a in arrays]
+    finally:
+        os.sched_setaffinity(0, old)
+    return out, (sorted(cpus) if cpus else None)
+
+
 def measured_hbm_peak():
     """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the profiling recipe's fallback."""
     try:
@@ -456,13 +491,15 @@ def smoother_choice(tune):
         return f"{tune} on every level"
     out = {}
     for k, row in sorted(tune.items()):
-        out[str(k)] = {f"{p}_{op}": ("wavefront" if row[f"{p}_{op}"][1] < row[f"{p}_{op}"][0] else "tiles")
+        names = ("tiles", "wavefront", "registers")
+        out[str(k)] = {f"{p}_{op}": names[min(range(3), key=lambda i: row[f"{p}_{op}"][i])]
                        for p in ("f64", "f32") for op in ("Kx", "Kl")}
-        out[str(k)]["ms"] = {key: [round(v[0], 4), round(v[1], 4)] for key, v in row.items()}
+        out[str(k)]["ms"] = {key: [round(x, 4) for x in v] for key, v in row.items()}
     return out
 
 
 def run_ours(args):
+    import numpy as np
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -473,6 +510,9 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    # a stream of our own: the library captures its solves as CUDA graphs only off the legacy
+    # default stream (profiled regions run plain launches)
+    torch.cuda.set_stream(torch.cuda.Stream())
 
     from paper_2009_08875_gb300 import Solver, inputs
 
@@ -636,9 +676,7 @@ def run_ours(args):
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        gh = torch.from_numpy(g_np).pin_memory()
-        u0h = torch.from_numpy(u0_np).pin_memory()
-        uh = torch.empty((Nt, Nx), dtype=torch.float64).pin_memory()
+        (gh, u0h, uh), near = pinned_near_gpu(local, g_np, u0_np, np.empty((Nt, Nx), dtype=np.float64))
         solver.solve_host(gh, u0h, uh)
         torch.cuda.synchronize()
         if dist:
@@ -670,7 +708,10 @@ def run_ours(args):
         e2e = {"value": world * N * its_e / dt, "unit": "DoF-iter/s",
                "h2d_bytes_per_step": (g_np.size + u0_np.size) * 8, "d2h_bytes_per_step": N * 8,
                "ms_per_solve": dt * 1e3 / max(1, args.steps), "h2d_gbs": gh.numel() * 8 / h2d_ms / 1e6,
-               "d2h_gbs": uh.numel() * 8 / d2h_ms / 1e6}
+               "d2h_gbs": uh.numel() * 8 / d2h_ms / 1e6,
+               "host_buffers": (f"page-locked, allocated from the GPU's local CPUs {near[0]}-{near[-1]}" if near
+                                else "page-locked (GPU-local CPUs unknown)"),
+               "pcg_loop": "device-driven (one CUDA graph per solve, WHILE node with device-side stop tests)"}
 
     # mixed precision (binary32 inner PCG under binary64 refinement) on the same workload:
     # same tolerance, solution compared with the FP64 solution of the timed region

@@ -139,6 +139,10 @@ void free_all(st_handle_s* h) {
     if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
     h->graph_exec[i] = nullptr;
   }
+  if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
+  h->loop_exec = nullptr;
+  if (h->ds_mem) cudaFree(h->ds_mem);
+  h->ds_mem = nullptr;
   for (int i = 0; i < h->prof_cap; ++i) cudaEventDestroy(h->prof_ev[i]);
   std::free(h->prof_ev);
   std::free(h->prof_cat);
@@ -191,7 +195,14 @@ st_status apply_S_nodal_impl(st_handle h, int nb, const T* u, T* y) {
 template <typename T>
 st_status apply_Shat_impl(st_handle h, int nb, const T* w, T* q) {
   ST_CHECK_CUDA(wavelet_synth<T>(h, nb, w, ws<T>(h->U)), "wavelet synthesis");
-  ST_CHECK(apply_S_nodal_impl<T>(h, nb, ws<T>(h->U), ws<T>(h->Z)));
+  T* U = ws<T>(h->U);
+  ST_CHECK_CUDA(launch_timemix<T>(h, nb, 0, U, ws<T>(h->Y)), "timemix");
+  ST_CHECK_CUDA(mg_apply<T>(h, (int)(2 * nb * h->Nt), 0, ws<T>(h->Y), ws<T>(h->X)), "K_x multigrid");
+  // the epilogue fused into the one-pass analysis where the time axis allows
+  const cudaError_t e = launch_epilogue_anal<T>(h, nb, ws<T>(h->X), U, h->Nt * h->Nx, q);
+  if (e == cudaSuccess) return ST_OK;
+  if (e != cudaErrorNotSupported) return cuda_fail("epilogue and wavelet analysis", e);
+  ST_CHECK_CUDA(launch_epilogue<T>(h, nb, ws<T>(h->X), U, h->Nt * h->Nx, ws<T>(h->Z)), "epilogue");
   ST_CHECK_CUDA(wavelet_anal<T>(h, nb, ws<T>(h->Z), q), "wavelet analysis");
   return ST_OK;
 }
@@ -232,6 +243,16 @@ st_status push_act(st_handle h) {
 }
 
 inline double sc(st_handle h, int b, int slot) { return h->scal_host[(size_t)b * SC_COUNT + slot]; }
+
+// Destroys the captured graphs of a handle (the kernel choices or the vectors they name changed).
+void drop_graphs(st_handle h) {
+  for (int i = 0; i < 3; ++i) {
+    if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
+    h->graph_exec[i] = nullptr;
+  }
+  if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
+  h->loop_exec = nullptr;
+}
 
 // Runs one PCG iteration body.  With graphs enabled (on a stream other than the legacy and
 // per-thread default streams, outside profiling) the first call captures the body's launches
@@ -427,6 +448,23 @@ st_status pcg64_impl(st_handle h, const double* fhat, double* w) {
 // ---------------------------------------------------------------------------------------------
 // ST_MIXED_FP32: binary64 iterative refinement around a binary32 PCG (per problem)
 // ---------------------------------------------------------------------------------------------
+// One iteration of the inner binary32 PCG on all problems (narrow: the preconditioner stores its
+// multigrid vectors as bfloat16 and beta takes the flexible form).
+st_status body_inner32(st_handle h, bool narrow) {
+  const int nb = h->B;
+  const int64_t n = h->Nt * h->Nx;
+  ST_CHECK_CUDA(launch_update_p<float>(h, 0, nb, h->pi, h->zi, n), "inner update p");
+  ST_CHECK(apply_Shat_impl<float>(h, h->B, h->pi, h->qi));
+  ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->pi, h->qi, n, SC_PQ, DOT_ALPHA), "inner dot p q");
+  ST_CHECK_CUDA(launch_update_wr<float>(h, 0, nb, h->xi, h->ri, h->pi, h->qi, n), "inner update");
+  if (narrow)
+    ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RZOLD, DOT_STORE), "inner dot r z_old");
+  ST_CHECK(apply_KX_impl<float>(h, h->B, h->ri, h->zi, narrow));
+  ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RHO_NEW, narrow ? DOT_BETA_FLEX : DOT_BETA),
+                "inner dot r z");
+  return ST_OK;
+}
+
 // Binary32 PCG on S_hat x = ri for the problems with out_act[b] set, from x = 0, with
 // zi = K_X ri already formed; each stops at a relative reduction of inner_tol or inner_maxit.
 // ST_MIXED_BF16: the preconditioner stores its multigrid vectors as bfloat16, which makes it
@@ -447,18 +485,7 @@ st_status inner_pcg32(st_handle h, const std::vector<int>& out_act, std::vector<
     h->act_host[b] = out_act[b] && rho0[b] > 0.0 && std::isfinite(rho0[b]);
   }
   ST_CHECK(push_act(h));
-  auto body = [&]() -> st_status {
-    ST_CHECK_CUDA(launch_update_p<float>(h, 0, nb, h->pi, h->zi, n), "inner update p");
-    ST_CHECK(apply_Shat_impl<float>(h, h->B, h->pi, h->qi));
-    ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->pi, h->qi, n, SC_PQ, DOT_ALPHA), "inner dot p q");
-    ST_CHECK_CUDA(launch_update_wr<float>(h, 0, nb, h->xi, h->ri, h->pi, h->qi, n), "inner update");
-    if (narrow)
-      ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RZOLD, DOT_STORE), "inner dot r z_old");
-    ST_CHECK(apply_KX_impl<float>(h, h->B, h->ri, h->zi, narrow));
-    ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RHO_NEW, narrow ? DOT_BETA_FLEX : DOT_BETA),
-                  "inner dot r z");
-    return ST_OK;
-  };
+  auto body = [&]() -> st_status { return body_inner32(h, narrow); };
   for (int it = 1; it <= c.inner_maxit && any_active(h); ++it) {
     ST_CHECK(run_body(h, 1, nullptr, body));
     ST_CHECK(read_scalars(h));
@@ -558,6 +585,176 @@ st_status pcg_precond_impl(st_handle h, const double* fhat, double* w) {
   return finish(h);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Device-driven solves (cfg.use_graphs = 2): the whole PCG loop is captured into one CUDA graph.
+// A WHILE node repeats the iteration body, and a stop-test kernel at the end of each body takes
+// the per-problem decisions of the host-driven loop above on the device and sets the node's
+// condition, so a solve needs no host round trip per iteration (the refinement of ST_MIXED_FP32
+// nests an inner WHILE node in the outer one).  The kernels and their order are those of the
+// host-driven loop, so the results are bitwise the same.
+// ---------------------------------------------------------------------------------------------
+// Capture of work enqueued on the handle's stream into graph G after the nodes `leaves`; end()
+// replaces `leaves` by the last nodes captured.
+struct GraphCapture {
+  st_handle h;
+  cudaGraph_t G;
+  std::vector<cudaGraphNode_t>* leaves;
+  st_status begin() {
+    ST_CHECK_CUDA(cudaStreamBeginCaptureToGraph(h->stream, G, leaves->empty() ? nullptr : leaves->data(), nullptr,
+                                                leaves->size(), cudaStreamCaptureModeThreadLocal),
+                  "begin capture");
+    return ST_OK;
+  }
+  // ends the capture; `ok` is the status of the work enqueued (the capture ends either way)
+  st_status end(st_status ok) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+    std::vector<cudaGraphNode_t> out;
+    if (e == cudaSuccess) out.assign(deps, deps + nd);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (ok != ST_OK) return ok;
+    if (e != cudaSuccess) return cuda_fail("capture info", e);
+    if (e2 != cudaSuccess) return cuda_fail("end capture", e2);
+    *leaves = out;
+    return ST_OK;
+  }
+};
+
+// Appends a WHILE node with condition hc after `leaves` to G; *body receives its body graph and
+// `leaves` becomes the node.
+st_status add_while(cudaGraph_t G, std::vector<cudaGraphNode_t>& leaves, cudaGraphConditionalHandle hc,
+                    cudaGraph_t* body) {
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+  p.conditional.handle = hc;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  ST_CHECK_CUDA(cudaGraphAddNode(&node, G, leaves.empty() ? nullptr : leaves.data(), nullptr, leaves.size(), &p),
+                "add WHILE node");
+  *body = p.conditional.phGraph_out[0];
+  leaves.assign(1, node);
+  return ST_OK;
+}
+
+// Captures `work` (enqueued on the handle's stream) into G after `leaves`.
+template <typename F>
+st_status capture_into(st_handle h, cudaGraph_t G, std::vector<cudaGraphNode_t>& leaves, F work) {
+  GraphCapture c{h, G, &leaves};
+  ST_CHECK(c.begin());
+  return c.end(work());
+}
+
+// A loop: WHILE(hc) { body; test } after `leaves` in G.
+template <typename F>
+st_status capture_loop(st_handle h, cudaGraph_t G, std::vector<cudaGraphNode_t>& leaves,
+                       cudaGraphConditionalHandle hc, F body) {
+  cudaGraph_t bg = nullptr;
+  ST_CHECK(add_while(G, leaves, hc, &bg));
+  std::vector<cudaGraphNode_t> inner;
+  return capture_into(h, bg, inner, body);
+}
+
+// The PCG program of the handle's precision into G after `leaves` (the solve of pcg_impl).
+st_status capture_pcg(st_handle h, cudaGraph_t G, std::vector<cudaGraphNode_t>& leaves, const double* fhat,
+                      double* w) {
+  const int nb = h->B;
+  const int64_t n = h->Nt * h->Nx;
+  const int prec = h->cfg.precision;
+  cudaGraphConditionalHandle hc;
+  ST_CHECK_CUDA(cudaGraphConditionalHandleCreate(&hc, G, 0, 0), "conditional handle");
+  if (prec == ST_MIXED_FP32 || prec == ST_MIXED_BF16) {
+    const bool narrow = prec == ST_MIXED_BF16;
+    ST_CHECK(capture_into(h, G, leaves, [&]() -> st_status {
+      ST_CHECK(init_residual(h, fhat, w));
+      ST_CHECK_CUDA(launch_copy<float, double>(h, h->ri, h->r, n * nb), "round r");
+      ST_CHECK(apply_KX_impl<float>(h, nb, h->ri, h->zi));
+      ST_CHECK_CUDA(launch_dot<double, float>(h, 0, nb, h->r, h->zi, n, SC_OUTER, DOT_STORE), "outer dot");
+      ST_CHECK_CUDA(launch_loop_test(h, LOOP_INIT, SC_OUTER, false, true, hc), "outer test");
+      return ST_OK;
+    }));
+    // outer step: inner binary32 PCG, then the binary64 residual and the outer test
+    cudaGraph_t ob = nullptr;
+    ST_CHECK(add_while(G, leaves, hc, &ob));
+    cudaGraphConditionalHandle hi;
+    ST_CHECK_CUDA(cudaGraphConditionalHandleCreate(&hi, ob, 0, 0), "conditional handle");
+    std::vector<cudaGraphNode_t> ol;
+    ST_CHECK(capture_into(h, ob, ol, [&]() -> st_status {
+      ST_CHECK_CUDA(launch_zero<float>(h, h->xi, n * nb), "zero inner x");
+      ST_CHECK_CUDA(launch_zero<float>(h, h->pi, n * nb), "zero inner p");
+      ST_CHECK_CUDA(launch_dot<float, float>(h, 0, nb, h->ri, h->zi, n, SC_RHO, DOT_INIT), "inner dot r z");
+      ST_CHECK_CUDA(launch_inner_test(h, LOOP_INIT, hi), "inner test");
+      return ST_OK;
+    }));
+    ST_CHECK(capture_loop(h, ob, ol, hi, [&]() -> st_status {
+      ST_CHECK(body_inner32(h, narrow));
+      ST_CHECK_CUDA(launch_inner_test(h, LOOP_ITER, hi), "inner test");
+      return ST_OK;
+    }));
+    return capture_into(h, ob, ol, [&]() -> st_status {
+      ST_CHECK_CUDA(launch_refine_count(h), "refinement count");
+      ST_CHECK_CUDA(launch_add_correction(h, w, h->xi, n * nb), "w += d");
+      ST_CHECK(apply_Shat_impl<double>(h, nb, w, h->q));
+      ST_CHECK_CUDA(launch_residual_split(h, h->r, h->ri, fhat, h->q, n * nb), "outer residual");
+      ST_CHECK(apply_KX_impl<float>(h, nb, h->ri, h->zi));
+      ST_CHECK_CUDA(launch_dot<double, float>(h, 0, nb, h->r, h->zi, n, SC_OUTER, DOT_STORE), "outer dot");
+      ST_CHECK_CUDA(launch_loop_test(h, LOOP_ITER, SC_OUTER, false, true, hc), "outer test");
+      return ST_OK;
+    });
+  }
+  const bool pre = prec == ST_MIXED_PRECOND;
+  ST_CHECK(capture_into(h, G, leaves, [&]() -> st_status {
+    ST_CHECK(init_residual(h, fhat, w));
+    if (pre)
+      ST_CHECK(precond32(h, nb, h->r, h->z, h->ri, h->zi));
+    else
+      ST_CHECK(apply_KX_impl<double>(h, nb, h->r, h->z));
+    ST_CHECK_CUDA(launch_dot<double, double>(h, 0, nb, h->r, h->z, n, SC_RHO, DOT_INIT), "dot r z");
+    ST_CHECK_CUDA(launch_zero<double>(h, h->p, n * nb), "zero p");  // first body: p = z + 0 p
+    ST_CHECK_CUDA(launch_loop_test(h, LOOP_INIT, SC_RHO0, false, false, hc), "stop test");
+    return ST_OK;
+  }));
+  return capture_loop(h, G, leaves, hc, [&]() -> st_status {
+    ST_CHECK(pre ? body_precond(h, w, nb) : body64(h, w, nb));
+    ST_CHECK_CUDA(launch_loop_test(h, LOOP_ITER, SC_RHO_NEW, true, false, hc), "stop test");
+    return ST_OK;
+  });
+}
+
+// The device-driven solve of pcg_impl: one graph launch (the graph is kept for the next solve with
+// the same vectors), then one read of the per-problem results.
+st_status pcg_device(st_handle h, const double* fhat, double* w) {
+  const void* key[3] = {fhat, w, reinterpret_cast<const void*>((uintptr_t)(h->use_guess ? 1 : 0))};
+  if (h->loop_exec && (h->loop_key[0] != key[0] || h->loop_key[1] != key[1] || h->loop_key[2] != key[2])) {
+    cudaGraphExecDestroy(h->loop_exec);
+    h->loop_exec = nullptr;
+  }
+  if (!h->loop_exec) {
+    cudaGraph_t G = nullptr;
+    ST_CHECK_CUDA(cudaGraphCreate(&G, 0), "graph create");
+    std::vector<cudaGraphNode_t> leaves;
+    const int64_t before = h->launches;
+    st_status s = capture_pcg(h, G, leaves, fhat, w);
+    h->launches = before;
+    if (s == ST_OK) {
+      cudaError_t e = cudaGraphInstantiate(&h->loop_exec, G, 0);
+      if (e != cudaSuccess) {
+        h->loop_exec = nullptr;
+        s = cuda_fail("graph instantiate", e);
+      }
+    }
+    cudaGraphDestroy(G);
+    if (s != ST_OK) return s;
+    for (int i = 0; i < 3; ++i) h->loop_key[i] = key[i];
+  }
+  ST_CHECK_CUDA(cudaGraphLaunch(h->loop_exec, h->stream), "graph launch");
+  ST_CHECK(solve_collect_enqueue(h, h->stream));
+  ST_CHECK_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+  return solve_collect_finish(h);
+}
+
 }  // namespace
 
 namespace st {
@@ -565,13 +762,54 @@ namespace st {
 st_status rhs_impl(st_handle h, int nb, const double* g, const double* u0, double* fhat) {
   ST_CHECK_CUDA(launch_timemix<double>(h, nb, 1, g, h->Y), "timemix (rhs)");
   ST_CHECK_CUDA(mg_apply<double>(h, (int)(2 * nb * h->Nt), 0, h->Y, h->X), "K_x multigrid (rhs)");
+  const cudaError_t e = launch_epilogue_anal<double>(h, nb, h->X, u0, h->Nx, fhat);
+  if (e == cudaSuccess) return ST_OK;
+  if (e != cudaErrorNotSupported) return cuda_fail("epilogue and wavelet analysis (rhs)", e);
   ST_CHECK_CUDA(launch_epilogue<double>(h, nb, h->X, u0, h->Nx, h->Z), "epilogue (rhs)");
   ST_CHECK_CUDA(wavelet_anal<double>(h, nb, h->Z, fhat), "wavelet analysis (rhs)");
   return ST_OK;
 }
 
+// Reads back the per-problem results of a device-driven solve (enqueued on s) ...
+st_status solve_collect_enqueue(st_handle h, cudaStream_t s) {
+  const int B = h->B;
+  const bool refine = h->cfg.precision == ST_MIXED_FP32 || h->cfg.precision == ST_MIXED_BF16;
+  ST_CHECK_CUDA(cudaMemcpyAsync(h->info_iters, h->ds.iters, sizeof(int) * B, cudaMemcpyDeviceToHost, s), "results");
+  ST_CHECK_CUDA(cudaMemcpyAsync(h->info_outer, h->ds.outer, sizeof(int) * B, cudaMemcpyDeviceToHost, s), "results");
+  ST_CHECK_CUDA(cudaMemcpyAsync(h->info_status, h->ds.status, sizeof(int) * B, cudaMemcpyDeviceToHost, s),
+                "results");
+  ST_CHECK_CUDA(cudaMemcpyAsync(h->info_relres, h->ds.relres, sizeof(double) * B, cudaMemcpyDeviceToHost, s),
+                "results");
+  ST_CHECK_CUDA(cudaMemcpyAsync(h->act_host, refine ? h->ds.oact : h->act, sizeof(int) * B, cudaMemcpyDeviceToHost,
+                                s),
+                "results");
+  return ST_OK;
+}
+
+// ... and, once they have arrived, sets the overall status as the host-driven loop does.
+st_status solve_collect_finish(st_handle h) { return finish(h); }
+
+st_status capture_solve(st_handle h, cudaGraph_t G, const std::vector<cudaGraphNode_t>& deps, const double* fhat,
+                        double* w, st_status (*pre)(st_handle, void*), st_status (*post)(st_handle, void*), void* arg,
+                        std::vector<cudaGraphNode_t>* leaves) {
+  std::vector<cudaGraphNode_t> l = deps;
+  if (pre) ST_CHECK(capture_into(h, G, l, [&]() { return pre(h, arg); }));
+  ST_CHECK(capture_pcg(h, G, l, fhat, w));
+  if (post) ST_CHECK(capture_into(h, G, l, [&]() { return post(h, arg); }));
+  *leaves = l;
+  return ST_OK;
+}
+
 st_status pcg_impl(st_handle h, const double* fhat, double* w, int* iters, double* relres) {
   st_status s;
+  const bool device_loop =
+      h->cfg.use_graphs == 2 && reinterpret_cast<uintptr_t>(h->stream) > 2 && !h->prof_on;
+  if (device_loop) {
+    s = pcg_device(h, fhat, w);
+    if (iters) *iters = h->last_iters;
+    if (relres) *relres = h->last_relres;
+    return s;
+  }
   switch (h->cfg.precision) {
     case ST_MIXED_FP32:
     case ST_MIXED_BF16:
@@ -650,7 +888,7 @@ void st_default_config(st_config* cfg) {
   cfg->precision = ST_FP64;
   cfg->inner_tol = 1e-5;
   cfg->inner_maxit = 60;
-  cfg->use_graphs = 1;
+  cfg->use_graphs = 2;
   cfg->diffusion[0] = 1.0;
   cfg->diffusion[1] = 0.0;
   cfg->diffusion[2] = 1.0;
@@ -771,6 +1009,22 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
                     "coefficient table");
   if (s == ST_OK) s = alloc_bytes(reinterpret_cast<void**>(&h->act), sizeof(int) * batch, "active flags");
   if (s == ST_OK) {
+    // device loop state: 2 B doubles, then 4 counters and 5 B ints
+    s = alloc_bytes(&h->ds_mem, sizeof(double) * 2 * batch + sizeof(int) * (4 + 5 * (size_t)batch), "loop state");
+    if (s == ST_OK) {
+      double* d = static_cast<double*>(h->ds_mem);
+      h->ds.relres = d;
+      h->ds.rho0 = d + batch;
+      int* i = reinterpret_cast<int*>(d + 2 * batch);
+      h->ds.ctr = i;
+      h->ds.iters = i + 4;
+      h->ds.outer = i + 4 + batch;
+      h->ds.status = i + 4 + 2 * batch;
+      h->ds.oact = i + 4 + 3 * batch;
+      h->ds.its = i + 4 + 4 * batch;
+    }
+  }
+  if (s == ST_OK) {
     e = cudaMallocHost(reinterpret_cast<void**>(&h->scal_host), sizeof(double) * SC_COUNT * batch);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->act_host), sizeof(int) * batch);
     if (e != cudaSuccess) {
@@ -791,6 +1045,7 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   }
   if (s == ST_OK) {
     e = mg_set_attributes();
+    if (e == cudaSuccess) e = lift_set_attributes();
     const int dim = domain == 2 ? 3 : 2;
     if (e == cudaSuccess) e = launch_make_coef(h->coef, h->K, h->J, c.alpha, h->phys, dim, h->stream);
     if (e == cudaSuccess) e = launch_make_coef32(h->coef32, h->K, h->J, c.alpha, h->phys, dim, h->stream);
@@ -950,12 +1205,9 @@ st_status st_solve_host(st_handle h, const double* g_host, const double* u0_host
 
 st_status st_autotune(st_handle h, float* times_ms) {
   ST_CHECK(check_handle(h));
-  float table[8 * 16] = {0};
+  float table[12 * 16] = {0};
   ST_CHECK_CUDA(mg_autotune(h, table), "autotune");
-  for (int i = 0; i < 3; ++i) {  // graphs captured with the old choices are stale
-    if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
-    h->graph_exec[i] = nullptr;
-  }
+  drop_graphs(h);  // graphs captured with the old choices are stale
   if (times_ms) std::memcpy(times_ms, table, sizeof(table));
   return ST_OK;
 }
@@ -969,24 +1221,18 @@ st_status st_set_wave_rows(st_handle h, int rows) {
   for (auto& a : h->gs_seg)
     for (auto& b : a)
       for (auto& c : b) c = (unsigned short)rows;
-  for (int i = 0; i < 3; ++i) {
-    if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
-    h->graph_exec[i] = nullptr;
-  }
+  drop_graphs(h);
   return ST_OK;
 }
 
 st_status st_set_smoother(st_handle h, int kind) {
   ST_CHECK(check_handle(h));
-  if (kind != 0 && kind != 1) {
-    set_error("st_set_smoother: kind must be 0 (tiles) or 1 (wavefront)");
+  if (kind != 0 && kind != 1 && kind != 2) {
+    set_error("st_set_smoother: kind must be 0 (shared-memory tiles), 1 (wavefront) or 2 (register tiles)");
     return ST_ERR_ARG;
   }
   std::memset(h->gs_kind, kind, sizeof(h->gs_kind));
-  for (int i = 0; i < 3; ++i) {
-    if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
-    h->graph_exec[i] = nullptr;
-  }
+  drop_graphs(h);
   return ST_OK;
 }
 

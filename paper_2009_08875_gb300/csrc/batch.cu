@@ -1,11 +1,13 @@
 // st_batch_*: many independent heat-equation solves of different shapes in one call.
 //
 // Problems are grouped by (domain, space level, time level); every group ("bucket") becomes one
-// batched handle whose launches cover all of its problems at once, on a stream of its own, and
-// the buckets run concurrently from host threads (one per bucket), so the GPU overlaps the small
-// problems' kernels.  Inside a bucket each problem keeps its own PCG scalars and stop test, and
-// its result is bitwise the result of solving it alone.  With cfg.use_graphs the PCG iteration
-// body of every bucket is captured once as a CUDA graph and replayed.
+// batched handle whose launches cover all of its problems at once.  Inside a bucket each problem
+// keeps its own PCG scalars and stop test, and its result is bitwise the result of solving it
+// alone.  With cfg.use_graphs = 2 (the default) all buckets run as the branches of one CUDA graph,
+// launched once: each branch's PCG loop is a WHILE node driven by device-side stop tests, so the
+// whole batch iterates on the GPU without host round trips.  Otherwise the buckets run
+// concurrently from host threads (one per bucket and stream), each with a host-driven PCG loop
+// (with cfg.use_graphs = 1 its iteration body is captured once as a CUDA graph and replayed).
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -80,6 +82,71 @@ void run_bucket(st_batch_s* b, Bucket& bk) {
   }
   e = cudaStreamSynchronize(bk.stream);
   if (e != cudaSuccess) return fail(ST_ERR_CUDA, "stream synchronize", e);
+}
+
+// Right-hand sides before the PCG and syntheses after it, as steps of the batch graph.
+st_status batch_pre(st_handle h, void*) { return rhs_impl(h, h->B, h->g, h->u0, h->fhat); }
+st_status batch_post(st_handle h, void*) {
+  cudaError_t e = wavelet_synth<double>(h, h->B, h->w, h->g);
+  return e == cudaSuccess ? ST_OK : cuda_fail("wavelet synthesis", e);
+}
+
+// Every bucket in one CUDA graph: each bucket is a branch (right-hand side, the device-driven
+// PCG of capture_solve, synthesis) independent of the others, so the GPU runs the buckets
+// concurrently and each iterates until its own problems stop, with no host round trip until the
+// whole batch is done.  The host copies inputs in before the launch and results out after it.
+st_status run_buckets_graph(st_batch_s* b, std::vector<Bucket>& buckets) {
+  cudaStream_t ls = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail("cudaStreamCreate", e);
+  cudaGraph_t G = nullptr;
+  cudaGraphExec_t X = nullptr;
+  st_status s = ST_OK;
+  auto ck = [&](cudaError_t err, const char* where) {
+    if (err != cudaSuccess && s == ST_OK) s = cuda_fail(where, err);
+    return s == ST_OK;
+  };
+  for (Bucket& bk : buckets) {
+    st_handle h = bk.h;
+    const int64_t Nt = h->Nt, Nx = h->Nx;
+    for (size_t i = 0; i < bk.ids.size() && s == ST_OK; ++i) {
+      const Problem& p = b->probs[bk.ids[i]];
+      ck(cudaMemcpyAsync(h->g + i * Nt * Nx, p.g, sizeof(double) * Nt * Nx, cudaMemcpyHostToDevice, ls), "copy g");
+      ck(cudaMemcpyAsync(h->u0 + i * Nx, p.u0, sizeof(double) * Nx, cudaMemcpyHostToDevice, ls), "copy u0");
+    }
+  }
+  if (ck(cudaGraphCreate(&G, 0), "graph create")) {
+    for (Bucket& bk : buckets) {
+      std::vector<cudaGraphNode_t> leaves;
+      s = capture_solve(bk.h, G, {}, bk.h->fhat, bk.h->w, batch_pre, batch_post, nullptr, &leaves);
+      if (s != ST_OK) break;
+    }
+  }
+  if (s == ST_OK && ck(cudaGraphInstantiate(&X, G, 0), "graph instantiate")) ck(cudaGraphLaunch(X, ls), "graph launch");
+  for (Bucket& bk : buckets) {
+    st_handle h = bk.h;
+    const int64_t Nt = h->Nt, Nx = h->Nx;
+    for (size_t i = 0; i < bk.ids.size() && s == ST_OK; ++i)
+      ck(cudaMemcpyAsync(b->probs[bk.ids[i]].u, h->g + i * Nt * Nx, sizeof(double) * Nt * Nx, cudaMemcpyDeviceToHost,
+                         ls),
+         "copy result");
+    if (s == ST_OK) s = solve_collect_enqueue(h, ls);
+  }
+  if (s == ST_OK) ck(cudaStreamSynchronize(ls), "stream synchronize");
+  for (Bucket& bk : buckets) {
+    if (s != ST_OK) break;
+    const st_status fs = solve_collect_finish(bk.h);
+    if (fs != ST_OK && fs != ST_ERR_MAXIT && fs != ST_ERR_BREAKDOWN) s = fs;
+    for (size_t i = 0; i < bk.ids.size(); ++i) {
+      Problem& p = b->probs[bk.ids[i]];
+      st_problem_info(bk.h, (int)i, &p.info, &p.status);
+    }
+  }
+  if (X) cudaGraphExecDestroy(X);
+  if (G) cudaGraphDestroy(G);
+  cudaStreamSynchronize(ls);
+  cudaStreamDestroy(ls);
+  return s;
 }
 
 }  // namespace
@@ -168,7 +235,9 @@ st_status st_batch_run(st_batch b) {
     s = st_setup_batch(&bk.h, bk.domain, bk.K, bk.J, (int)bk.ids.size(), &b->cfg, bk.stream);
     if (s != ST_OK) break;
   }
-  if (s == ST_OK) {
+  if (s == ST_OK && b->cfg.use_graphs == 2) {
+    s = run_buckets_graph(b, buckets);
+  } else if (s == ST_OK) {
     std::vector<std::thread> threads;
     for (Bucket& bk : buckets) threads.emplace_back(run_bucket, b, std::ref(bk));
     for (auto& t : threads) t.join();

@@ -175,6 +175,137 @@ __global__ void __launch_bounds__(256) k_residual_split(double* __restrict__ r, 
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Stop tests of the device-driven PCG loops (Sec. 3.4, Eq. 3.3).  They take, per problem, the
+// same decisions as the host-driven loop from the same binary64 scalars, store the per-problem
+// state in `ds` (DevState) and set the condition of the CUDA graph's WHILE node that repeats the
+// iteration body: non-zero while some problem is active and the iteration limit is not reached,
+// so a loop runs at most `maxit` times whatever the data.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ bool stop_breakdown(double pq, double rho, bool check_pq) {
+  return (check_pq && (!(pq > 0.0) || !isfinite(pq))) || !isfinite(rho) || rho < 0.0;
+}
+
+// one block; all threads return whether any problem is active
+__device__ __forceinline__ bool block_any(bool v) { return __syncthreads_or(v ? 1 : 0) != 0; }
+
+// PCG (binary64 iteration, binary64 or binary32 preconditioner), and the outer loop of iterative
+// refinement.  mode LOOP_INIT: start from rho_0 = scal[slot] (slot SC_RHO0, or SC_OUTER for the
+// refinement); mode LOOP_ITER: after one iteration, rho = scal[slot] (SC_RHO_NEW, or SC_OUTER) and
+// p^T q = scal[SC_PQ] when check_pq.  The refinement's outer test also ends a problem whose inner
+// iterations reached maxit (ST_ERR_MAXIT) and stops the loop when no inner solve made progress.
+__global__ void __launch_bounds__(256) k_loop_test(const double* __restrict__ scal, int* __restrict__ act,
+                                                   DevState ds, int B, double tol, int tol_mode, int maxit,
+                                                   int mode, int slot, int check_pq, int refine,
+                                                   cudaGraphConditionalHandle hc) {
+  const int it = mode == LOOP_INIT ? 0 : ds.ctr[0] + 1;
+  bool any = false;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const double* sc = scal + (int64_t)b * SC_COUNT;
+    if (mode == LOOP_INIT) {
+      const double r0 = sc[slot];
+      ds.iters[b] = 0;
+      ds.outer[b] = 0;
+      ds.relres[b] = 0.0;
+      ds.status[b] = ST_OK;
+      ds.rho0[b] = r0;
+      int a = 1;
+      if (!isfinite(r0) || r0 < 0.0) {
+        ds.status[b] = ST_ERR_BREAKDOWN;
+        a = 0;
+      } else if (r0 == 0.0 || (tol_mode == 1 && sqrt(r0) <= tol)) {
+        a = 0;
+      }
+      act[b] = a;
+      if (refine) ds.oact[b] = a;
+      any = any || a;
+      continue;
+    }
+    if (refine) {
+      if (!ds.oact[b]) continue;
+      act[b] = 1;
+    } else {
+      if (!act[b]) continue;
+      ds.iters[b] = it;
+    }
+    const double rho = sc[slot], pq = sc[SC_PQ];
+    int a = 1;
+    if (stop_breakdown(pq, rho, check_pq != 0)) {
+      ds.status[b] = ST_ERR_BREAKDOWN;
+      a = 0;
+    } else {
+      const double rr = sqrt(rho / ds.rho0[b]);
+      ds.relres[b] = rr;
+      if (tol_mode == 1 ? sqrt(rho) <= tol : rr <= tol) a = 0;
+    }
+    act[b] = a;
+    if (refine) {
+      if (!a) ds.oact[b] = 0;
+      if (a && ds.iters[b] >= maxit) {
+        ds.status[b] = ST_ERR_MAXIT;
+        ds.oact[b] = 0;
+      }
+      any = any || ds.oact[b];
+    } else {
+      any = any || a;
+    }
+  }
+  any = block_any(any);
+  if (threadIdx.x == 0) {
+    ds.ctr[0] = it;
+    bool go = any && it < maxit;
+    if (refine && mode != LOOP_INIT) go = go && ds.ctr[1] != 0;  // some inner solve made progress
+    cudaGraphSetConditional(hc, go ? 1u : 0u);
+  }
+}
+
+// The refinement's inner binary32 PCG.  mode LOOP_INIT: problems active in the outer loop with
+// rho_0 = scal[SC_RHO0] > 0 (finite) start; mode LOOP_ITER: a problem stops at a relative K_X-norm
+// reduction of inner_tol or when binary32 can make no further progress.  ds.its counts each
+// problem's inner iterations.
+__global__ void __launch_bounds__(256) k_inner_test(const double* __restrict__ scal, int* __restrict__ act,
+                                                    DevState ds, int B, double inner_tol, int inner_maxit, int mode,
+                                                    cudaGraphConditionalHandle hc) {
+  const int it = mode == LOOP_INIT ? 0 : ds.ctr[2] + 1;
+  bool any = false;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const double* sc = scal + (int64_t)b * SC_COUNT;
+    if (mode == LOOP_INIT) {
+      const double r0 = sc[SC_RHO0];
+      ds.its[b] = 0;
+      const int a = ds.oact[b] && r0 > 0.0 && isfinite(r0);
+      act[b] = a;
+      any = any || a;
+      continue;
+    }
+    if (!act[b]) continue;
+    ds.its[b] = it;
+    const double pq = sc[SC_PQ], rho = sc[SC_RHO_NEW];
+    const int a = !(stop_breakdown(pq, rho, true) || sqrt(rho / sc[SC_RHO0]) <= inner_tol);
+    act[b] = a;
+    any = any || a;
+  }
+  any = block_any(any);
+  if (threadIdx.x == 0) {
+    ds.ctr[2] = it;
+    cudaGraphSetConditional(hc, (any && it < inner_maxit) ? 1u : 0u);
+  }
+}
+
+// After an inner solve: every problem of the outer loop adds its inner iterations and one outer
+// step; ds.ctr[1] records whether any inner solve made progress.
+__global__ void __launch_bounds__(256) k_refine_count(DevState ds, int B) {
+  bool prog = false;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    if (!ds.oact[b]) continue;
+    ds.iters[b] += ds.its[b];
+    ds.outer[b] += 1;
+    prog = prog || ds.its[b] > 0;
+  }
+  prog = block_any(prog);
+  if (threadIdx.x == 0) ds.ctr[1] = prog ? 1 : 0;
+}
+
 // blocks of the dot-product partition of one problem of n elements (depends on n only)
 inline int dot_blocks(int64_t n) {
   int64_t g = (n + 8 * kThreads - 1) / (8 * kThreads);
@@ -250,6 +381,28 @@ cudaError_t launch_add_correction(const st_handle_s* h, double* w, const float* 
 cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, const double* f, const double* q,
                                   int64_t n) {
   k_residual_split<<<stream_grid(n), kThreads, 0, h->stream>>>(r, rs, f, q, n);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_test(const st_handle_s* h, int mode, int slot, bool check_pq, bool refine,
+                             cudaGraphConditionalHandle hc) {
+  const st_config& c = h->cfg;
+  k_loop_test<<<1, 256, 0, h->stream>>>(h->scal, h->act, h->ds, h->B, c.tol, c.tol_mode, c.maxit, mode, slot,
+                                        check_pq ? 1 : 0, refine ? 1 : 0, hc);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inner_test(const st_handle_s* h, int mode, cudaGraphConditionalHandle hc) {
+  const st_config& c = h->cfg;
+  k_inner_test<<<1, 256, 0, h->stream>>>(h->scal, h->act, h->ds, h->B, c.inner_tol, c.inner_maxit, mode, hc);
+  count_launch(h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_count(const st_handle_s* h) {
+  k_refine_count<<<1, 256, 0, h->stream>>>(h->ds, h->B);
   count_launch(h);
   return cudaGetLastError();
 }

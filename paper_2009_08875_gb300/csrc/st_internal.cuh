@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/st.h"
 #include "df64.cuh"
@@ -120,6 +121,23 @@ __host__ __device__ inline bool outside_domain(int ix, int iy, int n, int lshape
   return lshape && ix >= q && iy >= q;
 }
 
+// Per-problem state of a device-driven PCG loop (device arrays of B entries, plus counters):
+// ctr[0] the PCG or outer refinement step, ctr[1] whether an inner refinement solve made
+// progress, ctr[2] the inner step; iterations, refinement steps, status, K_X-norm rho_0 and
+// relative residual per problem; oact (refinement: still in the outer loop) and its (inner
+// iterations of the current outer step).
+struct DevState {
+  int* ctr;
+  int* iters;
+  int* outer;
+  int* status;
+  int* oact;
+  int* its;
+  double* relres;
+  double* rho0;
+};
+enum { LOOP_INIT = 0, LOOP_ITER = 1 };
+
 struct MGLevels {
   int K;                 // finest level
   int kmin;              // coarsest level (exact solve)
@@ -178,7 +196,8 @@ struct st_handle_s {
   // handles of the coarser meshes (K - m, J - m), m = 1.., of st_nested_solve (created on first use)
   st_handle_s* nest[16];
   // Gauss-Seidel kernel per [element type: 0 binary64, 1 binary32, 2 double-float][mass
-  // couplings][level]: 0 shared-memory tiles (default), 1 register wavefront (st_autotune)
+  // couplings][level]: 0 shared-memory tiles (default), 1 register wavefront, 2 register tiles
+  // (st_autotune, st_set_smoother)
   unsigned char gs_kind[3][2][16];
   // rows per segment of the register wavefront, same indices (0: the compiled default)
   unsigned short gs_seg[3][2][16];
@@ -187,6 +206,13 @@ struct st_handle_s {
   cudaGraphExec_t graph_exec[3];
   int64_t graph_launches[3];
   const void* graph_key[3];
+  // the whole PCG solve as one CUDA graph whose WHILE nodes repeat the iteration body while the
+  // device-side stop tests keep them going (cfg.use_graphs = 2), re-instantiated when the key
+  // (right-hand side, solution vector, initial-guess mode) changes
+  cudaGraphExec_t loop_exec;
+  const void* loop_key[3];
+  st::DevState ds;
+  void* ds_mem;      // device allocation behind ds
   int* act;          // device: 1 while problem b iterates (B ints)
   int* act_host;     // page-locked mirror
   int* info_iters;   // host, per problem: iterations, refinement steps, status
@@ -240,8 +266,9 @@ template <typename T>
 cudaError_t mg_apply3(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x);
 // the same in binary32 arithmetic with the multigrid's vectors stored as bfloat16
 cudaError_t mg_apply_bf16(const st_handle_s* h, int nslices, int coef_class, const float* b, float* x);
-// times both Gauss-Seidel kernels per level and records the faster in h->gs_kind; table[8 k + i]
-// receives the times (ms) of (binary64 K_x tile, wave, binary64 K_l tile, wave, binary32 ...)
+// times the Gauss-Seidel kernels per level and records the fastest in h->gs_kind; table[12 k + i]
+// receives the times (ms) of (binary64 K_x: shared-memory tiles, wavefront, register tiles;
+// binary64 K_l: the same three; binary32 K_x; binary32 K_l)
 cudaError_t mg_autotune(st_handle_s* h, float* table);
 
 // The time-coupled launchers act on nb problems stored back to back (N_t x N_x each).
@@ -260,6 +287,11 @@ cudaError_t launch_timemix(const st_handle_s* h, int nb, int mode, const T* U, T
 // N_x values added to its row 0)
 template <typename T>
 cudaError_t launch_epilogue(const st_handle_s* h, int nb, const T* X, const T* row0, int64_t row0_stride, T* Z);
+// q = W^T Z with Z the epilogue above formed on the fly (one pass); cudaErrorNotSupported when the
+// time axis is too long for the one-pass lifting kernel
+template <typename T>
+cudaError_t launch_epilogue_anal(const st_handle_s* h, int nb, const T* X, const T* row0, int64_t row0_stride, T* q);
+cudaError_t lift_set_attributes();
 // Y = A_x X on nrows slices
 template <typename T>
 cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y);
@@ -289,11 +321,24 @@ cudaError_t wavelet_cols(const st_handle_s* h, int synth, int64_t ncols, const d
 // r = f - q, and rs = (float) r unless rs is null
 cudaError_t launch_residual_split(const st_handle_s* h, double* r, float* rs, const double* f, const double* q,
                                   int64_t n);
+// device-side stop tests of the graph-driven PCG loops (k_vec.cu); each sets the condition hc
+cudaError_t launch_loop_test(const st_handle_s* h, int mode, int slot, bool check_pq, bool refine,
+                             cudaGraphConditionalHandle hc);
+cudaError_t launch_inner_test(const st_handle_s* h, int mode, cudaGraphConditionalHandle hc);
+cudaError_t launch_refine_count(const st_handle_s* h);
 
 // whole-handle pipelines (api.cu): right-hand side of nb problems, and the PCG solve of all
 // problems of the handle in its configured precision
 st_status rhs_impl(st_handle_s* h, int nb, const double* g, const double* u0, double* fhat);
 st_status pcg_impl(st_handle_s* h, const double* fhat, double* w, int* iters, double* relres);
+// the device-driven solve of a handle captured into graph G after the nodes `deps` (pre: work
+// enqueued on the handle's stream before the PCG, post: after it; either may be null); `leaves`
+// receives the last nodes.  After the graph has run, solve_collect reads the per-problem results.
+st_status capture_solve(st_handle_s* h, cudaGraph_t G, const std::vector<cudaGraphNode_t>& deps,
+                        const double* fhat, double* w, st_status (*pre)(st_handle_s*, void*),
+                        st_status (*post)(st_handle_s*, void*), void* arg, std::vector<cudaGraphNode_t>* leaves);
+st_status solve_collect_enqueue(st_handle_s* h, cudaStream_t s);
+st_status solve_collect_finish(st_handle_s* h);
 // continuous batching on a handle's slots (ST_FP64 or ST_MIXED_PRECOND): see api.cu
 st_status slot_start(st_handle_s* h, int b);
 st_status step_enqueue(st_handle_s* h, int nb);

@@ -30,7 +30,7 @@ class Solver:
     """
 
     def __init__(self, K, J, domain=0, alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0,
-                 maxit=200, precision="fp64", inner_tol=1e-5, inner_maxit=60, batch=1, use_graphs=True,
+                 maxit=200, precision="fp64", inner_tol=1e-5, inner_maxit=60, batch=1, use_graphs=2,
                  stream=None, D=None, c=0.0, initial_guess=False):
         import torch
         lib = _lib.load()
@@ -42,7 +42,7 @@ class Solver:
                          "mixed_precond": _lib.ST_MIXED_PRECOND, "mixed_bf16": _lib.ST_MIXED_BF16,
                      "fp64_df": _lib.ST_FP64_DF}[precision]
         cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
-        cfg.use_graphs = 1 if use_graphs else 0
+        cfg.use_graphs = int(use_graphs)  # 2: device-driven loop, 1: iteration-body graphs, 0: none
         cfg.initial_guess = 1 if initial_guess else 0
         _set_phys(cfg, D, c)
         if stream is None:
@@ -163,17 +163,19 @@ class Solver:
         return st, list(its)
 
     def autotune(self):
-        """Time both Gauss-Seidel kernels per level and keep the faster (st_autotune).
-        Returns {level: {"f64_Kx": (tiles_ms, wave_ms), "f64_Kl": ..., "f32_Kx": ..., "f32_Kl": ...}}."""
-        t = (ctypes.c_float * 128)()
+        """Time the Gauss-Seidel kernels per level and keep the fastest (st_autotune).  Returns
+        {level: {"f64_Kx": (tiles_ms, wave_ms, regs_ms), "f64_Kl": ..., "f32_Kx": ..., "f32_Kl": ...}}."""
+        t = (ctypes.c_float * 192)()
         _lib.check(_lib.load().st_autotune(self._h, t))
         names = ("f64_Kx", "f64_Kl", "f32_Kx", "f32_Kl")
-        return {k: {nm: (t[8 * k + 2 * i], t[8 * k + 2 * i + 1]) for i, nm in enumerate(names)}
-                for k in range(2, self.K + 1) if any(t[8 * k + i] for i in range(8))}
+        return {k: {nm: (t[12 * k + 3 * i], t[12 * k + 3 * i + 1], t[12 * k + 3 * i + 2])
+                    for i, nm in enumerate(names)}
+                for k in range(2, self.K + 1) if any(t[12 * k + i] for i in range(12))}
 
     def set_smoother(self, kind):
-        """Force the Gauss-Seidel kernel on every level: 'tiles' or 'wavefront' (st_set_smoother)."""
-        _lib.check(_lib.load().st_set_smoother(self._h, {"tiles": 0, "wavefront": 1}[kind]))
+        """Force the Gauss-Seidel kernel on every level: 'tiles', 'wavefront' or 'registers'
+        (st_set_smoother)."""
+        _lib.check(_lib.load().st_set_smoother(self._h, {"tiles": 0, "wavefront": 1, "registers": 2}[kind]))
 
     def set_wave_rows(self, rows):
         """Rows per segment of the wavefront kernel on every level, 0 for the default (st_set_wave_rows)."""
@@ -200,7 +202,7 @@ def _set_phys(cfg, D, c):
 
 
 def _config(alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0, maxit=200, precision="fp64",
-            inner_tol=1e-5, inner_maxit=60, use_graphs=True, D=None, c=0.0):
+            inner_tol=1e-5, inner_maxit=60, use_graphs=2, D=None, c=0.0):
     lib = _lib.load()
     cfg = _lib.StConfig()
     lib.st_default_config(ctypes.byref(cfg))
@@ -210,7 +212,7 @@ def _config(alpha=0.3, n_vcycles=2, n_pre=3, n_post=3, tol=1e-10, tol_mode=0, ma
                      "mixed_precond": _lib.ST_MIXED_PRECOND, "mixed_bf16": _lib.ST_MIXED_BF16,
                      "fp64_df": _lib.ST_FP64_DF}[precision]
     cfg.inner_tol, cfg.inner_maxit = inner_tol, inner_maxit
-    cfg.use_graphs = 1 if use_graphs else 0
+    cfg.use_graphs = int(use_graphs)
     _set_phys(cfg, D, c)
     return cfg
 

@@ -280,13 +280,33 @@ def test_iteration_counts_match_oracle(J):
     assert abs(n - info["iters"]) <= 1, (J, n, info["iters"])
 
 
+def _table_5_3_oracle():
+    """N_t -> the oracle's multigrid iteration count at K = 9 (tests/golden/table_5_3_oracle.txt,
+    written by make_table_5_3_oracle.py from oracle/ only)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table_5_3_oracle.txt")
+    out = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if line.strip() and not line.startswith("#"):
+                f = line.split()
+                out[int(f[0])] = int(f[1])
+    return out
+
+
 @pytest.mark.parametrize("Nt,its", _table_5_3())
 def test_table_5_3_iteration_counts(Nt, its):
     # Sec. 5.2, Table 5.3: eps = 1e-6 absolute (Eq. 3.3), u = exp(-2 pi^2 t) sin sin, g = 0, K = 9.
-    # The paper does not define its Gauss-Seidel smoother; with this project's reading (3 + 3
-    # symmetric three-colour sweeps, 2 V-cycles) the multigrid is a little less exact than the
-    # paper's, which costs 3 to 5 extra iterations here (with direct inverses the oracle is within
-    # 2 of the printed counts, see test_oracle_schur).  The bound pins the count from both sides.
+    # Where the oracle's count at K = 9 is stored, the GPU must take it within one iteration (the
+    # two differ only in rounding).  Against the paper: with direct inverses the oracle takes the
+    # printed counts at N_t = 9 and 17 and one more from N_t = 33 on (test_oracle_schur); with this
+    # project's multigrid reading (2 V-cycles of 3 + 3 three-colour sweeps, Sec. 5.1; the paper
+    # does not define its smoother) the oracle and the GPU take 3 to 5 more than printed (13, 14
+    # at N_t = 9, 17 against 8, 11): the multigrid's error of about 1e-3 spreads the smooth
+    # solution over other modes that the absolute 1e-6 rule must then resolve.  Lexicographic,
+    # hierarchical (coarse nodes first) and W-cycle smoothers of the same cost change the count by
+    # at most one, so the paper's multigrid is closer to an exact solve than its stated settings
+    # give; the bound below records that gap.
     K = 9
     J = int(np.log2(Nt - 1))
     g, u0, _ = inputs.decaying(K, J)
@@ -295,4 +315,7 @@ def test_table_5_3_iteration_counts(Nt, its):
         s.rhs(dev(g), dev(u0), f)
         w = torch.empty_like(f)
         n, _ = s.pcg_solve(f, w)
+    oracle = _table_5_3_oracle().get(Nt)
+    if oracle is not None:
+        assert abs(n - oracle) <= 1, (Nt, n, oracle)
     assert its <= n <= its + 5, (Nt, n, its)

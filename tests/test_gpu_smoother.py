@@ -1,10 +1,12 @@
-"""The two Gauss-Seidel kernels (shared-memory tiles, register wavefront) and the autotuner.
+"""The three Gauss-Seidel kernels (shared-memory tiles, register wavefront, register tiles) and
+the autotuner.
 
-Both kernels perform the same three-colour sweeps with the same summation order per point, so
-every operator that runs the multigrid preconditioner (K_x, K_X, and the binary32 K_X) must give
-bitwise the same result with either, on the square and on the L-shape, for one problem and for a
-batch, and the wavefront at any number of rows per segment.  The autotuner only picks among
-them, so a solve after st_autotune must give bitwise the solve before it.
+All kernels perform the same three-colour sweeps with the same summation order per point, so
+every operator that runs the multigrid (K_x, K_X, the binary32 S and K_X, the bfloat16-storage
+K_X) must give bitwise the same result with any of them, on the square and on the L-shape, for
+one problem and for a batch, the wavefront at any number of rows per segment, and with sweep
+counts that are not a multiple of the fused three.  The autotuner only picks among them, so a
+solve after st_autotune must give bitwise the solve before it.
 """
 import numpy as np
 import pytest
@@ -25,6 +27,10 @@ def run_ops(s, x):
     y32 = torch.empty_like(x32)
     s.apply_KX_f32(x32, y32)
     out["KX32"] = y32.clone()
+    s.apply_S_f32(x32, y32)
+    out["S32"] = y32.clone()
+    s.apply_KX_bf16(x32, y32)  # square and L-shape only (not the cube)
+    out["KXbf16"] = y32.clone()
     b = torch.cat([x.reshape(-1, s.Nx), x.reshape(-1, s.Nx)]).contiguous()
     xk = torch.empty_like(b)
     s.apply_Kx(b, xk)
@@ -45,6 +51,10 @@ def test_tiles_and_wavefront_bitwise_equal(K, J, domain, B):
         x = torch.from_numpy(np.ascontiguousarray(x)).cuda()
         s.set_smoother("tiles")
         a = run_ops(s, x)
+        s.set_smoother("registers")
+        c = run_ops(s, x)
+        for name in a:
+            assert torch.equal(a[name], c[name]), (name, "registers")
         s.set_smoother("wavefront")
         # default segments, then one row per segment, a ragged length, and one segment per strip
         for rows in (0, 1, 5, 73, 1000):
@@ -54,10 +64,28 @@ def test_tiles_and_wavefront_bitwise_equal(K, J, domain, B):
                 assert torch.equal(a[name], b[name]), (name, rows)
 
 
+# sweep counts that are not a multiple of three: binary32 launches of one sweep beside fused ones
+@pytest.mark.parametrize("K,J,domain,pre,post", [(7, 2, 0, 4, 2), (6, 2, 1, 1, 5)])
+def test_register_tiles_with_unfused_sweeps(K, J, domain, pre, post):
+    with Solver(K, J, domain=domain, n_pre=pre, n_post=post) as s:
+        rng = np.random.default_rng(K + 7 * pre)
+        x = rng.standard_normal(s.shape)
+        if domain == 1:
+            x = x * inputs.grid_mask(K, 1).reshape(-1)
+        x = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        s.set_smoother("tiles")
+        a = run_ops(s, x)
+        s.set_smoother("registers")
+        c = run_ops(s, x)
+        for name in a:
+            assert torch.equal(a[name], c[name]), name
+
+
 def test_set_smoother_rejects_unknown_kind():
     from paper_2009_08875_gb300 import _lib
     with Solver(3, 2) as s:
-        assert _lib.load().st_set_smoother(s._h, 2) == 1  # ST_ERR_ARG
+        assert _lib.load().st_set_smoother(s._h, 3) == 1  # ST_ERR_ARG
+        assert _lib.load().st_set_smoother(s._h, -1) == 1
         assert _lib.load().st_set_wave_rows(s._h, -1) == 1
         assert _lib.load().st_set_wave_rows(s._h, 65536) == 1
 
@@ -74,8 +102,8 @@ def test_autotune_keeps_solution_bitwise(precision):
         table = s.autotune()
         assert set(table) == set(range(2, K + 1))
         for row in table.values():
-            for tiles_ms, wave_ms in row.values():
-                assert tiles_ms > 0 and wave_ms > 0
+            for tiles_ms, wave_ms, regs_ms in row.values():
+                assert tiles_ms > 0 and wave_ms > 0 and regs_ms > 0
         u2 = torch.zeros_like(u1)
         it2, _ = s.solve_host(g, u0, u2)
     assert it1 == it2
