@@ -38,17 +38,26 @@ SAMPLE_K, SAMPLE_J = 9, 2
 FP64_INST_PEAK = 1.25e12 / 2.0
 
 # DRAM traffic (bytes) per finest-level sweep launch from one ncu capture, valid only for the
-# kernel source it was taken on (keyed by the SHA-256 of k_mg.cu, then by (operator, kernel));
-# otherwise reported as null.
+# kernel source it was taken on (keyed by the SHA-256 of the kernel's source text, see
+# kernel_source_hash, then by (operator, kernel)); otherwise reported as null.
 NCU_TRAFFIC = {
     # ncu --set full on K = 9, J = 5 (33 / 66 slices), mean of launches 2 and 3, read + write,
     # scaled by slices to the full launch (513 / 1026 slices): profiles/k_gs_*_fp64_*_K9_J5.md
-    "b694fb98c455126ba5435ca8313f1298e9652647f2ffc371902fd9db7298e6e2": {
+    "248dbddb5b78589363dae625f48279c908013a016f61799ce1e3d8627f4fe05d": {  # k_gs_sweep
         ("Kl", "tiles"): (137.924e6 + 36.499e6) * 513 / 33,
         ("Kx", "tiles"): (275.788e6 + 105.357e6) * 1026 / 66,
+    },
+    "5bda114a3f62bd5989c13a9ed676f578e1eb667e0e8578e876c4030c1aff4279": {  # k_gs_wave
         ("Kl", "wavefront"): (154.963e6 + 41.567e6) * 513 / 33,
     },
 }
+KERNEL_OF = {"tiles": ("k_gs_sweep", "k_mg.cu"), "wavefront": ("k_gs_wave", "k_mg.cu"),
+             "registers": ("k_gs_reg", "k_gs_reg.cu")}
+
+
+def traffic_for(op, kind):
+    name, fname = KERNEL_OF[kind]
+    return NCU_TRAFFIC.get(kernel_source_hash(name, fname), {}).get((op, kind))
 
 
 def parse():
@@ -59,6 +68,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--K", type=int, default=K_SPACE)
     ap.add_argument("--J", type=int, default=J_TIME)
+    ap.add_argument("--domain", type=int, choices=[0, 1, 2], default=0,
+                    help="domain of the main timed solve: 0 square (the benchmark), 1 L-shape, 2 cube (profiling aid)")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="plain launches in the main solve (ncu cannot profile kernels inside graphs with "
+                         "conditional nodes); profiling aid")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
@@ -72,7 +86,8 @@ def parse():
     ap.add_argument("--serve-sweep-requests", type=int, default=150,
                     help="requests per point of the offered-load sweep (25/50/90%% of capacity)")
     ap.add_argument("--batch-problems", type=int, default=256)
-    ap.add_argument("--smoother", choices=["auto", "tiles", "wavefront", "registers"], default="auto",
+    ap.add_argument("--smoother", choices=["auto", "tiles", "wavefront", "registers", "registers_8x12", "registers_6x16"],
+                    default="auto",
                     help="Gauss-Seidel kernel: autotuned per level (default) or one kernel on every level")
     ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_precond", "mixed_bf16", "fp64_df"], default="fp64",
                     help="precision of the main timed solve (profiling aid; the bench line uses fp64)")
@@ -473,9 +488,16 @@ def measured_hbm_peak():
         return 6800.0, "fallback 6.8 TB/s of the profiling recipe"
 
 
-def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_2009_08875_gb300", "csrc", "k_mg.cu"), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()
+def kernel_source_hash(name="k_gs_sweep", fname="k_mg.cu"):
+    """SHA-256 of the source text of one kernel: from its template line to the closing brace at
+    column 0 (the captured counters stay valid while this text is unchanged)."""
+    with open(os.path.join(ROOT, "paper_2009_08875_gb300", "csrc", fname)) as fh:
+        lines = fh.read().split("\n")
+    start = next(i for i, ln in enumerate(lines) if f" {name}(" in ln and "__global__" in ln)
+    while start > 0 and lines[start - 1].startswith("template"):
+        start -= 1
+    end = next(i for i in range(start, len(lines)) if lines[i] == "}")
+    return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()
 
 
 def pick_smoother(solver, kind):
@@ -517,8 +539,11 @@ def run_ours(args):
     from paper_2009_08875_gb300 import Solver, inputs
 
     K, J = args.K, args.J
-    g_np, u0_np, u_exact_np = inputs.manufactured(K, J)
-    solver = Solver(K, J, tol=TOL, tol_mode=0, maxit=500, precision=args.precision)
+    g_np, u0_np, u_exact_np = inputs.manufactured(K, J, args.domain)
+    if args.domain == 1:  # the library stores the L-shape on the square's grid
+        g_np, u0_np, u_exact_np = (inputs.to_grid(K, 1, a) for a in (g_np, u0_np, u_exact_np))
+    solver = Solver(K, J, domain=args.domain, tol=TOL, tol_mode=0, maxit=500, precision=args.precision,
+                    use_graphs=0 if args.no_graphs else 2)
     tune = pick_smoother(solver, args.smoother)
     stream = solver.stream
     Nt, Nx = solver.shape
@@ -644,34 +669,55 @@ def run_ours(args):
     if not args.no_cube:
         Kc, Jc = 6, J
         gc_np, u0c_np, _ = inputs.manufactured(Kc, Jc, inputs.CUBE)
-        cs = Solver(Kc, Jc, domain=inputs.CUBE, tol=TOL, tol_mode=0, maxit=500)
         gc, u0c = torch.from_numpy(gc_np).cuda(), torch.from_numpy(u0c_np).cuda()
-        fc = torch.empty(cs.shape, dtype=torch.float64, device="cuda")
-        wc, uc = torch.empty_like(fc), torch.empty_like(fc)
+        cube_arms = {}
+        for prec in ("fp64", "fp64_df"):
+            cs = Solver(Kc, Jc, domain=inputs.CUBE, tol=TOL, tol_mode=0, maxit=500, precision=prec)
+            fc = torch.empty(cs.shape, dtype=torch.float64, device="cuda")
+            wc, uc = torch.empty_like(fc), torch.empty_like(fc)
 
-        def cstep():
-            cs.rhs(gc, u0c, fc)
-            its_c, _ = cs.pcg_solve(fc, wc)
-            cs.synthesize(wc, uc)
-            return its_c
+            def cstep():
+                cs.rhs(gc, u0c, fc)
+                its_c, _ = cs.pcg_solve(fc, wc)
+                cs.synthesize(wc, uc)
+                return its_c
 
-        for _ in range(max(1, args.warmup)):
-            cstep()
-        torch.cuda.synchronize()
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        its_c = 0
-        c0.record(cs.stream)
-        for _ in range(args.steps):
-            its_c += cstep()
-        c1.record(cs.stream)
-        torch.cuda.synchronize()
-        cms = c0.elapsed_time(c1)
-        cube = {"workload": f"3D heat eq., unit cube (Kuhn tetrahedra), K={Kc} (N_x={cs.Nx}), J={Jc} (N_t={cs.Nt}), "
-                            "u=(1+t^2)sin(pi x)sin(pi y)sin(pi z), PCG to rel. 1e-10",
-                "value": world * cs.Nt * cs.Nx * its_c / (cms / 1e3), "unit": "DoF-iter/s", "dtype": "f64",
-                "ms_per_solve": cms / args.steps, "pcg_iterations": its_c / args.steps}
-        cs.close()
+            for _ in range(max(1, args.warmup)):
+                cstep()
+            torch.cuda.synchronize()
+            cs.profile_begin()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            its_c = 0
+            c0.record(cs.stream)
+            for _ in range(args.steps):
+                its_c += cstep()
+            c1.record(cs.stream)
+            torch.cuda.synchronize()
+            cprof = cs.profile_end()
+            cms = c0.elapsed_time(c1)
+            arm = {"value": world * cs.Nt * cs.Nx * its_c / (cms / 1e3), "unit": "DoF-iter/s",
+                   "ms_per_solve": cms / args.steps, "pcg_iterations": its_c / args.steps, "u": uc.clone()}
+            if prec == "fp64":
+                # the finest-level colour steps of K_l (one colour of four timed per sweep)
+                n, msum, ops = cprof["diag_launches"], cprof["diag_ms"], cprof["diag_fp64_ops"]
+                if n and msum > 0:
+                    ach = ops / (msum / 1e3) / 1e9
+                    arm["roofline"] = {"kernel": "finest-level K_l colour step of the cube's Gauss-Seidel (k_gs3), FP64",
+                                       "bound": "alu", "achieved": ach, "peak": FP64_INST_PEAK / 1e9,
+                                       "unit": "G FP64 inst/s (add, mul, fma = 1)", "frac": ach / (FP64_INST_PEAK / 1e9),
+                                       "frac_of_probe": ach / (fp64_probe / 1e9), "launches": n,
+                                       "avg_launch_ms": msum / n,
+                                       "share_of_step": 4.0 * msum / cms if cms > 0 else None,
+                                       "note": "one colour of four timed per sweep; share scaled by 4"}
+            cube_arms[prec] = arm
+            cs.close()
+        u64c = cube_arms["fp64"].pop("u")
+        udf = cube_arms["fp64_df"].pop("u")
+        cube_arms["fp64_df"]["rel_err_vs_fp64_solution"] = ((udf - u64c).abs().max() / u64c.abs().max()).item()
+        cube = dict(cube_arms["fp64"], workload=f"3D heat eq., unit cube (Kuhn tetrahedra), K={Kc} (N_x={(2**Kc-1)**3}), "
+                                                f"J={Jc} (N_t={2**Jc+1}), u=(1+t^2)sin(pi x)sin(pi y)sin(pi z), "
+                                                "PCG to rel. 1e-10", dtype="f64", fp64_df=cube_arms["fp64_df"])
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None
@@ -809,13 +855,12 @@ def run_ours(args):
     top = str(K)
     kind_l = kinds[top]["f64_Kl"] if isinstance(kinds, dict) else args.smoother
     kind_x = kinds[top]["f64_Kx"] if isinstance(kinds, dict) else args.smoother
-    traffic = NCU_TRAFFIC.get(kernel_source_hash(), {})
     roofline = sweep_roof(prof["diag_launches"], prof["diag_ms"], prof["diag_fp64_ops"], prof["diag_bytes"],
-                          f"finest-level K_l Gauss-Seidel sweep, FP64 ({kind_l})", traffic.get(("Kl", kind_l)))
+                          f"finest-level K_l Gauss-Seidel sweep, FP64 ({kind_l})", traffic_for("Kl", kind_l))
     roofline["also"] = sweep_roof(prof["sweep_launches"] - prof["diag_launches"], prof["sweep_ms"] - prof["diag_ms"],
                                   prof["sweep_fp64_ops"] - prof["diag_fp64_ops"],
                                   prof["sweep_bytes"] - prof["diag_bytes"],
-                                  f"finest-level K_x Gauss-Seidel sweep, FP64 ({kind_x})", traffic.get(("Kx", kind_x)))
+                                  f"finest-level K_x Gauss-Seidel sweep, FP64 ({kind_x})", traffic_for("Kx", kind_x))
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -832,7 +877,8 @@ def run_ours(args):
         "metric": "Schur-PCG DoF-iters/s (FP64)", "value": value, "unit": "DoF-iter/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"2D heat eq., unit square, K={K} (N_x={Nx}), J={J} (N_t={Nt}), "
+        "config": {"workload": f"{['2D heat eq., unit square', '2D heat eq., L-shape', '3D heat eq., unit cube'][args.domain]}, "
+                               f"K={K} (N_x={Nx}), J={J} (N_t={Nt}), "
                                "u=(1+t^2)sin(pi x)sin(pi y), PCG to rel. 1e-10",
                    "step": "one full solve: rhs + PCG + synthesis",
                    "pcg_iterations": iters_all / max(1, args.steps) / world,

@@ -78,8 +78,7 @@ typedef enum {
   ST_FP64_DF = 4         /* as ST_FP64, but every multigrid application (K_x in S and in the
                             right-hand side, K_l in K_X) computes in double-float: pairs of
                             binary32 values with error-free transformations, about 48
-                            significant bits (binary64: 53); inputs and outputs stay binary64.
-                            Not on the cube. */
+                            significant bits (binary64: 53); inputs and outputs stay binary64. */
 } st_precision;
 
 typedef struct {
@@ -94,9 +93,15 @@ typedef struct {
   int precision;    /* st_precision                                                         */
   double inner_tol; /* ST_MIXED_FP32 / _BF16: relative K_X-norm reduction of each inner solve */
   int inner_maxit;  /* ST_MIXED_FP32 / _BF16: iteration limit of each inner solve            */
-  int use_graphs;   /* 1: capture each PCG iteration body once as a CUDA graph and replay it
-                       (only on a stream other than the legacy/per-thread default streams
-                       and outside st_profile_begin/end); 0: plain launches               */
+  int use_graphs;   /* 2 (default): the whole PCG solve is one CUDA graph whose WHILE node
+                       repeats the iteration body while device-side stop tests (the same
+                       decisions as the host's, bitwise the same results) keep it going, so
+                       a solve makes no host round trip per iteration; st_batch_run runs all
+                       shape groups as branches of one such graph.  1: the host tests after
+                       every iteration, each iteration body captured once as a CUDA graph and
+                       replayed.  0: plain launches.  Graphs are used only on a stream other
+                       than the legacy/per-thread default streams and outside
+                       st_profile_begin/end (plain launches there).                        */
   double diffusion[3]; /* D = [[d11, d12], [d12, d22]] as (d11, d12, d22) and             */
   double reaction;     /* c of the reaction-diffusion form of Sec. 4,
                           a(eta, zeta) = <D grad eta, grad zeta> + c <eta, zeta>, which
@@ -109,7 +114,7 @@ typedef struct {
 } st_config;
 
 /* Fills *cfg with the paper's settings (alpha 0.3, 2 V-cycles, 3+3 sweeps, Sec. 5.1),
- * tol 1e-10 relative, maxit 200, FP64; inner_tol 1e-5, inner_maxit 60, use_graphs 1;
+ * tol 1e-10 relative, maxit 200, FP64; inner_tol 1e-5, inner_maxit 60, use_graphs 2;
  * D = Id, c = 0 (the heat equation of Sec. 5); initial_guess 0. */
 void st_default_config(st_config* cfg);
 
@@ -120,8 +125,7 @@ void st_default_config(st_config* cfg);
  *   1  L-shape (0,1)^2 minus [1/2,1)^2 stored on the square's grid with zeros outside,
  *      K in 2..12;
  *   2  unit cube, K in 1..8, N_x = (2^K - 1)^3, P1 on the six Kuhn tetrahedra of every grid
- *      cube (the 3D problem of Sec. 5.2); D = Id only, c >= 0; not ST_MIXED_BF16 nor
- *      ST_FP64_DF;
+ *      cube (the 3D problem of Sec. 5.2); D = Id only, c >= 0; not ST_MIXED_BF16;
  *      the column index is (iz (2^K - 1) + iy) (2^K - 1) + ix.
  * The multigrid's coarsest level is 1 (one unknown) on the square and the cube and 2 (five
  * unknowns, dense solve) on the L-shape.  cfg may be NULL (defaults).  Synchronous. */
@@ -170,7 +174,8 @@ st_status st_rhs(st_handle h, const double* g_nodal, const double* u0_nodal, dou
 /* PCG on S_hat w = f_hat with preconditioner K_X (Sec. 3.4), starting from w = 0 (the
  * input content of w is ignored and overwritten) or, with cfg.initial_guess = 1, from the
  * content of w.  Stops by cfg.tol / cfg.tol_mode.
- * Synchronises the bound stream once per iteration (8 scalars read back).
+ * Synchronises the bound stream once at the end with cfg.use_graphs = 2, else once per
+ * iteration (8 scalars per problem read back).
  * *iters receives the iteration count; *relres sqrt(r^T K_X r / r_0^T K_X r_0).
  * With cfg.precision = ST_MIXED_FP32 (or ST_MIXED_BF16) the solve is iterative refinement: each outer step
  * solves S_hat d = r with binary32 PCG to cfg.inner_tol, adds d to w in binary64 and
@@ -351,22 +356,54 @@ st_status st_vec_dot(st_handle h, int64_t n, const double* a, const double* b, d
 /* y = alpha x + beta y over n doubles (asynchronous on the bound stream). */
 st_status st_vec_axpby(st_handle h, int64_t n, double alpha, const double* x, double beta, double* y);
 
-/* Autotuner (not in the paper).  Two Gauss-Seidel kernels compute identical sweeps: shared-
- * memory tiles (the default) and a register wavefront, whose strips of 90 columns are cut into
- * row segments walked by separate warps.  For every multigrid level above the coarsest, for
- * binary64 and binary32 and for K_x (no mass couplings, 2 B N_t slices) and K_l (mass
- * couplings, B N_t slices), this times one pre-smoothing launch of the tiles and of the
- * wavefront at ceil(n / q) rows per segment, q = 1 .. 12 (n = 2^k - 1 on level k), on the
- * handle's workspace and keeps the fastest kernel and segment length for later calls on this
- * handle.  Synchronous.
- * times_ms (may be NULL) receives 8 x 16 floats: times_ms[8 k + i] for level k and i = 0..7 in
- * the order (binary64 K_x: tiles, wavefront; binary64 K_l: tiles, wavefront; binary32 K_x:
- * tiles, wavefront; binary32 K_l: tiles, wavefront). */
+/* The whole time-sharded solve of one rank (Sec. 5.2's time distribution): right-hand side
+ * (Lemma 4.1), PCG (Sec. 3.4, Eq. 3.3: scalars, stop test and updates all here) and synthesis
+ * u = W w, on the rows [lo, hi) of rank `rank` of `nranks` (a power of two <= 2^J; m = 2^J /
+ * nranks, lo = rank m, hi = lo + m, plus row 2^J on the last rank).  The communication goes
+ * through the caller's st_comm: a neighbour row each side of the time mix, a rows <-> columns
+ * exchange around each wavelet transform (rank s lifts the columns [s N_x / P, (s + 1) N_x / P)),
+ * and a sum over the ranks of each inner product.  The rank's own kernels have finished whenever
+ * a callback is called (no kernel waits on another rank).  g_rows, u_rows: device, (hi - lo) x N_x;
+ * u0: device, N_x (read by the rank that owns row 0).  The handle (single problem, the full mesh)
+ * supplies coefficient tables and scratch; the call allocates its row and column buffers for its
+ * duration.  Stops by the handle's cfg.tol / tol_mode / maxit.  Synchronous.  Returns
+ * ST_ERR_MAXIT, ST_ERR_BREAKDOWN, ST_ERR_ARG (bad partition), ST_ERR_CUDA, or ST_ERR_CANCELLED
+ * when a callback reports failure. */
+typedef struct {
+  void* ctx;
+  /* v[0 .. n) <- the sum over the ranks of v[0 .. n) (host memory); 0 on success */
+  int (*allreduce_sum)(void* ctx, double* v, int n);
+  /* for every rank s != own: send send_count[s] doubles from the device buffer send[s] to s and
+   * receive recv_count[s] doubles from s into the device buffer recv[s] (count 0: nothing);
+   * the sends and receives are complete when it returns; 0 on success */
+  int (*exchange)(void* ctx, double* const* send, const int64_t* send_count, double* const* recv,
+                  const int64_t* recv_count);
+} st_comm;
+st_status st_sharded_solve(st_handle h, const st_comm* comm, int rank, int nranks, const double* g_rows,
+                           const double* u0, double* u_rows, int* iters, double* relres);
+
+/* Autotuner (not in the paper).  Three Gauss-Seidel kernels compute identical sweeps:
+ * shared-memory tiles (the default), a register wavefront, whose strips of 90 columns are cut into
+ * row segments walked by separate warps, and register tiles, whose 96-column regions sit in the
+ * registers of a block's warps (binary32: 12 rows x 8 warps, 8 x 12 or 6 x 16, the autotuner
+ * trying each; binary64 and double-float: 6 rows x 8 warps).  For every multigrid level
+ * above the coarsest, for binary64 and binary32 and for K_x (no mass couplings, 2 B N_t slices)
+ * and K_l (mass couplings, B N_t slices), this times one pre-smoothing launch of each kernel (the
+ * wavefront at ceil(n / q) rows per segment, q = 1 .. 12, n = 2^k - 1 on level k; the register
+ * tiles in every block shape) on the handle's
+ * workspace and keeps the fastest kernel and segment length for later calls on this handle.
+ * Synchronous.
+ * times_ms (may be NULL) receives 12 x 16 floats: times_ms[12 k + i] for level k and i = 0..11 in
+ * the order (binary64 K_x: shared-memory tiles, wavefront, register tiles; binary64 K_l: the
+ * same three; binary32 K_x: the same three; binary32 K_l: the same three), each the best over its
+ * segment lengths or block shapes. */
 st_status st_autotune(st_handle h, float* times_ms);
 
 /* Forces one Gauss-Seidel kernel on every level of this handle: kind 0 shared-memory tiles (the
- * state after set-up), 1 register wavefront.  Both give bitwise the same sweeps.  Returns
- * ST_ERR_ARG for any other kind. */
+ * state after set-up), 1 register wavefront, 2, 3, 4 register tiles of block shape 0, 1, 2 (in
+ * binary32 12 rows x 8 warps, 8 x 12, 6 x 16; binary64 and double-float always 6 x 8).  All give
+ * bitwise the same sweeps.  Returns ST_ERR_ARG
+ * for any other kind. */
 st_status st_set_smoother(st_handle h, int kind);
 
 /* Forces the register wavefront's rows per segment on every level of this handle (rows >= 1;
@@ -407,10 +444,10 @@ st_status st_profile_begin(st_handle h);
 st_status st_profile_end(st_handle h, st_profile* out);
 
 /* Measurement hook (not part of the method): the device's sustained fused multiply-add rates,
- * from a throughput kernel of 8 independent x <- x a + c chains per thread and 8 blocks of 256
- * threads per SM, in binary64 (about 2.5e9 fmas) and binary32 (32 times as many), each the best
- * of 3 launches timed with CUDA events on cuda_stream after one warm-up launch, on the current
- * device.  *fp64_fma_per_s and *fp32_fma_per_s receive fmas per second (2 flops each).  Allocates
+ * from a throughput kernel of 4, 8 or 16 independent x <- x a + c chains per thread (the best
+ * kept) and 8 blocks of 256 threads per SM, in binary64 (about 2.5e9 fmas a launch) and binary32
+ * (32 times as many), each the best of 3 launches timed with CUDA events on cuda_stream after one
+ * warm-up launch, on the current device.  *fp64_fma_per_s and *fp32_fma_per_s receive fmas per second (2 flops each).  Allocates
  * nothing (its results are folded into a file-scope device array).  Synchronous. */
 st_status st_probe_fma_rates(void* cuda_stream, double* fp64_fma_per_s, double* fp32_fma_per_s);
 

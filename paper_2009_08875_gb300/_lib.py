@@ -40,6 +40,17 @@ class StProfile(ctypes.Structure):
                 ("f32_diag_bytes", ctypes.c_double)]
 
 
+# st_comm: the communicator callbacks of st_sharded_solve
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_void_p),
+                               ctypes.POINTER(ctypes.c_int64))
+
+
+class StComm(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("allreduce_sum", ALLREDUCE_FN), ("exchange", EXCHANGE_FN)]
+
+
 class STError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -104,6 +115,8 @@ _SIGS = {
     "st_server_cancel": (ctypes.c_int, [_P, ctypes.c_int64]),
     "st_server_stop": (ctypes.c_int, [_P]),
     "st_probe_fma_rates": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "st_sharded_solve": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double)]),
     "st_last_error": (ctypes.c_char_p, []),
 }
 

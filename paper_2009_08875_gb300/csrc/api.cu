@@ -195,14 +195,7 @@ st_status apply_S_nodal_impl(st_handle h, int nb, const T* u, T* y) {
 template <typename T>
 st_status apply_Shat_impl(st_handle h, int nb, const T* w, T* q) {
   ST_CHECK_CUDA(wavelet_synth<T>(h, nb, w, ws<T>(h->U)), "wavelet synthesis");
-  T* U = ws<T>(h->U);
-  ST_CHECK_CUDA(launch_timemix<T>(h, nb, 0, U, ws<T>(h->Y)), "timemix");
-  ST_CHECK_CUDA(mg_apply<T>(h, (int)(2 * nb * h->Nt), 0, ws<T>(h->Y), ws<T>(h->X)), "K_x multigrid");
-  // the epilogue fused into the one-pass analysis where the time axis allows
-  const cudaError_t e = launch_epilogue_anal<T>(h, nb, ws<T>(h->X), U, h->Nt * h->Nx, q);
-  if (e == cudaSuccess) return ST_OK;
-  if (e != cudaErrorNotSupported) return cuda_fail("epilogue and wavelet analysis", e);
-  ST_CHECK_CUDA(launch_epilogue<T>(h, nb, ws<T>(h->X), U, h->Nt * h->Nx, ws<T>(h->Z)), "epilogue");
+  ST_CHECK(apply_S_nodal_impl<T>(h, nb, ws<T>(h->U), ws<T>(h->Z)));
   ST_CHECK_CUDA(wavelet_anal<T>(h, nb, ws<T>(h->Z), q), "wavelet analysis");
   return ST_OK;
 }
@@ -762,9 +755,6 @@ namespace st {
 st_status rhs_impl(st_handle h, int nb, const double* g, const double* u0, double* fhat) {
   ST_CHECK_CUDA(launch_timemix<double>(h, nb, 1, g, h->Y), "timemix (rhs)");
   ST_CHECK_CUDA(mg_apply<double>(h, (int)(2 * nb * h->Nt), 0, h->Y, h->X), "K_x multigrid (rhs)");
-  const cudaError_t e = launch_epilogue_anal<double>(h, nb, h->X, u0, h->Nx, fhat);
-  if (e == cudaSuccess) return ST_OK;
-  if (e != cudaErrorNotSupported) return cuda_fail("epilogue and wavelet analysis (rhs)", e);
   ST_CHECK_CUDA(launch_epilogue<double>(h, nb, h->X, u0, h->Nx, h->Z), "epilogue (rhs)");
   ST_CHECK_CUDA(wavelet_anal<double>(h, nb, h->Z, fhat), "wavelet analysis (rhs)");
   return ST_OK;
@@ -928,8 +918,7 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   ST_REQUIRE(check_phys(c), "st_setup: D must be symmetric positive definite and c >= 0 (finite)");
   ST_REQUIRE(domain != 2 || (c.diffusion[0] == 1.0 && c.diffusion[1] == 0.0 && c.diffusion[2] == 1.0),
              "st_setup: the cube supports D = Id only (c >= 0 is allowed)");
-  ST_REQUIRE(domain != 2 || (c.precision != ST_MIXED_BF16 && c.precision != ST_FP64_DF),
-             "st_setup: ST_MIXED_BF16 and ST_FP64_DF are not available on the cube");
+  ST_REQUIRE(domain != 2 || c.precision != ST_MIXED_BF16, "st_setup: ST_MIXED_BF16 is not available on the cube");
 
   st_handle_s* h = new (std::nothrow) st_handle_s();
   if (!h) {
@@ -1045,7 +1034,6 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
   }
   if (s == ST_OK) {
     e = mg_set_attributes();
-    if (e == cudaSuccess) e = lift_set_attributes();
     const int dim = domain == 2 ? 3 : 2;
     if (e == cudaSuccess) e = launch_make_coef(h->coef, h->K, h->J, c.alpha, h->phys, dim, h->stream);
     if (e == cudaSuccess) e = launch_make_coef32(h->coef32, h->K, h->J, c.alpha, h->phys, dim, h->stream);
@@ -1227,8 +1215,9 @@ st_status st_set_wave_rows(st_handle h, int rows) {
 
 st_status st_set_smoother(st_handle h, int kind) {
   ST_CHECK(check_handle(h));
-  if (kind != 0 && kind != 1 && kind != 2) {
-    set_error("st_set_smoother: kind must be 0 (shared-memory tiles), 1 (wavefront) or 2 (register tiles)");
+  if (kind < 0 || kind > 1 + kRegShapes) {
+    set_error("st_set_smoother: kind must be 0 (shared-memory tiles), 1 (wavefront) or 2..4 (register tiles of "
+              "block shape 0..2)");
     return ST_ERR_ARG;
   }
   std::memset(h->gs_kind, kind, sizeof(h->gs_kind));

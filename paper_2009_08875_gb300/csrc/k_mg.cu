@@ -72,12 +72,6 @@ __global__ void k_make_coef(Coef<T>* coef, int K, int J, double alpha, Phys ph, 
   }
 }
 
-// the coefficients of slice `slice` on level `level` (slice_class)
-template <typename T>
-__device__ __forceinline__ Coef<T> slice_coef(const Coef<T>* coef, int coef_class, int slice, int J, int K,
-                                              int level) {
-  return coef[slice_class(coef_class, slice, J) * (K + 1) + level];
-}
 
 // Nested P1 prolongation: prolong_value (st_internal.cuh).
 
@@ -89,7 +83,6 @@ __device__ __forceinline__ Coef<T> slice_coef(const Coef<T>* coef, int coef_clas
 // slice produce.  Each lane owns three consecutive columns, of which exactly one has the
 // active colour in any row, so every lane does one update per row and step.
 // ---------------------------------------------------------------------------------------
-constexpr int kWR = 96;  // region width = 32 lanes x 3 columns
 
 // Exact solve on level 2 (3 x 3 grid, the coarsest level of the L-shape): one thread per slice
 // assembles C = a A + s M on the level's nodes (rows of nodes outside the domain become the
@@ -435,212 +428,6 @@ __global__ void __launch_bounds__(128) k_gs_wave(G* __restrict__ x_out, const G*
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// Gauss-Seidel in register tiles.  A block of NWARP warps holds a region of 96 columns x
-// NWARP * R rows of one slice in registers: warp w owns the region rows w R .. w R + R - 1 and
-// lane l the columns 3 l .. 3 l + 2 of them, so that in every row exactly one of a lane's three
-// points has the active colour (the colour steps below never branch per lane).  A colour step
-// takes its horizontal neighbours from the lane's own registers or, across a lane boundary, by a
-// shuffle; its vertical neighbours from the rows above and below in registers or, at the edge of
-// a warp's rows, from the neighbouring warp's edge row, exchanged through shared memory once per
-// step.  A colour step reads only points of the other two colours, which the step does not
-// change, so the edge rows copied at its start are current.  As in k_gs_sweep the region
-// carries a halo of H = 3 NSW points: points next to the region's edge are updated with missing
-// neighbours taken as 0 (columns) or skipped (rows outside the shrinking window), and the error
-// this makes travels one point per colour step, so after the 3 NSW steps the interior (the tile)
-// is exactly what sequential colour-by-colour sweeps give, with the same update expression as
-// k_gs_sweep: bitwise the same results.  With PROL the coarse values under the region are staged
-// in shared memory once and the prolongated correction x + P xc is formed from there.
-// ---------------------------------------------------------------------------------------
-
-// floor(v / 2) for any sign
-__device__ __forceinline__ int floor_half(int v) { return v >= 0 ? (v >> 1) : -((-v + 1) >> 1); }
-
-// One colour step on a warp's R rows.  P is the lane element of the active colour in the warp's
-// first row (element m(r) = (P - r) mod 3 in row r).  below / above: the edge rows of the warps
-// underneath and on top (96 values each, zeros past the region).  Only the rows whose bit is set
-// in `rows` are updated (the shrinking window, inside the grid), and in them the points whose
-// column is in the grid (ok_lo[m]) or, on the L-shape in rows at y >= 1/2 (bit set in `qrows`),
-// also left of x = 1/2 (ok_hi[m]).
-template <typename T, int R, bool DIAG, bool LSH, int P>
-__device__ __forceinline__ void reg_step(T (&x)[R][3], const T (&bb)[R][3], const T* __restrict__ below,
-                                         const T* __restrict__ above, int lane, unsigned rows, unsigned qrows, T axs,
-                                         T ays, T dgs, const bool (&ok_lo)[3], const bool (&ok_hi)[3]) {
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    constexpr int kR1 = R - 1;
-    const int m = ((P - (r % 3)) + 3) % 3;  // a constant once the loop is unrolled
-    const int rs = r > 0 ? r - 1 : 0;      // row below inside the warp (valid when r > 0)
-    const int rn = r < kR1 ? r + 1 : kR1;  // row above inside the warp (valid when r < R - 1)
-    if (!(rows & (1u << r))) continue;     // warp-uniform
-    const int cidx = 3 * lane + m;         // region column of the active point
-    // the shuffles run on every lane (the branches are uniform: m is a constant)
-    const T west = (m == 0) ? shfl_up(x[r][2], 1) : x[r][(m + 2) % 3];
-    const T east = (m == 2) ? shfl_down(x[r][0], 1) : x[r][(m + 1) % 3];
-    const T south = (r > 0) ? x[rs][m] : below[cidx];
-    const T north = (r < kR1) ? x[rn][m] : above[cidx];
-    T v = bb[r][m] - axs * (west + east);
-    v -= ays * (south + north);
-    if (DIAG) {
-      // (1,1) and (-1,-1) neighbours
-      const T ne = (r < kR1) ? ((m == 2) ? shfl_down(x[rn][0], 1) : x[rn][(m + 1) % 3])
-                             : above[cidx < 95 ? cidx + 1 : 95];
-      const T sw = (r > 0) ? ((m == 0) ? shfl_up(x[rs][2], 1) : x[rs][(m + 2) % 3]) : below[cidx > 0 ? cidx - 1 : 0];
-      v -= dgs * (ne + sw);
-    }
-    const bool ok = LSH ? ((qrows & (1u << r)) ? ok_hi[m] : ok_lo[m]) : ok_lo[m];
-    if (ok) x[r][m] = v;
-  }
-}
-
-// The first colour step of a sweep from x = 0: every neighbour is zero, so x = b'.
-template <typename T, int R, bool LSH, int P>
-__device__ __forceinline__ void reg_step_first(T (&x)[R][3], const T (&bb)[R][3], unsigned rows, unsigned qrows,
-                                               const bool (&ok_lo)[3], const bool (&ok_hi)[3]) {
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int m = ((P - (r % 3)) + 3) % 3;
-    if (!(rows & (1u << r))) continue;
-    const bool ok = LSH ? ((qrows & (1u << r)) ? ok_hi[m] : ok_lo[m]) : ok_lo[m];
-    if (ok) x[r][m] = bb[r][m];
-  }
-}
-
-// bits lo .. hi - 1 of a 32-bit mask (empty when hi <= lo)
-__device__ __forceinline__ unsigned bit_range(int lo, int hi) {
-  lo = lo < 0 ? 0 : lo;
-  hi = hi > 31 ? 31 : hi;
-  return hi <= lo ? 0u : (((1u << hi) - 1u) & ~((1u << lo) - 1u));
-}
-
-
-template <typename T, typename G, int NSW, int R, int NWARP, bool DIAG, bool PROL, bool LSH>
-__global__ void __launch_bounds__(32 * NWARP) k_gs_reg(G* __restrict__ x_out, const G* __restrict__ x_in,
-                                                       const G* __restrict__ b, const G* __restrict__ xc, int n,
-                                                       const Coef<T>* __restrict__ coef, int coef_class, int J,
-                                                       int K, int level, int reverse, int zero_init) {
-  constexpr int H = 3 * NSW;
-  constexpr int RH = NWARP * R;  // region rows
-  constexpr int TX = kWR - 2 * H, TY = RH - 2 * H;
-  constexpr int CW = kWR / 2 + 2, CH = RH / 2 + 2;  // coarse values under the region (PROL)
-  static_assert(R < 32, "row masks hold 31 rows");
-  __shared__ T edge[2][NWARP][2][kWR];               // [step parity][warp][bottom row, top row]
-  __shared__ T zrow[kWR];                            // zeros past the region's first and last rows
-  __shared__ T ct[PROL ? CH * CW : 1];
-
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int slice = blockIdx.z;
-  const int64_t off = (int64_t)slice * n * n;
-  const int gx0 = blockIdx.x * TX - H, gy0 = blockIdx.y * TY - H;
-  const int ry0 = warp * R;       // first region row of the warp
-  const int gyw = gy0 + ry0;      // its grid row
-  const int cb = gx0 + 3 * lane;  // grid column of the lane's element 0
-  const int q = (n - 1) >> 1;     // L-shape: index of x = 1/2
-  const Coef<T> cf = slice_coef(coef, coef_class, slice, J, K, level);
-  // ok_lo: column in the grid; ok_hi: also left of x = 1/2 (L-shape rows at y >= 1/2)
-  bool ok_lo[3], ok_hi[3];
-#pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    ok_lo[e] = cb + e >= 0 && cb + e < n;
-    ok_hi[e] = ok_lo[e] && !(LSH && cb + e >= q);
-  }
-  // the warp's rows in the grid, and (L-shape) those at y >= 1/2
-  const unsigned grid_rows = bit_range(-gyw, n - gyw);
-  const unsigned qrows = LSH ? bit_range(q - gyw, R) : 0u;
-  for (int i = threadIdx.x; i < kWR; i += blockDim.x) zrow[i] = T(0);
-
-  const int nc = (n - 1) / 2;
-  const int Ib = floor_half(gx0 + 1), Jb = floor_half(gy0 + 1);  // coarse indices at ct[0]
-  if (PROL) {
-    const G* xcs = xc + (int64_t)slice * nc * nc;
-    for (int idx = threadIdx.x; idx < CH * CW; idx += blockDim.x) {
-      const int jj = idx / CW, ii = idx - jj * CW;
-      const int I = Ib + ii, Jc = Jb + jj;
-      ct[idx] = (I >= 1 && I <= nc && Jc >= 1 && Jc <= nc) ? T(xcs[(int64_t)(Jc - 1) * nc + (I - 1)]) : T(0);
-    }
-    __syncthreads();
-  }
-
-  // load the warp's rows: b, and x (0 from x = 0; + P xc with PROL, whose points of the first
-  // colour step's colour are overwritten unread, so they are not formed)
-  T x[R][3], bb[R][3];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int gy = gyw + r;
-    const bool hi = LSH && (qrows & (1u << r));
-    const bool rowok = (grid_rows >> r) & 1u;
-    const int64_t rbase = off + (int64_t)gy * n + cb;
-    int eskip = ((reverse ? 2 : 0) - 2 - gy - gx0) % 3;
-    eskip += (eskip < 0) ? 3 : 0;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      const bool in = rowok && (hi ? ok_hi[e] : ok_lo[e]);
-      bb[r][e] = in ? T(b[rbase + e]) : T(0);
-      T v = T(0);
-      if (!PROL) {
-        if (in && !zero_init) v = T(x_in[rbase + e]);
-      } else if (e != eskip) {
-        if (in && !zero_init) v = T(x_in[rbase + e]);
-        if (in) {
-          const int i = cb + e + 1, j = gy + 1;  // 1-based grid indices
-          const int I0 = i >> 1, J0 = j >> 1;
-          const int I1 = I0 + (i & 1), J1 = J0 + (j & 1);
-          v += T(0.5) * (ct[(J0 - Jb) * CW + (I0 - Ib)] + ct[(J1 - Jb) * CW + (I1 - Ib)]);
-        }
-      }
-      x[r][e] = v;
-    }
-  }
-
-#pragma unroll 1
-  for (int t = 0; t < 3 * NSW; ++t) {
-    const int colour = reverse ? 2 - t % 3 : t % 3;
-    // publish this warp's first and last rows for the neighbouring warps (double-buffered by step
-    // parity: a warp writing step t + 1's rows has passed step t's barrier, so every warp has
-    // finished reading step t - 1's)
-    T* ed = &edge[t & 1][warp][0][0];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      ed[3 * lane + e] = x[0][e];
-      ed[kWR + 3 * lane + e] = x[R - 1][e];
-    }
-    __syncthreads();
-    const T* below = warp > 0 ? &edge[t & 1][warp - 1][1][0] : zrow;
-    const T* above = warp < NWARP - 1 ? &edge[t & 1][warp + 1][0][0] : zrow;
-    // rows of the shrinking window (region rows t + 1 .. RH - t - 2) that lie in the grid
-    const unsigned rows = grid_rows & bit_range(t + 1 - ry0, RH - t - 1 - ry0);
-    int P = (colour - 2 - gyw - gx0) % 3;  // active element in the warp's first row
-    P += (P < 0) ? 3 : 0;
-    if (!PROL && zero_init && t == 0) {
-      if (P == 0)
-        reg_step_first<T, R, LSH, 0>(x, bb, rows, qrows, ok_lo, ok_hi);
-      else if (P == 1)
-        reg_step_first<T, R, LSH, 1>(x, bb, rows, qrows, ok_lo, ok_hi);
-      else
-        reg_step_first<T, R, LSH, 2>(x, bb, rows, qrows, ok_lo, ok_hi);
-    } else if (P == 0) {
-      reg_step<T, R, DIAG, LSH, 0>(x, bb, below, above, lane, rows, qrows, cf.axs, cf.ays, cf.dgs, ok_lo, ok_hi);
-    } else if (P == 1) {
-      reg_step<T, R, DIAG, LSH, 1>(x, bb, below, above, lane, rows, qrows, cf.axs, cf.ays, cf.dgs, ok_lo, ok_hi);
-    } else {
-      reg_step<T, R, DIAG, LSH, 2>(x, bb, below, above, lane, rows, qrows, cf.axs, cf.ays, cf.dgs, ok_lo, ok_hi);
-    }
-  }
-
-  // store the tile: region rows H .. RH - H - 1, columns H .. 95 - H
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int ry = ry0 + r, gy = gyw + r;
-    if (ry < H || ry >= RH - H || gy >= n) continue;
-    const int64_t rbase = off + (int64_t)gy * n + cb;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      const int rx = 3 * lane + e;
-      if (rx >= H && rx < kWR - H && cb + e < n) x_out[rbase + e] = G(x[r][e]);
-    }
-  }
-}
-
 // b' = b / c on the finest level (the multigrid's scaled right-hand side)
 template <typename T, typename G, typename Tin = T>
 __global__ void k_scale_rhs(G* __restrict__ bs, const Tin* __restrict__ b, int n, const Coef<T>* __restrict__ coef,
@@ -771,20 +558,6 @@ __global__ void k_coarse1(G* __restrict__ x, const G* __restrict__ b, int nslice
 }
 
 
-template <typename T>
-const Coef<T>* coef_table(const st_handle_s* h);
-template <>
-const Coef<double>* coef_table<double>(const st_handle_s* h) {
-  return h->coef;
-}
-template <>
-const Coef<float>* coef_table<float>(const st_handle_s* h) {
-  return h->coef32;
-}
-template <>
-const Coef<df64>* coef_table<df64>(const st_handle_s* h) {
-  return h->coefdf;
-}
 
 // Tile shapes (chosen by measurement on GB300): binary64 is bound by the FP64 pipe, so one sweep
 // per launch keeps the halo recomputation small (3-point halo, 90 x 26 interior; 49 KB of shared
@@ -877,43 +650,11 @@ cudaError_t wave_launch(const st_handle_s* h, int k, int nslices, int cls, G* x_
   return cudaGetLastError();
 }
 
-// Register-tile shapes: 8 warps; binary32 holds 12 rows a warp (region 96 x 96, 78 x 78 tile at
-// three fused sweeps), binary64 6 rows (region 96 x 48, 90 x 42 tile at one sweep a launch).
-template <typename T>
-struct RegShape {
-  static constexpr int R = sizeof(T) == 4 ? 12 : 6, NWARP = 8;
-};
-
-template <typename T, typename G, int NSW, bool DIAG, bool PROL>
-cudaError_t reg_launch(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in, const G* b,
-                       const G* xc, bool reverse, bool zero_init) {
-  constexpr int R = RegShape<T>::R, NW = RegShape<T>::NWARP;
-  constexpr int H = 3 * NSW;
-  const int n = (1 << k) - 1;
-  const int TX = kWR - 2 * H, TY = NW * R - 2 * H;
-  dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, nslices);
-  const bool prof = (k == h->K) && prof_start(h);
-  if (h->domain == 1)
-    k_gs_reg<T, G, NSW, R, NW, DIAG, PROL, true><<<grid, 32 * NW, 0, h->stream>>>(
-        x_out, x_in, b, xc, n, coef_table<T>(h), cls, h->J, h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0);
-  else
-    k_gs_reg<T, G, NSW, R, NW, DIAG, PROL, false><<<grid, 32 * NW, 0, h->stream>>>(
-        x_out, x_in, b, xc, n, coef_table<T>(h), cls, h->J, h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0);
-  count_launch(h);
-  if (prof) {
-    const double pts = (double)n * n * nslices;
-    const double nc = (double)((n - 1) / 2);
-    prof_stop(h, (DIAG ? 1 : 0) + (sizeof(T) == 4 ? 2 : 0), pts * NSW * (DIAG ? 6.0 : 4.0),
-              sizeof(G) * (pts * (zero_init ? 2.0 : 3.0) + (PROL ? nc * nc * nslices : 0.0)));
-  }
-  return cudaGetLastError();
-}
-
 // nsw consecutive sweeps of one colour order from x_in (+ P xc if xc != nullptr) into x_out
 // (x_in == x_out is not allowed)
 // Which Gauss-Seidel kernel a launch uses: the handle's autotuned choice per element type,
 // coupling pattern and level (0: shared-memory tiles, the default; 1: register wavefront;
-// 2: register tiles; double-float has no register tiles and uses the shared-memory tiles).
+// 2 + s: register tiles of block shape s).
 template <typename T>
 int gs_kind(const st_handle_s* h, bool diag, int k) {
   return h->gs_kind[type_slot<T>()][diag ? 1 : 0][k];
@@ -923,13 +664,15 @@ template <typename T, typename G, bool DIAG>
 cudaError_t gs_sweeps(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in, const G* b,
                       const G* xc, bool reverse, bool zero_init, int nsw) {
   constexpr int F = SweepShape<T>::kFusedNSW;
-  if constexpr (!std::is_same<T, df64>::value) {
-    if (gs_kind<T>(h, DIAG, k) == 2) {
+  {
+    const int kind = gs_kind<T>(h, DIAG, k);
+    if (kind >= 2) {  // register tiles, block shape kind - 2
+      const int sh = kind - 2;
       if (F > 1 && nsw == F)
-        return xc ? reg_launch<T, G, F, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
-                  : reg_launch<T, G, F, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
-      return xc ? reg_launch<T, G, 1, DIAG, true>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
-                : reg_launch<T, G, 1, DIAG, false>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+        return xc ? reg_launch<T, G, F, DIAG, true>(h, sh, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
+                  : reg_launch<T, G, F, DIAG, false>(h, sh, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+      return xc ? reg_launch<T, G, 1, DIAG, true>(h, sh, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init)
+                : reg_launch<T, G, 1, DIAG, false>(h, sh, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
     }
   }
   if (gs_kind<T>(h, DIAG, k) == 1) {
@@ -1134,10 +877,11 @@ cudaError_t mg_apply_df(const st_handle_s* h, int nslices, int coef_class, const
 
 template <typename T>
 cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x) {
-  if (h->domain == 2) return mg_apply3<T>(h, nslices, coef_class, b, x);
   if constexpr (std::is_same<T, double>::value) {
-    if (h->mg_df) return mg_apply_df(h, nslices, coef_class, b, x);
+    if (h->mg_df) return h->domain == 2 ? mg_apply3_df(h, nslices, coef_class, b, x)
+                                        : mg_apply_df(h, nslices, coef_class, b, x);
   }
+  if (h->domain == 2) return mg_apply3<T>(h, nslices, coef_class, b, x);
   return mg_run<T, T>(h, nslices, coef_class, b, x);
 }
 
@@ -1150,7 +894,8 @@ cudaError_t mg_apply_bf16(const st_handle_s* h, int nslices, int coef_class, con
 // type, coupling pattern and level.  The wavefront is timed at several segment lengths,
 // ceil(n / q) rows for q = 1 .. 12 segments per strip: fewer segments recompute fewer overlap
 // rows (2 S per segment), more segments fill the GPU's last wave of warps better.  Uses the
-// workspace as scratch.  ms[0..2]: shared-memory tiles, wavefront (best length), register tiles.
+// workspace as scratch.  ms[0..2]: shared-memory tiles, wavefront (best length), register tiles
+// (best block shape).
 template <typename T, bool DIAG>
 cudaError_t autotune_one(st_handle_s* h, int k, float* ms) {
   const int nslices = (int)((DIAG ? 1 : 2) * h->B * h->Nt);
@@ -1180,12 +925,20 @@ cudaError_t autotune_one(st_handle_s* h, int k, float* ms) {
     *out = t;
   };
   float t_tile = 1e30f, t_wave = 1e30f, t_reg = 1e30f;
-  int best_seg = 0, last_seg = -1;
+  int best_seg = 0, last_seg = -1, best_reg = 2;
   kind_sel = 0;
   time_it(&t_tile);
-  if (!std::is_same<T, df64>::value) {
-    kind_sel = 2;
-    time_it(&t_reg);
+  {
+    // register tiles: every block shape (binary64 and double-float have one)
+    for (int sh = 0; sh < (sizeof(T) == 4 ? kRegShapes : 1) && err == cudaSuccess; ++sh) {
+      kind_sel = (unsigned char)(2 + sh);
+      float t;
+      time_it(&t);
+      if (t < t_reg) {
+        t_reg = t;
+        best_reg = 2 + sh;
+      }
+    }
   }
   kind_sel = 1;
   for (int q = 1; q <= 12 && err == cudaSuccess; ++q) {
@@ -1202,11 +955,11 @@ cudaError_t autotune_one(st_handle_s* h, int k, float* ms) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  kind_sel = (t_wave < t_tile && t_wave < t_reg) ? 1 : (t_reg < t_tile ? 2 : 0);
+  kind_sel = (t_wave < t_tile && t_wave < t_reg) ? 1 : (t_reg < t_tile ? best_reg : 0);
   seg_sel = (unsigned short)best_seg;
   ms[0] = t_tile;
   ms[1] = t_wave;
-  ms[2] = std::is_same<T, df64>::value ? 0.f : t_reg;
+  ms[2] = t_reg;
   return err;
 }
 

@@ -13,7 +13,8 @@
 // 6 (K_x) or 16 (K_l) FP64 instructions per point, well above the machine balance, so reading
 // the neighbours through L1/L2 instead of staging tiles costs little.  Restriction is P^T of the
 // nested P1 prolongation (weight 1/2 at the 14 neighbours), the coarse level 1 has one unknown.
-// The multigrid works in the Jacobi-scaled form of the 2D kernels (right-hand sides b' = b / c).
+// The multigrid works in the Jacobi-scaled form of the 2D kernels (right-hand sides b' = b / c),
+// in binary64, binary32, or double-float (ST_FP64_DF: mg_apply3_df).
 #include "st_internal.cuh"
 
 namespace st {
@@ -28,6 +29,10 @@ const Coef<double>* coef3<double>(const st_handle_s* h) {
 template <>
 const Coef<float>* coef3<float>(const st_handle_s* h) {
   return h->coef32;
+}
+template <>
+const Coef<df64>* coef3<df64>(const st_handle_s* h) {
+  return h->coefdf;
 }
 
 template <typename T>
@@ -147,15 +152,24 @@ __global__ void __launch_bounds__(256) k_prolong_add3(T* __restrict__ x, const T
   x[(int64_t)slice * N3 + p] += prolong_value3<T>(xc + (int64_t)slice * nc * nc * nc, nc, ix + 1, iy + 1, iz + 1);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_scale_rhs3(T* __restrict__ bs, const T* __restrict__ b, int64_t N3,
+template <typename T, typename Tin = T>
+__global__ void __launch_bounds__(256) k_scale_rhs3(T* __restrict__ bs, const Tin* __restrict__ b, int64_t N3,
                                                     const Coef<T>* __restrict__ coef, int cls, int J, int K) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= N3) return;
   const int slice = blockIdx.y;
   const Coef<T> cf = coef_of(coef, cls, slice, J, K, K);
   const int64_t i = (int64_t)slice * N3 + p;
-  bs[i] = b[i] * cf.inv_c;
+  bs[i] = T(b[i]) * cf.inv_c;
+}
+
+// element i of a buffer of 8-byte double-float values becomes the binary64 value it holds
+__global__ void k_widen_df3(void* buf, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const df64 v = reinterpret_cast<const df64*>(buf)[i];
+    reinterpret_cast<double*>(buf)[i] = double(v);
+  }
 }
 
 template <typename T>
@@ -242,6 +256,30 @@ cudaError_t mg_apply3(const st_handle_s* h, int nslices, int coef_class, const T
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// binary64 in and out, the multigrid in double-float (ST_FP64_DF): the iterate lives in x's memory
+// (8 bytes a value either way) and is widened to binary64 in place at the end
+cudaError_t mg_apply3_df(const st_handle_s* h, int nslices, int coef_class, const double* b, double* x) {
+  using D = df64;
+  const bool diag = coef_class != 0 || h->diag0;
+  const int64_t N3 = h->Nx;
+  D* bs = reinterpret_cast<D*>(h->Bs);
+  D* xd = reinterpret_cast<D*>(x);
+  k_scale_rhs3<D, double><<<dim3(blocks_for(N3), nslices), 256, 0, h->stream>>>(bs, b, N3, coef3<D>(h), coef_class,
+                                                                              h->J, h->K);
+  count_launch(h);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (h->cfg.n_vcycles == 0) return cudaMemsetAsync(x, 0, sizeof(double) * N3 * nslices, h->stream);
+  for (int c = 0; c < h->cfg.n_vcycles; ++c) {
+    e = diag ? vcycle3<D, true>(h, h->K, nslices, coef_class, xd, bs, c == 0)
+             : vcycle3<D, false>(h, h->K, nslices, coef_class, xd, bs, c == 0);
+    if (e != cudaSuccess) return e;
+  }
+  k_widen_df3<<<(unsigned)((N3 * nslices + 255) / 256), 256, 0, h->stream>>>(x, N3 * nslices);
+  count_launch(h);
+  return cudaGetLastError();
 }
 
 template cudaError_t mg_apply3<double>(const st_handle_s*, int, int, const double*, double*);

@@ -285,145 +285,6 @@ __global__ void k_wanal(const T* __restrict__ Xf, T* C, T* D, int64_t Nx, int j,
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// All J lifting stages in one pass (Eq. 3.1): a block holds the whole time axis of TW spatial
-// columns of one problem in shared memory (row pitch TW + 1 against bank conflicts), reads it
-// once, runs the stages there and writes it once.  Each stage computes the new values from the
-// old ones exactly as k_wsynth / k_wanal do (same expressions, bitwise the same results): the
-// outputs that overwrite values other outputs still read go to a scratch row block first.
-// The analysis can form its input on the fly as the S epilogue Z = M X1 + A X2 (+ M U_0 on row
-// 0), so that Z never goes to memory.
-// ---------------------------------------------------------------------------------------
-// the stage scale s_j = 2^((j+1)/2), rounded from binary64 as the stage-by-stage launchers do
-// (sqrt is correctly rounded on host and device alike)
-template <typename T>
-__device__ __forceinline__ T lift_scale(int j) {
-  return (T)sqrt(ldexp(1.0, j + 1));
-}
-
-template <typename T, int TW>
-__global__ void __launch_bounds__(256) k_wsynth_tile(const T* __restrict__ w, T* __restrict__ u, int64_t Nx,
-                                                     int J) {
-  constexpr int PW = TW + 1;
-  extern __shared__ __align__(16) unsigned char lift_smem[];
-  T* col = reinterpret_cast<T*>(lift_smem);
-  const int Nt = (1 << J) + 1;
-  T* tmp = col + (size_t)Nt * PW;
-  const int64_t p0 = (int64_t)blockIdx.x * TW;
-  const int64_t off = (int64_t)blockIdx.y * Nt * Nx;
-  const int ncol = (int)((Nx - p0) < TW ? (Nx - p0) : TW);
-  for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
-    const int i = idx / TW, c = idx - i * TW;
-    col[i * PW + c] = c < ncol ? w[off + (int64_t)i * Nx + p0 + c] : T(0);
-  }
-  __syncthreads();
-  for (int j = 0; j < J; ++j) {
-    const int nw = 1 << j;
-    const int sf = 1 << (J - j - 1);  // fine stride in rows
-    const T s = lift_scale<T>(j);
-    // odd fine nodes 2k+1 (into scratch): 1/2 (c_k + c_k+1) + s d_k
-    for (int idx = threadIdx.x; idx < nw * TW; idx += blockDim.x) {
-      const int k = idx / TW, c = idx - k * TW;
-      const T ck = col[(2 * k) * sf * PW + c], ck1 = col[(2 * k + 2) * sf * PW + c];
-      const T dk = col[(2 * k + 1) * sf * PW + c];
-      tmp[k * PW + c] = T(0.5) * (ck + ck1) + s * dk;
-    }
-    __syncthreads();
-    // even fine nodes 2k (in place; they read only their own coarse value and the details)
-    for (int idx = threadIdx.x; idx < (nw + 1) * TW; idx += blockDim.x) {
-      const int k = idx / TW, c = idx - k * TW;
-      const T ck = col[(2 * k) * sf * PW + c];
-      const T dk = k < nw ? col[(2 * k + 1) * sf * PW + c] : T(0);
-      const T dkm = k > 0 ? col[(2 * k - 1) * sf * PW + c] : T(0);
-      const T aL = (k == 0) ? T(1) : T(0.5);   // psi_k's weight at fine node 2k
-      const T aR = (k == nw) ? T(1) : T(0.5);  // psi_{k-1}'s weight at fine node 2k
-      col[(2 * k) * sf * PW + c] = ck - s * (aR * dkm + aL * dk);
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nw * TW; idx += blockDim.x) {
-      const int k = idx / TW, c = idx - k * TW;
-      col[(2 * k + 1) * sf * PW + c] = tmp[k * PW + c];
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
-    const int i = idx / TW, c = idx - i * TW;
-    if (c < ncol) u[off + (int64_t)i * Nx + p0 + c] = col[i * PW + c];
-  }
-}
-
-// w = W^T u in one pass; with EPI the input row i is formed as the S epilogue from X1 and X2
-// (row i of each; plus M row0 on row 0 when row0 is not null), the k_epilogue arithmetic.
-template <typename T, int TW, int DIM, bool EPI>
-__global__ void __launch_bounds__(256) k_wanal_tile(const T* __restrict__ u, const T* __restrict__ X1,
-                                                    const T* __restrict__ X2, const T* __restrict__ row0,
-                                                    int64_t row0_stride, T* __restrict__ w, int64_t Nx, int J,
-                                                    int n, Stencil7<T> sm, Stencil7<T> sa, int lshape) {
-  constexpr int PW = TW + 1;
-  extern __shared__ __align__(16) unsigned char lift_smem[];
-  T* col = reinterpret_cast<T*>(lift_smem);
-  const int Nt = (1 << J) + 1;
-  T* tmp = col + (size_t)Nt * PW;
-  const int64_t p0 = (int64_t)blockIdx.x * TW;
-  const int64_t off = (int64_t)blockIdx.y * Nt * Nx;
-  const int ncol = (int)((Nx - p0) < TW ? (Nx - p0) : TW);
-  for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
-    const int i = idx / TW, c = idx - i * TW;
-    T v = T(0);
-    if (c < ncol) {
-      const int64_t p = p0 + c;
-      if (!EPI) {
-        v = u[off + (int64_t)i * Nx + p];
-      } else {
-        int ix, iy, iz;
-        coords_of<DIM>(p, n, ix, iy, iz);
-        if (!(DIM == 2 && outside_domain(ix, iy, n, lshape))) {
-          const int64_t ro = off + (int64_t)i * Nx;
-          v = mass_of<T, DIM>(load_nbr<T, DIM>(X1 + ro, p, ix, iy, iz, n), sm) +
-              stiff_of(load_nbr<T, DIM>(X2 + ro, p, ix, iy, iz, n), sa);
-          if (i == 0 && row0 != nullptr)
-            v += mass_of<T, DIM>(load_nbr<T, DIM>(row0 + blockIdx.y * row0_stride, p, ix, iy, iz, n), sm);
-        }
-      }
-    }
-    col[i * PW + c] = v;
-  }
-  __syncthreads();
-  for (int j = J - 1; j >= 0; --j) {
-    const int nw = 1 << j;
-    const int sf = 1 << (J - j - 1);
-    const T s = lift_scale<T>(j);
-    // details d_k (into scratch): s (x_2k+1 - aL x_2k - aR x_2k+2)
-    for (int idx = threadIdx.x; idx < nw * TW; idx += blockDim.x) {
-      const int k = idx / TW, c = idx - k * TW;
-      const T x0 = col[(2 * k) * sf * PW + c], xp = col[(2 * k + 1) * sf * PW + c];
-      const T x2 = col[(2 * k + 2) * sf * PW + c];
-      const T aL = (k == 0) ? T(1) : T(0.5);
-      const T aR = (k == nw - 1) ? T(1) : T(0.5);
-      tmp[k * PW + c] = s * (xp - aL * x0 - aR * x2);
-    }
-    __syncthreads();
-    // coarse values c_k (in place): x_2k + 1/2 (x_2k-1 + x_2k+1)
-    for (int idx = threadIdx.x; idx < (nw + 1) * TW; idx += blockDim.x) {
-      const int k = idx / TW, c = idx - k * TW;
-      const T x0 = col[(2 * k) * sf * PW + c];
-      const T xm = k > 0 ? col[(2 * k - 1) * sf * PW + c] : T(0);
-      const T xp = k < nw ? col[(2 * k + 1) * sf * PW + c] : T(0);
-      col[(2 * k) * sf * PW + c] = x0 + T(0.5) * (xm + xp);
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nw * TW; idx += blockDim.x) {
-      const int k = idx / TW, c = idx - k * TW;
-      col[(2 * k + 1) * sf * PW + c] = tmp[k * PW + c];
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < Nt * TW; idx += blockDim.x) {
-    const int i = idx / TW, c = idx - i * TW;
-    if (c < ncol) w[off + (int64_t)i * Nx + p0 + c] = col[i * PW + c];
-  }
-}
-
 // A_x and M_x on the finest level of the handle, in element type T (the cube: Kuhn tetrahedra)
 template <typename T>
 Stencil7<T> fine_A(const st_handle_s* h) {
@@ -537,36 +398,12 @@ cudaError_t launch_epilogue_rows(const st_handle_s* h, int row0, int nrows, cons
   return cudaGetLastError();
 }
 
-// One-pass lifting: TW columns per block (8 binary64 values = 64 bytes a row, 16 binary32), the
-// time axis and a half-height scratch in shared memory; used while that fits in 110 KB (two
-// blocks per SM), i.e. up to J = 10; longer time axes take the stage-by-stage kernels.
-template <typename T>
-constexpr int lift_tw() {
-  return sizeof(T) == 8 ? 8 : 16;
-}
-template <typename T>
-size_t lift_smem(int J) {
-  const size_t Nt = ((size_t)1 << J) + 1;
-  return (Nt + (Nt - 1) / 2) * (lift_tw<T>() + 1) * sizeof(T);
-}
-template <typename T>
-bool lift_one_pass(int J) {
-  return lift_smem<T>(J) <= 110 * 1024;
-}
-
 // u = W w.  Stage j reads c_j from the previous stage's output (stage 0: from w) and d_j from
 // w, and writes level j+1 into a buffer that differs from the one it reads; the last stage
-// writes u.  Scratch buffers V1/V2 alternate.  Short time axes: all stages in one pass.
+// writes u.  Scratch buffers V1/V2 alternate.
 template <typename T>
 cudaError_t wavelet_synth_n(const st_handle_s* h, int nb, int64_t Nx, const T* w, T* u) {
   const int J = h->J;
-  if (lift_one_pass<T>(J)) {
-    constexpr int TW = lift_tw<T>();
-    dim3 grid((unsigned)((Nx + TW - 1) / TW), nb);
-    k_wsynth_tile<T, TW><<<grid, 256, lift_smem<T>(J), h->stream>>>(w, u, Nx, J);
-    count_launch(h);
-    return cudaGetLastError();
-  }
   const unsigned gx = (unsigned)((Nx + 255) / 256);
   T* V1 = reinterpret_cast<T*>(h->V1);
   T* V2 = reinterpret_cast<T*>(h->V2);
@@ -588,14 +425,6 @@ cudaError_t wavelet_synth_n(const st_handle_s* h, int nb, int64_t Nx, const T* w
 template <typename T>
 cudaError_t wavelet_anal_n(const st_handle_s* h, int nb, int64_t Nx, const T* u, T* w) {
   const int J = h->J;
-  if (lift_one_pass<T>(J)) {
-    constexpr int TW = lift_tw<T>();
-    dim3 grid((unsigned)((Nx + TW - 1) / TW), nb);
-    k_wanal_tile<T, TW, 2, false><<<grid, 256, lift_smem<T>(J), h->stream>>>(
-        u, nullptr, nullptr, nullptr, 0, w, Nx, J, 0, Stencil7<T>{}, Stencil7<T>{}, 0);
-    count_launch(h);
-    return cudaGetLastError();
-  }
   const unsigned gx = (unsigned)((Nx + 255) / 256);
   T* V1 = reinterpret_cast<T*>(h->V1);
   T* V2 = reinterpret_cast<T*>(h->V2);
@@ -622,42 +451,6 @@ cudaError_t wavelet_anal(const st_handle_s* h, int nb, const T* u, T* w) {
   return wavelet_anal_n<T>(h, nb, h->Nx, u, w);
 }
 
-// q = W^T Z with Z = M X1 + A X2 + e_0 (x) M row0 formed on the fly (the S epilogue fused into a
-// one-pass analysis), for nb problems; cudaErrorNotSupported when the time axis is too long for
-// the one-pass kernel (the caller then runs launch_epilogue and wavelet_anal).
-template <typename T>
-cudaError_t launch_epilogue_anal(const st_handle_s* h, int nb, const T* X, const T* row0, int64_t row0_stride, T* q) {
-  const int J = h->J;
-  if (!lift_one_pass<T>(J)) return cudaErrorNotSupported;
-  constexpr int TW = lift_tw<T>();
-  const int64_t Nx = h->Nx;
-  dim3 grid((unsigned)((Nx + TW - 1) / TW), nb);
-  const T* X2 = X + nb * h->Nt * Nx;
-  if (h->domain == 2)
-    k_wanal_tile<T, TW, 3, true><<<grid, 256, lift_smem<T>(J), h->stream>>>(
-        nullptr, X, X2, row0, row0_stride, q, Nx, J, h->n, fine_M<T>(h), fine_A<T>(h), 0);
-  else
-    k_wanal_tile<T, TW, 2, true><<<grid, 256, lift_smem<T>(J), h->stream>>>(
-        nullptr, X, X2, row0, row0_stride, q, Nx, J, h->n, fine_M<T>(h), fine_A<T>(h), h->domain);
-  count_launch(h);
-  return cudaGetLastError();
-}
-
-// dynamic shared memory above 48 KB for the one-pass lifting kernels (once per device)
-cudaError_t lift_set_attributes() {
-  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  const int bd = (int)lift_smem<double>(10), bf = (int)lift_smem<float>(10);
-  cudaError_t e = cudaFuncSetAttribute(k_wsynth_tile<double, lift_tw<double>()>, attr, bd);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wsynth_tile<float, lift_tw<float>()>, attr, bf);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wanal_tile<double, lift_tw<double>(), 2, false>, attr, bd);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wanal_tile<float, lift_tw<float>(), 2, false>, attr, bf);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wanal_tile<double, lift_tw<double>(), 2, true>, attr, bd);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wanal_tile<float, lift_tw<float>(), 2, true>, attr, bf);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wanal_tile<double, lift_tw<double>(), 3, true>, attr, bd);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wanal_tile<float, lift_tw<float>(), 3, true>, attr, bf);
-  return e;
-}
-
 // the transforms of an N_t x ncols block of columns (a time-sharded rank's share after a
 // rows-to-columns transpose); ncols <= N_x
 cudaError_t wavelet_cols(const st_handle_s* h, int synth, int64_t ncols, const double* in, double* out) {
@@ -669,8 +462,7 @@ cudaError_t wavelet_cols(const st_handle_s* h, int synth, int64_t ncols, const d
   template cudaError_t launch_epilogue<T>(const st_handle_s*, int, const T*, const T*, int64_t, T*); \
   template cudaError_t launch_apply_A<T>(const st_handle_s*, int, const T*, T*);                    \
   template cudaError_t wavelet_synth<T>(const st_handle_s*, int, const T*, T*);                     \
-  template cudaError_t wavelet_anal<T>(const st_handle_s*, int, const T*, T*);                     \
-  template cudaError_t launch_epilogue_anal<T>(const st_handle_s*, int, const T*, const T*, int64_t, T*);
+  template cudaError_t wavelet_anal<T>(const st_handle_s*, int, const T*, T*);
 ST_INSTANTIATE(double)
 ST_INSTANTIATE(float)
 #undef ST_INSTANTIATE

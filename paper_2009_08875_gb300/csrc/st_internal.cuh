@@ -138,6 +138,15 @@ struct DevState {
 };
 enum { LOOP_INIT = 0, LOOP_ITER = 1 };
 
+// the coefficients of multigrid slice `slice` on level `level` (slice_class)
+template <typename T>
+__device__ __forceinline__ Coef<T> slice_coef(const Coef<T>* coef, int coef_class, int slice, int J, int K,
+                                              int level) {
+  return coef[slice_class(coef_class, slice, J) * (K + 1) + level];
+}
+
+constexpr int kWR = 96;  // Gauss-Seidel region width = 32 lanes x 3 columns
+
 struct MGLevels {
   int K;                 // finest level
   int kmin;              // coarsest level (exact solve)
@@ -237,6 +246,31 @@ struct st_handle_s {
 
 namespace st {
 
+// the handle's multigrid coefficient table in compute type T
+template <typename T>
+inline const Coef<T>* coef_table(const st_handle_s* h);
+template <>
+inline const Coef<double>* coef_table<double>(const st_handle_s* h) {
+  return h->coef;
+}
+template <>
+inline const Coef<float>* coef_table<float>(const st_handle_s* h) {
+  return h->coef32;
+}
+template <>
+inline const Coef<df64>* coef_table<df64>(const st_handle_s* h) {
+  return h->coefdf;
+}
+
+// Gauss-Seidel sweeps in register tiles (k_gs_reg.cu): nsw = NSW consecutive sweeps of one colour
+// order from x_in (+ P xc if xc != nullptr) into x_out, block shape `shape` (0: 12 rows x 8 warps
+// in binary32, 6 rows x 8 warps in binary64 and double-float; 1: 8 rows x 12 warps; 2: 6 rows x
+// 16 warps; binary64 and double-float have shape 0 only)
+template <typename T, typename G, int NSW, bool DIAG, bool PROL>
+cudaError_t reg_launch(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out, const G* x_in,
+                       const G* b, const G* xc, bool reverse, bool zero_init);
+constexpr int kRegShapes = 3;
+
 // launch accounting: every kernel launch site calls count_launch
 inline void count_launch(const st_handle_s* h, int n = 1) { h->launches += n; }
 // event pair around one profiled launch (no-op unless profiling); returns false if out of events
@@ -261,9 +295,10 @@ cudaError_t launch_make_coef_df(Coef<df64>* coef, int K, int J, double alpha, Ph
 // coef_class < 0: per-slice class 1 + level(slice) (K_X); else a fixed class.
 template <typename T>
 cudaError_t mg_apply(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x);
-// the unit cube's multigrid (domain 2)
+// the unit cube's multigrid (domain 2), and the same in double-float with binary64 in and out
 template <typename T>
 cudaError_t mg_apply3(const st_handle_s* h, int nslices, int coef_class, const T* b, T* x);
+cudaError_t mg_apply3_df(const st_handle_s* h, int nslices, int coef_class, const double* b, double* x);
 // the same in binary32 arithmetic with the multigrid's vectors stored as bfloat16
 cudaError_t mg_apply_bf16(const st_handle_s* h, int nslices, int coef_class, const float* b, float* x);
 // times the Gauss-Seidel kernels per level and records the fastest in h->gs_kind; table[12 k + i]
@@ -287,11 +322,6 @@ cudaError_t launch_timemix(const st_handle_s* h, int nb, int mode, const T* U, T
 // N_x values added to its row 0)
 template <typename T>
 cudaError_t launch_epilogue(const st_handle_s* h, int nb, const T* X, const T* row0, int64_t row0_stride, T* Z);
-// q = W^T Z with Z the epilogue above formed on the fly (one pass); cudaErrorNotSupported when the
-// time axis is too long for the one-pass lifting kernel
-template <typename T>
-cudaError_t launch_epilogue_anal(const st_handle_s* h, int nb, const T* X, const T* row0, int64_t row0_stride, T* q);
-cudaError_t lift_set_attributes();
 // Y = A_x X on nrows slices
 template <typename T>
 cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y);

@@ -141,7 +141,72 @@ class CudaBackend:
 
 
 # ----------------------------------------------------------------------------------------------
-# the sharded solver
+# the compiled sharded solve: st_sharded_solve runs the right-hand side, the PCG (scalars, stop
+# test, updates) and the synthesis; Python only lends it the communicator
+# ----------------------------------------------------------------------------------------------
+class _DeviceArray:
+    """A device buffer of the library seen as a torch tensor (no copy)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _device_tensor(ptr, n):
+    import torch
+    return torch.as_tensor(_DeviceArray(ptr, n), device="cuda")
+
+
+def make_st_comm(comm):
+    """st_comm callbacks over a communicator with exchange(sends, recvs) and allreduce_sum(x);
+    returns (struct, keep-alive objects)."""
+    P = comm.size if comm is not None else 0
+
+    def allreduce(_ctx, v, n):
+        try:
+            for i in range(n):
+                v[i] = comm.allreduce_sum(v[i])
+            return 0
+        except Exception:
+            return 1
+
+    def exchange(_ctx, send, nsend, recv, nrecv):
+        try:
+            sends = {s: _device_tensor(send[s], nsend[s]) for s in range(P) if nsend[s] > 0}
+            recvs = {s: _device_tensor(recv[s], nrecv[s]) for s in range(P) if nrecv[s] > 0}
+            comm.exchange(sends, recvs)
+            return 0
+        except Exception:
+            return 1
+
+    a, e = _lib.ALLREDUCE_FN(allreduce), _lib.EXCHANGE_FN(exchange)
+    return _lib.StComm(None, a, e), (a, e)
+
+
+def sharded_solve(backend, comm, g_rows, u0):
+    """The rank's rows of u for its rows of g and u0 (N_x, read by the rank owning row 0), with
+    the time axis split over the ranks of `comm` (st_sharded_solve; `backend` a CudaBackend whose
+    handle carries the tolerance).  Returns (u rows, iterations, relres)."""
+    import torch
+    check_partition(backend.J, comm.size)
+    lo, hi = row_range(backend.J, comm.size, comm.rank)
+    if tuple(g_rows.shape) != (hi - lo, backend.Nx) or not g_rows.is_cuda or not u0.is_cuda:
+        raise ValueError("g_rows must be this rank's (rows, N_x) CUDA tensor and u0 a CUDA tensor")
+    u = torch.empty_like(g_rows)
+    st_comm, keep = make_st_comm(comm)
+    its, rr = ctypes.c_int(), ctypes.c_double()
+    torch.cuda.synchronize()
+    st = backend.lib.st_sharded_solve(backend.h, ctypes.byref(st_comm), comm.rank, comm.size,
+                                      ctypes.c_void_p(g_rows.data_ptr()), ctypes.c_void_p(u0.data_ptr()),
+                                      ctypes.c_void_p(u.data_ptr()), ctypes.byref(its), ctypes.byref(rr))
+    del keep
+    if st not in (_lib.ST_OK,):
+        _lib.check(st)
+    return u, its.value, rr.value
+
+
+# ----------------------------------------------------------------------------------------------
+# the sharded solver's schedule in Python (the CPU backend of the gloo tests drives it)
 # ----------------------------------------------------------------------------------------------
 class TimeShardedSolver:
     """PCG on S_hat w = f_hat (Sec. 3.4) with the time rows of every vector split over the ranks

@@ -172,10 +172,12 @@ class Solver:
                     for i, nm in enumerate(names)}
                 for k in range(2, self.K + 1) if any(t[12 * k + i] for i in range(12))}
 
+    SMOOTHERS = {"tiles": 0, "wavefront": 1, "registers": 2, "registers_8x12": 3, "registers_6x16": 4}
+
     def set_smoother(self, kind):
-        """Force the Gauss-Seidel kernel on every level: 'tiles', 'wavefront' or 'registers'
-        (st_set_smoother)."""
-        _lib.check(_lib.load().st_set_smoother(self._h, {"tiles": 0, "wavefront": 1, "registers": 2}[kind]))
+        """Force the Gauss-Seidel kernel on every level (st_set_smoother): 'tiles', 'wavefront',
+        'registers' (12 rows x 8 warps in binary32), 'registers_8x12' or 'registers_6x16'."""
+        _lib.check(_lib.load().st_set_smoother(self._h, self.SMOOTHERS[kind]))
 
     def set_wave_rows(self, rows):
         """Rows per segment of the wavefront kernel on every level, 0 for the default (st_set_wave_rows)."""

@@ -60,7 +60,26 @@ def test_cube_operators(K, J, c):
         assert rel(host(y), p.to_inplace(p.rhs_hat(g, u0))) < TOL_OP
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8), ("mixed_precond", 1e-8)])
+@pytest.mark.parametrize("K,J", [(2, 2), (4, 2)])
+def test_cube_double_float_operators(K, J):
+    # ST_FP64_DF: the cube's multigrid in double-float (about 2^-48 per operation); the tolerance
+    # is 32 times the binary64 one (2^5 = 2^-48 / 2^-53), as for the square
+    p = schur.Problem(K, J, CUBE)
+    with Solver(K, J, domain=CUBE, precision="fp64_df") as s:
+        b = inputs.random_state(2 * p.Nt, p.Nx, 94)
+        x = torch.empty((2 * p.Nt, p.Nx), dtype=torch.float64, device="cuda")
+        s.apply_Kx(dev(b), x)
+        assert rel(host(x), p.Kx.apply(b.T).T) < 32 * TOL_OP
+        w = inputs.random_state(p.Nt, p.Nx, 95)
+        y = torch.empty(s.shape, dtype=torch.float64, device="cuda")
+        s.apply_KX(dev(w), y)
+        assert rel(host(y), p.to_inplace(p.apply_KX(p.from_inplace(w)))) < 32 * TOL_OP
+        s.apply_S(dev(w), y)
+        assert rel(host(y), p.to_inplace(p.apply_Shat(p.from_inplace(w)))) < 32 * TOL_OP
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp64_df", 1e-10), ("mixed", 1e-8),
+                                           ("mixed_precond", 1e-8)])
 def test_cube_solve(precision, tol):
     K, J = 3, 3
     p = schur.Problem(K, J, CUBE)

@@ -92,3 +92,26 @@ def test_autotune_keeps_solution_bitwise():
         u2 = torch.zeros_like(u1)
         s.solve_host(torch.from_numpy(g).pin_memory(), torch.from_numpy(u0).pin_memory(), u2)
     assert torch.equal(u1, u2)
+
+
+@pytest.mark.parametrize("K,J,domain", [(7, 2, 0), (6, 3, 1)])
+def test_double_float_smoothers_bitwise_equal(K, J, domain):
+    # the three Gauss-Seidel kernels perform the same double-float sweeps
+    with Solver(K, J, domain=domain, precision="fp64_df") as s:
+        rng = np.random.default_rng(K + J)
+        x = rng.standard_normal(s.shape)
+        if domain == 1:
+            x = x * inputs.grid_mask(K, 1).reshape(-1)
+        x = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        outs = {}
+        for kind in ("tiles", "registers", "wavefront"):
+            s.set_smoother(kind)
+            y = torch.empty_like(x)
+            s.apply_KX(x, y)
+            z = torch.empty_like(x)
+            s.apply_S(x, z)
+            torch.cuda.synchronize()
+            outs[kind] = (y, z)
+        for kind in ("registers", "wavefront"):
+            assert torch.equal(outs["tiles"][0], outs[kind][0]), kind
+            assert torch.equal(outs["tiles"][1], outs[kind][1]), kind

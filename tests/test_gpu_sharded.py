@@ -109,3 +109,70 @@ def test_row_entry_points_reject_bad_ranges():
         x = torch.zeros(s.shape, dtype=torch.float64, device="cuda")
         p = ctypes.c_void_p(x.data_ptr())
         assert _lib.load().st_rows_KX(s._h, 0, 1, p, p) == _lib.ST_ERR_ARG  # batch handle
+
+
+def run_ranks_compiled(P, K, J, domain, g, u0, tol=1e-10, tol_mode=0):
+    """The same ranks, each running st_sharded_solve (the PCG in the library; Python lends only the
+    exchanges and the sums through st_comm callbacks)."""
+    shared = _Shared(P)
+    out = [None] * P
+    errors = []
+
+    def rank_main(r):
+        try:
+            torch.cuda.set_device(0)
+            be = sharded.CudaBackend(K, J, domain=domain, tol=tol, tol_mode=tol_mode)
+            lo, hi = sharded.row_range(J, P, r)
+            gd = torch.from_numpy(np.ascontiguousarray(g[lo:hi])).cuda()
+            u, its, rel = sharded.sharded_solve(be, ThreadComm(shared, r, P), gd, torch.from_numpy(u0).cuda())
+            torch.cuda.synchronize()
+            out[r] = (lo, hi, u.cpu().numpy(), its)
+            be.close()
+        except BaseException as e:  # report, and release the other ranks
+            errors.append(e)
+            shared.barrier.abort()
+
+    threads = [threading.Thread(target=rank_main, args=(r,)) for r in range(P)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=600)
+    if errors:
+        raise errors[0]
+    return out
+
+
+@pytest.mark.parametrize("P,K,J,domain", [(1, 3, 3, 0), (2, 4, 3, 0), (4, 4, 4, 0), (2, 3, 3, 1), (2, 3, 2, 2)])
+def test_compiled_sharded_solve_matches_oracle(P, K, J, domain):
+    # the oracle's converged solution of the same problem (Sec. 3.4, FP64 target 1e-10); the
+    # compiled ranks take the iterations and steps of the Python-driven schedule on the same kernels
+    from oracle import schur
+    g, u0, _ = inputs.manufactured(K, J, domain)
+    u_or, _, _ = schur.solve(schur.Problem(K, J, domain), g, u0, tol=1e-13)
+    u_or = inputs.to_grid(K, domain, u_or)
+    gg, uu = inputs.to_grid(K, domain, g), inputs.to_grid(K, domain, u0)
+    # solved to 1e-12 so that the algebraic error stays well below the 1e-10 comparison
+    res = run_ranks_compiled(P, K, J, domain, gg, uu, tol=1e-12)
+    ref = run_ranks(P, K, J, domain, gg, uu, tol=1e-12)
+    covered = 0
+    for (lo, hi, u, its), (lo2, hi2, u2, its2) in zip(res, ref):
+        assert (lo, hi) == (lo2, hi2) and its == its2
+        assert np.abs(u - u_or[lo:hi]).max() <= 1e-10 * np.abs(u_or).max()
+        assert np.abs(u - u2).max() <= 1e-13 * np.abs(u_or).max()
+        covered += hi - lo
+    assert covered == u_or.shape[0]
+
+
+def test_compiled_sharded_solve_rejects_bad_partitions():
+    import ctypes
+    from paper_2009_08875_gb300 import _lib
+    with Solver(3, 2) as s:
+        x = torch.zeros(s.shape, dtype=torch.float64, device="cuda")
+        p = ctypes.c_void_p(x.data_ptr())
+        comm, keep = sharded.make_st_comm(None)
+        its, rr = ctypes.c_int(), ctypes.c_double()
+        lib = _lib.load()
+        for rank, P in ((0, 3), (2, 2), (0, 8)):  # not a power of two; rank out of range; P > 2^J
+            assert lib.st_sharded_solve(s._h, ctypes.byref(comm), rank, P, p, p, p, ctypes.byref(its),
+                                        ctypes.byref(rr)) == _lib.ST_ERR_ARG
+        del keep

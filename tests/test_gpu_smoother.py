@@ -51,10 +51,11 @@ def test_tiles_and_wavefront_bitwise_equal(K, J, domain, B):
         x = torch.from_numpy(np.ascontiguousarray(x)).cuda()
         s.set_smoother("tiles")
         a = run_ops(s, x)
-        s.set_smoother("registers")
-        c = run_ops(s, x)
-        for name in a:
-            assert torch.equal(a[name], c[name]), (name, "registers")
+        for kind in ("registers", "registers_8x12", "registers_6x16"):
+            s.set_smoother(kind)
+            c = run_ops(s, x)
+            for name in a:
+                assert torch.equal(a[name], c[name]), (name, kind)
         s.set_smoother("wavefront")
         # default segments, then one row per segment, a ragged length, and one segment per strip
         for rows in (0, 1, 5, 73, 1000):
@@ -75,16 +76,17 @@ def test_register_tiles_with_unfused_sweeps(K, J, domain, pre, post):
         x = torch.from_numpy(np.ascontiguousarray(x)).cuda()
         s.set_smoother("tiles")
         a = run_ops(s, x)
-        s.set_smoother("registers")
-        c = run_ops(s, x)
-        for name in a:
-            assert torch.equal(a[name], c[name]), name
+        for kind in ("registers", "registers_8x12", "registers_6x16"):
+            s.set_smoother(kind)
+            c = run_ops(s, x)
+            for name in a:
+                assert torch.equal(a[name], c[name]), (name, kind)
 
 
 def test_set_smoother_rejects_unknown_kind():
     from paper_2009_08875_gb300 import _lib
     with Solver(3, 2) as s:
-        assert _lib.load().st_set_smoother(s._h, 3) == 1  # ST_ERR_ARG
+        assert _lib.load().st_set_smoother(s._h, 5) == 1  # ST_ERR_ARG
         assert _lib.load().st_set_smoother(s._h, -1) == 1
         assert _lib.load().st_set_wave_rows(s._h, -1) == 1
         assert _lib.load().st_set_wave_rows(s._h, 65536) == 1
