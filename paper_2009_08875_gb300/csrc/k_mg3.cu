@@ -10,8 +10,9 @@
 // nodes share a colour: the couplings' index sums are +-1, +-2, +-3), pre-sweeps in colour order
 // 0..3, post-sweeps 3..0 (a symmetric V-cycle), in place: one launch per colour, one thread per
 // point of that colour, whose neighbours all have other colours.  The binary64 3D update costs
-// 6 (K_x) or 16 (K_l) FP64 instructions per point, well above the machine balance, so reading
-// the neighbours through L1/L2 instead of staging tiles costs little.  Restriction is P^T of the
+// 6 (K_x) or 14 (K_l) FP64 instructions per point, well above the machine balance, so reading
+// the neighbours through L1/L2 instead of staging tiles costs little (ncu: the K_l colour step
+// keeps the FP64 pipe 84% busy).  Restriction is P^T of the
 // nested P1 prolongation (weight 1/2 at the 14 neighbours), the coarse level 1 has one unknown.
 // The multigrid works in the Jacobi-scaled form of the 2D kernels (right-hand sides b' = b / c),
 // in binary64, binary32, or double-float (ST_FP64_DF: mg_apply3_df).
@@ -191,7 +192,9 @@ cudaError_t colour_sweep(const st_handle_s* h, int k, int nslices, int cls, T* x
   if (prof) {
     // one colour of the sweep is timed; its work is a quarter of the sweep's
     const double pts = (double)n * n * n * nslices / 4.0;
-    prof_stop(h, (DIAG ? 1 : 0) + (sizeof(T) == 4 ? 2 : 0), pts * (DIAG ? 16.0 : 6.0), pts * sizeof(T) * 3.0);
+    // FP64 instructions per point: 5 adds and 1 fma (K_x); 11 adds and 3 fmas with the mass
+    // couplings of K_l (counted by ncu: the add / fma ratio of the launch is 3.67)
+    prof_stop(h, (DIAG ? 1 : 0) + (sizeof(T) == 4 ? 2 : 0), pts * (DIAG ? 14.0 : 6.0), pts * sizeof(T) * 3.0);
   }
   return cudaGetLastError();
 }
