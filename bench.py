@@ -86,7 +86,8 @@ def parse():
     ap.add_argument("--serve-sweep-requests", type=int, default=150,
                     help="requests per point of the offered-load sweep (25/50/90%% of capacity)")
     ap.add_argument("--batch-problems", type=int, default=256)
-    ap.add_argument("--smoother", choices=["auto", "tiles", "wavefront", "registers", "registers_8x12", "registers_6x16"],
+    ap.add_argument("--smoother", choices=["auto", "tiles", "wavefront", "registers", "registers_8x12", "registers_6x16",
+                             "registers_wide", "registers_wide_8x12"],
                     default="auto",
                     help="Gauss-Seidel kernel: autotuned per level (default) or one kernel on every level")
     ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_precond", "mixed_bf16", "fp64_df"], default="fp64",

@@ -1,0 +1,356 @@
+// Gauss-Seidel sweeps of the time-slice-batched binary32 multigrid (k_mg.cu) in wide register
+// tiles with paired arithmetic: the same three-colour sweeps as k_gs_sweep and k_gs_reg, two
+// points of one colour per lane and row updated by one packed binary32 instruction (Blackwell's
+// add / fma on float pairs).
+#include <cuda_bf16.h>
+
+#include "df64.cuh"
+#include "st_internal.cuh"
+
+namespace st {
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// A block of NWARP warps holds a region of 192 columns x NWARP * R rows of one slice: warp w
+// owns the region rows w R .. w R + R - 1, lane l the columns 6 l .. 6 l + 5 of them.  Columns
+// 6 l + e and 6 l + e + 3 have the same colour ((i + j) mod 3), so in every row the two points
+// of the active colour sit in one register pair x[r][m] = (column 6 l + m, column 6 l + m + 3),
+// m = the active element, and every neighbour sum of the update is a pair as well: the update
+// x = b' - (a_x/c)(W + E) - (a_y/c)(S + N) - (d/c)(NE + SW) of the Jacobi-scaled system runs as
+// packed adds and fmas on both points at once.  Horizontal neighbours come from the lane's own
+// pairs or, across a lane boundary, one shuffle per pair; vertical neighbours from the rows above
+// and below in registers or, at the edge of a warp's rows, from the neighbouring warp's edge row
+// (shared memory, double-buffered by step parity, one barrier per colour step).  The scaled
+// right-hand side b' sits in shared memory (read once per point and colour step).
+//
+// Placement: the region lies inside the grid (n >= 192 and n >= NWARP R), clamped against the
+// grid's edges, so no point of it is outside the grid and no update is masked.  On a side where
+// the region ends at the grid's boundary the missing neighbours are the Dirichlet zeros, which
+// is exact; on a side inside the grid the region carries a halo of H = 3 NSW points whose
+// missing neighbours are taken from wherever is convenient (zeros, or the lane's own values);
+// the error this makes travels one point per colour step, so after the 3 NSW steps the points
+// at least H from such a side - the block's tile - are exactly what sequential colour-by-colour
+// sweeps give.  Every point is updated with the same operations in the same order as in the
+// other kernels (fma(-a_x/c, W + E, b'), then fma(-a_y/c, S + N, .), then fma(-d/c, NE + SW, .)),
+// and a packed fma rounds each half once, like its scalar counterpart: bitwise the same sweeps.
+// ---------------------------------------------------------------------------------------
+
+constexpr int kWW = 192;  // region width: 32 lanes x 6 columns
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// One colour step on a warp's R rows.  P is the active element of the warp's first row (row r:
+// m(r) = (P - r) mod 3).  bs: b' of the warp's rows, bs[r * 96 + k * 32 + lane] = the pair k of
+// the lane in row r.  below / above: the edge rows of the warps underneath and on top, in the
+// same pair layout (zeros past the region).  zl / zr: the lane's west / east neighbour across
+// the region's edge is the grid boundary (a zero).
+template <int R, bool DIAG, int P>
+__device__ __forceinline__ void wide_step(float2 (&x)[R][3], const float2* __restrict__ bs,
+                                          const float2* __restrict__ below, const float2* __restrict__ above,
+                                          int lane, bool zl, bool zr, float2 nax, float2 nay, float2 ndg) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    constexpr int kR1 = R - 1;
+    const int m = ((P - (r % 3)) + 3) % 3;  // a constant once the loop is unrolled
+    const int rs = r > 0 ? r - 1 : 0;
+    const int rn = r < kR1 ? r + 1 : kR1;
+    // west and east pairs (columns 6 l + m -+ 1 and 6 l + m + 3 -+ 1)
+    float2 W, E;
+    if (m == 0) {
+      const float t = shfl_up(x[r][2].y, 1);
+      W = make_float2(zl ? 0.f : t, x[r][2].x);
+    } else {
+      W = x[r][(m + 2) % 3];
+    }
+    if (m == 2) {
+      const float t = shfl_down(x[r][0].x, 1);
+      E = make_float2(x[r][0].y, zr ? 0.f : t);
+    } else {
+      E = x[r][(m + 1) % 3];
+    }
+    const float2 S = (r > 0) ? x[rs][m] : below[m * 32 + lane];
+    const float2 N = (r < kR1) ? x[rn][m] : above[m * 32 + lane];
+    float2 v = fma2(nax, add2(W, E), bs[r * 96 + m * 32 + lane]);
+    v = fma2(nay, add2(S, N), v);
+    if (DIAG) {
+      // (1,1) neighbours: the row above shifted east; (-1,-1): the row below shifted west
+      float2 NE, SW;
+      if (r < kR1) {
+        if (m == 2) {
+          const float t = shfl_down(x[rn][0].x, 1);
+          NE = make_float2(x[rn][0].y, zr ? 0.f : t);
+        } else {
+          NE = x[rn][(m + 1) % 3];
+        }
+      } else {
+        if (m == 2) {
+          const float t = above[lane + 1].x;  // lane 31 reads the next pair's slot: unused (zr or halo)
+          NE = make_float2(above[lane].y, zr ? 0.f : t);
+        } else {
+          NE = above[((m + 1) % 3) * 32 + lane];
+        }
+      }
+      if (r > 0) {
+        if (m == 0) {
+          const float t = shfl_up(x[rs][2].y, 1);
+          SW = make_float2(zl ? 0.f : t, x[rs][2].x);
+        } else {
+          SW = x[rs][(m + 2) % 3];
+        }
+      } else {
+        if (m == 0) {
+          const float t = below[64 + lane - 1].y;  // lane 0 reads the previous pair's slot: unused (zl or halo)
+          SW = make_float2(zl ? 0.f : t, below[64 + lane].x);
+        } else {
+          SW = below[((m + 2) % 3) * 32 + lane];
+        }
+      }
+      v = fma2(ndg, add2(NE, SW), v);
+    }
+    x[r][m] = v;
+  }
+}
+
+// The first colour step of a sweep from x = 0: every neighbour is zero, so x = b'.
+template <int R, int P>
+__device__ __forceinline__ void wide_step_first(float2 (&x)[R][3], const float2* __restrict__ bs, int lane) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int m = ((P - (r % 3)) + 3) % 3;
+    x[r][m] = bs[r * 96 + m * 32 + lane];
+  }
+}
+
+// dynamic shared memory of one block: b' (RH rows x 96 pairs), the edge rows (2 parities x NWARP
+// warps x 2 rows x 96 pairs; also the coarse values of the prolongation before the first step),
+// and a zero row of 96 pairs
+template <int R, int NWARP>
+constexpr size_t wide_smem() {
+  return sizeof(float2) * (size_t)(NWARP * R * 96 + 2 * NWARP * 2 * 96 + 96);
+}
+
+template <typename G, int NSW, int R, int NWARP, int MINB, bool DIAG, bool PROL>
+__global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_out, const G* __restrict__ x_in,
+                                                            const G* __restrict__ b, const G* __restrict__ xc,
+                                                            int n, const Coef<float>* __restrict__ coef,
+                                                            int coef_class, int J, int K, int level, int reverse,
+                                                            int zero_init) {
+  constexpr int H = 3 * NSW;
+  constexpr int RH = NWARP * R;  // region rows
+  constexpr int TX = kWW - 2 * H, TY = RH - 2 * H;
+  constexpr int CW = kWW / 2 + 2, CH = RH / 2 + 2;  // coarse values under the region (PROL)
+  static_assert(CW * CH <= 2 * NWARP * 2 * 96 * 2, "coarse values fit in the edge-row space");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* bsh = reinterpret_cast<float2*>(smem_raw);  // [RH][3][32]
+  float2* edge = bsh + RH * 96;                        // [2][NWARP][2][3][32]
+  float2* zrow = edge + 2 * NWARP * 2 * 96;            // [3][32]
+  float* ct = reinterpret_cast<float*>(edge);          // [CH][CW] before the first step
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slice = blockIdx.z;
+  const int64_t off = (int64_t)slice * n * n;
+  // the block's tile and its region, clamped into the grid
+  const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
+  const int x0 = min(max(tx0 - H, 0), n - kWW), y0 = min(max(ty0 - H, 0), n - RH);
+  const int ry0 = warp * R;
+  const int gyw = y0 + ry0;       // grid row of the warp's first row
+  const int cb = x0 + 6 * lane;   // grid column of the lane's element 0
+  const bool zl = lane == 0 && x0 == 0;
+  const bool zr = lane == 31 && x0 + kWW == n;
+  const Coef<float> cf = slice_coef(coef, coef_class, slice, J, K, level);
+  const float2 nax = make_float2(-cf.axs, -cf.axs), nay = make_float2(-cf.ays, -cf.ays);
+  const float2 ndg = make_float2(-cf.dgs, -cf.dgs);
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) zrow[i] = make_float2(0.f, 0.f);
+
+  const int nc = (n - 1) / 2;
+  const int Ib = (x0 + 1) >> 1, Jb = (y0 + 1) >> 1;  // coarse indices at ct[0]
+  if (PROL) {
+    const G* xcs = xc + (int64_t)slice * nc * nc;
+    for (int idx = threadIdx.x; idx < CH * CW; idx += blockDim.x) {
+      const int jj = idx / CW, ii = idx - jj * CW;
+      const int I = Ib + ii, Jc = Jb + jj;
+      ct[idx] = (I >= 1 && I <= nc && Jc >= 1 && Jc <= nc) ? float(xcs[(int64_t)(Jc - 1) * nc + (I - 1)]) : 0.f;
+    }
+    __syncthreads();
+  }
+
+  // load: b' into shared memory, x into registers (0 from x = 0; + P xc with PROL, whose points
+  // of the first colour step's colour are overwritten unread, so they are not formed)
+  float2 x[R][3];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gy = gyw + r;
+    const int64_t rbase = off + (int64_t)gy * n + cb;
+    float bv[6], xv[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      bv[e] = float(b[rbase + e]);
+      xv[e] = zero_init ? 0.f : float(x_in[rbase + e]);
+    }
+    if (PROL) {
+      int eskip = ((reverse ? 2 : 0) - 2 - gy - x0) % 3;
+      eskip += (eskip < 0) ? 3 : 0;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        if (e % 3 == eskip) {
+          xv[e] = 0.f;
+        } else {
+          const int i = cb + e + 1, j = gy + 1;  // 1-based grid indices
+          const int I0 = i >> 1, J0 = j >> 1;
+          const int I1 = I0 + (i & 1), J1 = J0 + (j & 1);
+          xv[e] += 0.5f * (ct[(J0 - Jb) * CW + (I0 - Ib)] + ct[(J1 - Jb) * CW + (I1 - Ib)]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      bsh[(ry0 + r) * 96 + k * 32 + lane] = make_float2(bv[k], bv[k + 3]);
+      x[r][k] = make_float2(xv[k], xv[k + 3]);
+    }
+  }
+  if (PROL) __syncthreads();  // ct (the edge-row space) is read before the first step writes it
+
+  const float2* bw = bsh + ry0 * 96;
+#pragma unroll 1
+  for (int t = 0; t < 3 * NSW; ++t) {
+    const int colour = reverse ? 2 - t % 3 : t % 3;
+    float2* ed = edge + ((t & 1) * NWARP + warp) * 192;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ed[k * 32 + lane] = x[0][k];
+      ed[96 + k * 32 + lane] = x[R - 1][k];
+    }
+    __syncthreads();
+    const float2* below = warp > 0 ? edge + ((t & 1) * NWARP + warp - 1) * 192 + 96 : zrow;
+    const float2* above = warp < NWARP - 1 ? edge + ((t & 1) * NWARP + warp + 1) * 192 : zrow;
+    int P = (colour - 2 - gyw - x0) % 3;  // active element in the warp's first row
+    P += (P < 0) ? 3 : 0;
+    if (!PROL && zero_init && t == 0) {
+      if (P == 0)
+        wide_step_first<R, 0>(x, bw, lane);
+      else if (P == 1)
+        wide_step_first<R, 1>(x, bw, lane);
+      else
+        wide_step_first<R, 2>(x, bw, lane);
+    } else if (P == 0) {
+      wide_step<R, DIAG, 0>(x, bw, below, above, lane, zl, zr, nax, nay, ndg);
+    } else if (P == 1) {
+      wide_step<R, DIAG, 1>(x, bw, below, above, lane, zl, zr, nax, nay, ndg);
+    } else {
+      wide_step<R, DIAG, 2>(x, bw, below, above, lane, zl, zr, nax, nay, ndg);
+    }
+  }
+
+  // store the tile: grid rows ty0 .. ty0 + TY - 1, columns tx0 .. tx0 + TX - 1 (inside the grid)
+  const int ty1 = min(ty0 + TY, n), tx1 = min(tx0 + TX, n);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int gy = gyw + r;
+    if (gy < ty0 || gy >= ty1) continue;
+    const int64_t rbase = off + (int64_t)gy * n + cb;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const int gx = cb + e;
+      const float v = e < 3 ? x[r][e].x : x[r][e - 3].y;
+      if (gx >= tx0 && gx < tx1) x_out[rbase + e] = G(v);
+    }
+  }
+}
+
+// Block shapes (rows per warp, warps, minimum resident blocks per SM)
+template <int SHAPE>
+struct WideShape;
+template <>
+struct WideShape<0> {
+  static constexpr int R = 12, NWARP = 8, MINB = 2;
+};
+template <>
+struct WideShape<1> {
+  static constexpr int R = 8, NWARP = 12, MINB = 1;
+};
+
+template <typename G, int NSW, int SHAPE, bool DIAG, bool PROL>
+cudaError_t wide_launch_shape(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in,
+                              const G* b, const G* xc, bool reverse, bool zero_init) {
+  using S = WideShape<SHAPE>;
+  constexpr int H = 3 * NSW, RH = S::R * S::NWARP;
+  const int n = (1 << k) - 1;
+  const int TX = kWW - 2 * H, TY = RH - 2 * H;
+  dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, nslices);
+  constexpr size_t smem = wide_smem<S::R, S::NWARP>();
+  const bool prof = (k == h->K) && prof_start(h);
+  k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, DIAG, PROL><<<grid, 32 * S::NWARP, smem, h->stream>>>(
+      x_out, x_in, b, xc, n, coef_table<float>(h), cls, h->J, h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0);
+  count_launch(h);
+  if (prof) {
+    const double pts = (double)n * n * nslices;
+    const double nc = (double)((n - 1) / 2);
+    prof_stop(h, (DIAG ? 1 : 0) + 2, pts * NSW * (DIAG ? 6.0 : 4.0),
+              sizeof(G) * (pts * (zero_init ? 2.0 : 3.0) + (PROL ? nc * nc * nslices : 0.0)));
+  }
+  return cudaGetLastError();
+}
+
+template <typename G, int SHAPE>
+cudaError_t wide_attr_shape() {
+  using S = WideShape<SHAPE>;
+  const int smem = (int)wide_smem<S::R, S::NWARP>();
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaSuccess;
+#define ST_WIDE_ATTR(NSW, DIAG, PROL)                                                                         \
+  if (e == cudaSuccess)                                                                                       \
+    e = cudaFuncSetAttribute(k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, DIAG, PROL>, attr, smem);
+  ST_WIDE_ATTR(1, false, false)
+  ST_WIDE_ATTR(1, false, true)
+  ST_WIDE_ATTR(1, true, false)
+  ST_WIDE_ATTR(1, true, true)
+  ST_WIDE_ATTR(3, false, false)
+  ST_WIDE_ATTR(3, false, true)
+  ST_WIDE_ATTR(3, true, false)
+  ST_WIDE_ATTR(3, true, true)
+#undef ST_WIDE_ATTR
+  return e;
+}
+
+}  // namespace
+
+bool wide_fits(const st_handle_s* h, int shape, int k) {
+  const int n = (1 << k) - 1;
+  const int rh = shape == 0 ? WideShape<0>::R * WideShape<0>::NWARP : WideShape<1>::R * WideShape<1>::NWARP;
+  return h->domain == 0 && n >= kWW && n >= rh;
+}
+
+template <typename G, int NSW, bool DIAG, bool PROL>
+cudaError_t wide_launch(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out, const G* x_in,
+                        const G* b, const G* xc, bool reverse, bool zero_init) {
+  if (shape == 1)
+    return wide_launch_shape<G, NSW, 1, DIAG, PROL>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+  return wide_launch_shape<G, NSW, 0, DIAG, PROL>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+}
+
+cudaError_t wide_set_attributes() {
+  cudaError_t e = wide_attr_shape<float, 0>();
+  if (e == cudaSuccess) e = wide_attr_shape<float, 1>();
+  if (e == cudaSuccess) e = wide_attr_shape<__nv_bfloat16, 0>();
+  if (e == cudaSuccess) e = wide_attr_shape<__nv_bfloat16, 1>();
+  return e;
+}
+
+#define ST_WIDE(G, NSW)                                                                                       \
+  template cudaError_t wide_launch<G, NSW, false, false>(const st_handle_s*, int, int, int, int, G*, const G*, \
+                                                         const G*, const G*, bool, bool);                      \
+  template cudaError_t wide_launch<G, NSW, false, true>(const st_handle_s*, int, int, int, int, G*, const G*,  \
+                                                        const G*, const G*, bool, bool);                       \
+  template cudaError_t wide_launch<G, NSW, true, false>(const st_handle_s*, int, int, int, int, G*, const G*,  \
+                                                        const G*, const G*, bool, bool);                       \
+  template cudaError_t wide_launch<G, NSW, true, true>(const st_handle_s*, int, int, int, int, G*, const G*,   \
+                                                       const G*, const G*, bool, bool);
+ST_WIDE(float, 1)
+ST_WIDE(float, 3)
+ST_WIDE(__nv_bfloat16, 1)
+ST_WIDE(__nv_bfloat16, 3)
+#undef ST_WIDE
+
+}  // namespace st

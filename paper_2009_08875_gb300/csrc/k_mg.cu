@@ -805,6 +805,7 @@ cudaError_t mg_set_attributes() {
   if (e == cudaSuccess) e = set_smem_attr<float, __nv_bfloat16, SF::kFusedNSW, SF::kFusedHR>();
   if (e == cudaSuccess) e = set_smem_attr<float, __nv_bfloat16, 1, SF::kSingleHR>();
   if (e == cudaSuccess) e = set_smem_attr<df64, df64, 1, SweepShape<df64>::kSingleHR>();
+  if (e == cudaSuccess) e = wide_set_attributes();
   return e;
 }
 

@@ -1,5 +1,5 @@
-"""The three Gauss-Seidel kernels (shared-memory tiles, register wavefront, register tiles) and
-the autotuner.
+"""The Gauss-Seidel kernels (shared-memory tiles, register wavefront, register tiles, and the
+binary32 wide register regions with paired arithmetic) and the autotuner.
 
 All kernels perform the same three-colour sweeps with the same summation order per point, so
 every operator that runs the multigrid (K_x, K_X, the binary32 S and K_X, the bfloat16-storage
@@ -39,9 +39,14 @@ def run_ops(s, x):
     return out
 
 
-# K = 3 (one tile / strip), K = 6 and K = 8 (several strips and vertical segments, ragged edges)
+REGISTER_KINDS = ("registers", "registers_8x12", "registers_6x16", "registers_wide", "registers_wide_8x12")
+
+
+# K = 3 (one tile / strip), K = 6 and K = 8 (several strips and vertical segments, ragged edges);
+# K = 8 and 9 on the square also run the wide binary32 regions on their finest one or two levels
+# (two and three regions per row, the last clamped against the grid's edge)
 @pytest.mark.parametrize("K,J,domain,B", [(3, 3, 0, 1), (6, 4, 0, 1), (8, 2, 0, 1), (6, 3, 1, 1), (5, 3, 0, 3),
-                                          (7, 2, 1, 2)])
+                                          (7, 2, 1, 2), (9, 1, 0, 1), (8, 1, 0, 2), (8, 2, 1, 1)])
 def test_tiles_and_wavefront_bitwise_equal(K, J, domain, B):
     with Solver(K, J, domain=domain, batch=B) as s:
         rng = np.random.default_rng(K * 100 + J)
@@ -51,7 +56,7 @@ def test_tiles_and_wavefront_bitwise_equal(K, J, domain, B):
         x = torch.from_numpy(np.ascontiguousarray(x)).cuda()
         s.set_smoother("tiles")
         a = run_ops(s, x)
-        for kind in ("registers", "registers_8x12", "registers_6x16"):
+        for kind in REGISTER_KINDS:
             s.set_smoother(kind)
             c = run_ops(s, x)
             for name in a:
@@ -66,7 +71,7 @@ def test_tiles_and_wavefront_bitwise_equal(K, J, domain, B):
 
 
 # sweep counts that are not a multiple of three: binary32 launches of one sweep beside fused ones
-@pytest.mark.parametrize("K,J,domain,pre,post", [(7, 2, 0, 4, 2), (6, 2, 1, 1, 5)])
+@pytest.mark.parametrize("K,J,domain,pre,post", [(7, 2, 0, 4, 2), (6, 2, 1, 1, 5), (8, 1, 0, 4, 2), (9, 1, 0, 1, 5)])
 def test_register_tiles_with_unfused_sweeps(K, J, domain, pre, post):
     with Solver(K, J, domain=domain, n_pre=pre, n_post=post) as s:
         rng = np.random.default_rng(K + 7 * pre)
@@ -76,7 +81,7 @@ def test_register_tiles_with_unfused_sweeps(K, J, domain, pre, post):
         x = torch.from_numpy(np.ascontiguousarray(x)).cuda()
         s.set_smoother("tiles")
         a = run_ops(s, x)
-        for kind in ("registers", "registers_8x12", "registers_6x16"):
+        for kind in REGISTER_KINDS:
             s.set_smoother(kind)
             c = run_ops(s, x)
             for name in a:
@@ -86,15 +91,15 @@ def test_register_tiles_with_unfused_sweeps(K, J, domain, pre, post):
 def test_set_smoother_rejects_unknown_kind():
     from paper_2009_08875_gb300 import _lib
     with Solver(3, 2) as s:
-        assert _lib.load().st_set_smoother(s._h, 5) == 1  # ST_ERR_ARG
+        assert _lib.load().st_set_smoother(s._h, 7) == 1  # ST_ERR_ARG
         assert _lib.load().st_set_smoother(s._h, -1) == 1
         assert _lib.load().st_set_wave_rows(s._h, -1) == 1
         assert _lib.load().st_set_wave_rows(s._h, 65536) == 1
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed_precond"])
-def test_autotune_keeps_solution_bitwise(precision):
-    K, J = 6, 4
+# K = 8: the binary32 candidates include the wide regions on level 8
+@pytest.mark.parametrize("precision,K,J", [("fp64", 6, 4), ("mixed_precond", 6, 4), ("mixed", 8, 3)])
+def test_autotune_keeps_solution_bitwise(precision, K, J):
     g, u0 = inputs.smooth_forcing(K, J, seed=3)
     g = torch.from_numpy(inputs.to_grid(K, 0, g)).pin_memory()
     u0 = torch.from_numpy(inputs.to_grid(K, 0, u0)).pin_memory()
