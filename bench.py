@@ -56,7 +56,8 @@ KERNEL_OF = {"tiles": ("k_gs_sweep", "k_mg.cu"), "wavefront": ("k_gs_wave", "k_m
 
 
 def traffic_for(op, kind):
-    name, fname = KERNEL_OF[kind]
+    # every register-tile kind runs the register tiles (k_gs_reg) in binary64
+    name, fname = KERNEL_OF["registers" if kind.startswith("registers") else kind]
     return NCU_TRAFFIC.get(kernel_source_hash(name, fname), {}).get((op, kind))
 
 

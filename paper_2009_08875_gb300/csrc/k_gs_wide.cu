@@ -4,6 +4,8 @@
 // add / fma on float pairs).
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "df64.cuh"
 #include "st_internal.cuh"
 
@@ -37,6 +39,9 @@ namespace {
 // ---------------------------------------------------------------------------------------
 
 constexpr int kWW = 192;  // region width: 32 lanes x 6 columns
+#ifndef ST_WIDE_ASYNC_B0
+#define ST_WIDE_ASYNC_B0 0
+#endif
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -113,6 +118,34 @@ __device__ __forceinline__ void wide_step(float2 (&x)[R][3], const float2* __res
   }
 }
 
+// x += P xc on a warp's R rows (the coarse-grid correction of the V-cycle; nested P1: the average
+// of the coarse values at the two ends of the coarse edge whose midpoint the fine node is, the
+// same node twice at even-even nodes).  cw: the coarse values staged row by row (CW a row) from
+// the coarse node under the lane's element 0 of the warp's first row.  With PA = (x0 + 1) mod 2
+// and PY = (y0 + 1) mod 2 the coarse offsets of every element are constants: element e of row r
+// reads coarse rows (r + PY) / 2 and that + (r + PY) mod 2, columns (PA + e) / 2 and that +
+// (PA + e) mod 2.  At the points of the first colour step's colour the sum is formed but never
+// read (that step overwrites them reading only the other colours).
+template <int R, int CW, int PA, int PY>
+__device__ __forceinline__ void wide_add_prol(float2 (&x)[R][3], const float* __restrict__ cw) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int j0 = (r + PY) >> 1, j1 = j0 + ((r + PY) & 1);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const int i0 = (PA + e) >> 1, i1 = i0 + ((PA + e) & 1);
+      const float c = 0.5f * (cw[j0 * CW + i0] + cw[j1 * CW + i1]);
+      if (e < 3)
+        x[r][e].x += c;
+      else
+        x[r][e - 3].y += c;
+    }
+    // keep the shared loads of later rows from being hoisted here (registers: x already holds the
+    // whole region)
+    asm volatile("" ::: "memory");
+  }
+}
+
 // The first colour step of a sweep from x = 0: every neighbour is zero, so x = b'.
 template <int R, int P>
 __device__ __forceinline__ void wide_step_first(float2 (&x)[R][3], const float2* __restrict__ bs, int lane) {
@@ -131,12 +164,13 @@ constexpr size_t wide_smem() {
   return sizeof(float2) * (size_t)(NWARP * R * 96 + 2 * NWARP * 2 * 96 + 96);
 }
 
-template <typename G, int NSW, int R, int NWARP, int MINB, bool DIAG, bool PROL>
-__global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_out, const G* __restrict__ x_in,
-                                                            const G* __restrict__ b, const G* __restrict__ xc,
-                                                            int n, const Coef<float>* __restrict__ coef,
-                                                            int coef_class, int J, int K, int level, int reverse,
-                                                            int zero_init) {
+// The kernel body for one parity class of block regions: PA = (x0 + 1) mod 2, PY = (y0 + 1) mod 2
+// fix the coarse offsets of the prolongation (PROL); every class is its own code path, so the
+// registers of one do not add to another's.
+template <typename G, int NSW, int R, int NWARP, bool ASYNCB, bool DIAG, bool PROL, int PA, int PY>
+__device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __restrict__ x_in, const G* __restrict__ b,
+                                          const G* __restrict__ xc, int n, const Coef<float>* __restrict__ coef,
+                                          int coef_class, int J, int K, int level, int reverse, int zero_init) {
   constexpr int H = 3 * NSW;
   constexpr int RH = NWARP * R;  // region rows
   constexpr int TX = kWW - 2 * H, TY = RH - 2 * H;
@@ -164,53 +198,50 @@ __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_
   const float2 ndg = make_float2(-cf.dgs, -cf.dgs);
   for (int i = threadIdx.x; i < 96; i += blockDim.x) zrow[i] = make_float2(0.f, 0.f);
 
-  const int nc = (n - 1) / 2;
-  const int Ib = (x0 + 1) >> 1, Jb = (y0 + 1) >> 1;  // coarse indices at ct[0]
-  if (PROL) {
-    const G* xcs = xc + (int64_t)slice * nc * nc;
-    for (int idx = threadIdx.x; idx < CH * CW; idx += blockDim.x) {
-      const int jj = idx / CW, ii = idx - jj * CW;
-      const int I = Ib + ii, Jc = Jb + jj;
-      ct[idx] = (I >= 1 && I <= nc && Jc >= 1 && Jc <= nc) ? float(xcs[(int64_t)(Jc - 1) * nc + (I - 1)]) : 0.f;
-    }
-    __syncthreads();
-  }
-
-  // load: b' into shared memory, x into registers (0 from x = 0; + P xc with PROL, whose points
-  // of the first colour step's colour are overwritten unread, so they are not formed)
+  // load: x into registers (0 from x = 0) and b' into shared memory, in the pair layout
   float2 x[R][3];
+  {
+    const G* xw = x_in + off + (int64_t)gyw * n + cb;
+    const G* bg = b + off + (int64_t)gyw * n + cb;
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int gy = gyw + r;
-    const int64_t rbase = off + (int64_t)gy * n + cb;
-    float bv[6], xv[6];
+    for (int r = 0; r < R; ++r) {
 #pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      bv[e] = float(b[rbase + e]);
-      xv[e] = zero_init ? 0.f : float(x_in[rbase + e]);
-    }
-    if (PROL) {
-      int eskip = ((reverse ? 2 : 0) - 2 - gy - x0) % 3;
-      eskip += (eskip < 0) ? 3 : 0;
-#pragma unroll
-      for (int e = 0; e < 6; ++e) {
-        if (e % 3 == eskip) {
-          xv[e] = 0.f;
+      for (int k = 0; k < 3; ++k) {
+        float2* d = &bsh[(ry0 + r) * 96 + k * 32 + lane];
+        if constexpr (ASYNCB && std::is_same<G, float>::value) {
+          // binary32: asynchronous 4-byte copies straight into the pair slots (no registers held)
+          const unsigned dx = (unsigned)__cvta_generic_to_shared(&d->x);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dx), "l"(bg + (int64_t)r * n + k));
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dx + 4u), "l"(bg + (int64_t)r * n + k + 3));
         } else {
-          const int i = cb + e + 1, j = gy + 1;  // 1-based grid indices
-          const int I0 = i >> 1, J0 = j >> 1;
-          const int I1 = I0 + (i & 1), J1 = J0 + (j & 1);
-          xv[e] += 0.5f * (ct[(J0 - Jb) * CW + (I0 - Ib)] + ct[(J1 - Jb) * CW + (I1 - Ib)]);
+          *d = make_float2(float(bg[(int64_t)r * n + k]), float(bg[(int64_t)r * n + k + 3]));
         }
+        x[r][k] = zero_init ? make_float2(0.f, 0.f)
+                            : make_float2(float(xw[(int64_t)r * n + k]), float(xw[(int64_t)r * n + k + 3]));
       }
     }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      bsh[(ry0 + r) * 96 + k * 32 + lane] = make_float2(bv[k], bv[k + 3]);
-      x[r][k] = make_float2(xv[k], xv[k + 3]);
-    }
+    // each thread's copies are complete here; the first step's barrier publishes them to the block
+    if constexpr (ASYNCB && std::is_same<G, float>::value) asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
-  if (PROL) __syncthreads();  // ct (the edge-row space) is read before the first step writes it
+  if (PROL) {
+    // the coarse values under the region, coarse row by coarse row (coarse interior indices
+    // Ib .. Ib + CW - 1 by Jb .. Jb + CH - 1, zero outside 1 .. nc), then x += P xc
+    const int nc = (n - 1) / 2;
+    const int Ib = (x0 + 1) >> 1, Jb = (y0 + 1) >> 1;
+    const G* xcs = xc + (int64_t)slice * nc * nc;
+    for (int jj = warp; jj < CH; jj += NWARP) {
+      const int Jc = Jb + jj;
+      const bool rowok = Jc >= 1 && Jc <= nc;
+      const G* src = xcs + (int64_t)(Jc - 1) * nc - 1;  // indexed by the 1-based I
+      for (int ii = lane; ii < CW; ii += 32) {
+        const int I = Ib + ii;
+        ct[jj * CW + ii] = (rowok && I >= 1 && I <= nc) ? float(src[I]) : 0.f;
+      }
+    }
+    __syncthreads();
+    wide_add_prol<R, CW, PA, PY>(x, ct + (ry0 >> 1) * CW + 3 * lane);
+    __syncthreads();  // ct (the edge-row space) is read before the first step writes it
+  }
 
   const float2* bw = bsh + ry0 * 96;
 #pragma unroll 1
@@ -259,16 +290,48 @@ __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_
   }
 }
 
+template <typename G, int NSW, int R, int NWARP, int MINB, bool ASYNCB, bool DIAG, bool PROL>
+__global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_out, const G* __restrict__ x_in,
+                                                            const G* __restrict__ b, const G* __restrict__ xc,
+                                                            int n, const Coef<float>* __restrict__ coef,
+                                                            int coef_class, int J, int K, int level, int reverse,
+                                                            int zero_init) {
+  if (!PROL) {
+    wide_body<G, NSW, R, NWARP, ASYNCB, DIAG, PROL, 0, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
+                                                   zero_init);
+    return;
+  }
+  // the region origin as in wide_body: block-uniform parities
+  constexpr int H = 3 * NSW, RH = NWARP * R;
+  const int x0 = min(max((int)blockIdx.x * (kWW - 2 * H) - H, 0), n - kWW);
+  const int y0 = min(max((int)blockIdx.y * (RH - 2 * H) - H, 0), n - RH);
+  const int pa = (x0 + 1) & 1, py = (y0 + 1) & 1;
+  if (pa == 0 && py == 0)
+    wide_body<G, NSW, R, NWARP, ASYNCB, DIAG, PROL, 0, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
+                                                   zero_init);
+  else if (pa == 0)
+    wide_body<G, NSW, R, NWARP, ASYNCB, DIAG, PROL, 0, 1>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
+                                                   zero_init);
+  else if (py == 0)
+    wide_body<G, NSW, R, NWARP, ASYNCB, DIAG, PROL, 1, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
+                                                   zero_init);
+  else
+    wide_body<G, NSW, R, NWARP, ASYNCB, DIAG, PROL, 1, 1>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
+                                                   zero_init);
+}
+
 // Block shapes (rows per warp, warps, minimum resident blocks per SM)
 template <int SHAPE>
 struct WideShape;
 template <>
 struct WideShape<0> {
   static constexpr int R = 12, NWARP = 8, MINB = 2;
+  static constexpr bool ASYNCB = ST_WIDE_ASYNC_B0;  // b' through registers
 };
 template <>
 struct WideShape<1> {
-  static constexpr int R = 8, NWARP = 12, MINB = 1;
+  static constexpr int R = 8, NWARP = 12, MINB = 2;
+  static constexpr bool ASYNCB = true;  // b' by asynchronous copies (registers: 80 a thread)
 };
 
 template <typename G, int NSW, int SHAPE, bool DIAG, bool PROL>
@@ -281,7 +344,7 @@ cudaError_t wide_launch_shape(const st_handle_s* h, int k, int nslices, int cls,
   dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, nslices);
   constexpr size_t smem = wide_smem<S::R, S::NWARP>();
   const bool prof = (k == h->K) && prof_start(h);
-  k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, DIAG, PROL><<<grid, 32 * S::NWARP, smem, h->stream>>>(
+  k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, DIAG, PROL><<<grid, 32 * S::NWARP, smem, h->stream>>>(
       x_out, x_in, b, xc, n, coef_table<float>(h), cls, h->J, h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0);
   count_launch(h);
   if (prof) {
@@ -301,7 +364,7 @@ cudaError_t wide_attr_shape() {
   cudaError_t e = cudaSuccess;
 #define ST_WIDE_ATTR(NSW, DIAG, PROL)                                                                         \
   if (e == cudaSuccess)                                                                                       \
-    e = cudaFuncSetAttribute(k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, DIAG, PROL>, attr, smem);
+    e = cudaFuncSetAttribute(k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, DIAG, PROL>, attr, smem);
   ST_WIDE_ATTR(1, false, false)
   ST_WIDE_ATTR(1, false, true)
   ST_WIDE_ATTR(1, true, false)
