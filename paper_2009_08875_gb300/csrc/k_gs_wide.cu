@@ -39,6 +39,10 @@ namespace {
 // ---------------------------------------------------------------------------------------
 
 constexpr int kWW = 192;  // region width: 32 lanes x 6 columns
+#ifndef ST_WIDE_PROL_DIRECT
+#define ST_WIDE_PROL_DIRECT 1
+#endif
+constexpr bool kProlDirect = ST_WIDE_PROL_DIRECT;
 #ifndef ST_WIDE_ASYNC_B0
 #define ST_WIDE_ASYNC_B0 0
 #endif
@@ -146,6 +150,41 @@ __device__ __forceinline__ void wide_add_prol(float2 (&x)[R][3], const float* __
   }
 }
 
+// The same with the coarse values read straight from global memory into registers: the lane's
+// columns need the coarse columns I0 .. I0 + 3 (1-based, I0 = the coarse node under its element 0)
+// and the warp's rows the coarse rows J0 .. J0 + R / 2 (zero outside 1 .. nc); the loads go out
+// with the fine loads, and no barrier or staging is needed.
+template <typename G, int R, int PA, int PY>
+__device__ __forceinline__ void wide_add_prol_direct(float2 (&x)[R][3], const G* __restrict__ xcs, int nc, int I0,
+                                                     int J0) {
+  constexpr int JR = R / 2 + 1;
+  float cv[JR][4];
+#pragma unroll
+  for (int jr = 0; jr < JR; ++jr) {
+    const int Jc = J0 + jr;
+    const bool rowok = Jc >= 1 && Jc <= nc;
+    const int64_t rowbase = (int64_t)(Jc - 1) * nc - 1;  // + I: the 1-based coarse node (Jc, I)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int I = I0 + c;
+      cv[jr][c] = (rowok && I >= 1 && I <= nc) ? float(xcs[rowbase + I]) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int j0 = (r + PY) >> 1, j1 = j0 + ((r + PY) & 1);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const int i0 = (PA + e) >> 1, i1 = i0 + ((PA + e) & 1);
+      const float c = 0.5f * (cv[j0][i0] + cv[j1][i1]);
+      if (e < 3)
+        x[r][e].x += c;
+      else
+        x[r][e - 3].y += c;
+    }
+  }
+}
+
 // The first colour step of a sweep from x = 0: every neighbour is zero, so x = b'.
 template <int R, int P>
 __device__ __forceinline__ void wide_step_first(float2 (&x)[R][3], const float2* __restrict__ bs, int lane) {
@@ -167,12 +206,15 @@ constexpr size_t wide_smem() {
 // The kernel body for one parity class of block regions: PA = (x0 + 1) mod 2, PY = (y0 + 1) mod 2
 // fix the coarse offsets of the prolongation (PROL); every class is its own code path, so the
 // registers of one do not add to another's.
-template <typename G, int NSW, int R, int NWARP, bool ASYNCB, bool DIAG, bool PROL, int PA, int PY>
+template <typename G, int NSW, int R, int NWARP, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, int PA, int PY>
 __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __restrict__ x_in, const G* __restrict__ b,
                                           const G* __restrict__ xc, int n, const Coef<float>* __restrict__ coef,
                                           int coef_class, int J, int K, int level, int reverse, int zero_init) {
   constexpr int H = 3 * NSW;
   constexpr int RH = NWARP * R;  // region rows
+  // binary32 storage: b' may come by asynchronous copies, which frees the registers the direct
+  // prolongation needs; bfloat16 storage stages the coarse values in shared memory
+  constexpr bool kF32 = std::is_same<G, float>::value;
   constexpr int TX = kWW - 2 * H, TY = RH - 2 * H;
   constexpr int CW = kWW / 2 + 2, CH = RH / 2 + 2;  // coarse values under the region (PROL)
   static_assert(CW * CH <= 2 * NWARP * 2 * 96 * 2, "coarse values fit in the edge-row space");
@@ -208,7 +250,7 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         float2* d = &bsh[(ry0 + r) * 96 + k * 32 + lane];
-        if constexpr (ASYNCB && std::is_same<G, float>::value) {
+        if constexpr ((ASYNCB || (PROL && PDIR)) && kF32) {
           // binary32: asynchronous 4-byte copies straight into the pair slots (no registers held)
           const unsigned dx = (unsigned)__cvta_generic_to_shared(&d->x);
           asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dx), "l"(bg + (int64_t)r * n + k));
@@ -221,9 +263,13 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
       }
     }
     // each thread's copies are complete here; the first step's barrier publishes them to the block
-    if constexpr (ASYNCB && std::is_same<G, float>::value) asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if constexpr ((ASYNCB || (PROL && PDIR)) && kF32) asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
-  if (PROL) {
+  if (PROL && PDIR && kF32) {
+    const int nc = (n - 1) / 2;
+    wide_add_prol_direct<G, R, PA, PY>(x, xc + (int64_t)slice * nc * nc, nc, ((x0 + 1) >> 1) + 3 * lane,
+                                       ((y0 + 1) >> 1) + (ry0 >> 1));
+  } else if (PROL) {
     // the coarse values under the region, coarse row by coarse row (coarse interior indices
     // Ib .. Ib + CW - 1 by Jb .. Jb + CH - 1, zero outside 1 .. nc), then x += P xc
     const int nc = (n - 1) / 2;
@@ -290,14 +336,14 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
   }
 }
 
-template <typename G, int NSW, int R, int NWARP, int MINB, bool ASYNCB, bool DIAG, bool PROL>
+template <typename G, int NSW, int R, int NWARP, int MINB, bool ASYNCB, bool PDIR, bool DIAG, bool PROL>
 __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_out, const G* __restrict__ x_in,
                                                             const G* __restrict__ b, const G* __restrict__ xc,
                                                             int n, const Coef<float>* __restrict__ coef,
                                                             int coef_class, int J, int K, int level, int reverse,
                                                             int zero_init) {
   if (!PROL) {
-    wide_body<G, NSW, R, NWARP, ASYNCB, DIAG, PROL, 0, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
+    wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, 0, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
                                                    zero_init);
     return;
   }
@@ -307,16 +353,16 @@ __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_
   const int y0 = min(max((int)blockIdx.y * (RH - 2 * H) - H, 0), n - RH);
   const int pa = (x0 + 1) & 1, py = (y0 + 1) & 1;
   if (pa == 0 && py == 0)
-    wide_body<G, NSW, R, NWARP, ASYNCB, DIAG, PROL, 0, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
+    wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, 0, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
                                                    zero_init);
   else if (pa == 0)
-    wide_body<G, NSW, R, NWARP, ASYNCB, DIAG, PROL, 0, 1>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
+    wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, 0, 1>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
                                                    zero_init);
   else if (py == 0)
-    wide_body<G, NSW, R, NWARP, ASYNCB, DIAG, PROL, 1, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
+    wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, 1, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
                                                    zero_init);
   else
-    wide_body<G, NSW, R, NWARP, ASYNCB, DIAG, PROL, 1, 1>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
+    wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, 1, 1>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
                                                    zero_init);
 }
 
@@ -327,11 +373,13 @@ template <>
 struct WideShape<0> {
   static constexpr int R = 12, NWARP = 8, MINB = 2;
   static constexpr bool ASYNCB = ST_WIDE_ASYNC_B0;  // b' through registers
+  static constexpr bool PDIRECT = kProlDirect;      // coarse values straight into registers
 };
 template <>
 struct WideShape<1> {
   static constexpr int R = 8, NWARP = 12, MINB = 2;
   static constexpr bool ASYNCB = true;  // b' by asynchronous copies (registers: 80 a thread)
+  static constexpr bool PDIRECT = false;  // coarse values staged in shared memory
 };
 
 template <typename G, int NSW, int SHAPE, bool DIAG, bool PROL>
@@ -344,7 +392,7 @@ cudaError_t wide_launch_shape(const st_handle_s* h, int k, int nslices, int cls,
   dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, nslices);
   constexpr size_t smem = wide_smem<S::R, S::NWARP>();
   const bool prof = (k == h->K) && prof_start(h);
-  k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, DIAG, PROL><<<grid, 32 * S::NWARP, smem, h->stream>>>(
+  k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL><<<grid, 32 * S::NWARP, smem, h->stream>>>(
       x_out, x_in, b, xc, n, coef_table<float>(h), cls, h->J, h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0);
   count_launch(h);
   if (prof) {
@@ -364,7 +412,7 @@ cudaError_t wide_attr_shape() {
   cudaError_t e = cudaSuccess;
 #define ST_WIDE_ATTR(NSW, DIAG, PROL)                                                                         \
   if (e == cudaSuccess)                                                                                       \
-    e = cudaFuncSetAttribute(k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, DIAG, PROL>, attr, smem);
+    e = cudaFuncSetAttribute(k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL>, attr, smem);
   ST_WIDE_ATTR(1, false, false)
   ST_WIDE_ATTR(1, false, true)
   ST_WIDE_ATTR(1, true, false)
