@@ -50,75 +50,139 @@ constexpr bool kProlDirect = ST_WIDE_PROL_DIRECT;
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// The Gauss-Seidel update value of pair m (columns 6 l + m and 6 l + m + 3) of row r of a warp's
+// R rows: b' - (a_x/c)(W + E) - (a_y/c)(S + N) [- (d/c)(NE + SW)], with the neighbours of the
+// current iterate.  bs: b' of the warp's rows, bs[r * 96 + k * 32 + lane] = the pair k of the
+// lane in row r.  below / above: the edge rows of the warps underneath and on top, in the same
+// pair layout (zeros past the region).  zl / zr: the lane's west / east neighbour across the
+// region's edge is the grid boundary (a zero).  r and m are constants once inlined in an
+// unrolled loop.
+template <int R, bool DIAG>
+__device__ __forceinline__ float2 pair_update(const float2 (&x)[R][3], int r, int m, const float2* __restrict__ bs,
+                                              const float2* __restrict__ below, const float2* __restrict__ above,
+                                              int lane, bool zl, bool zr, float2 nax, float2 nay, float2 ndg) {
+  constexpr int kR1 = R - 1;
+  const int rs = r > 0 ? r - 1 : 0;
+  const int rn = r < kR1 ? r + 1 : kR1;
+  // west and east pairs (columns 6 l + m -+ 1 and 6 l + m + 3 -+ 1)
+  float2 W, E;
+  if (m == 0) {
+    const float t = shfl_up(x[r][2].y, 1);
+    W = make_float2(zl ? 0.f : t, x[r][2].x);
+  } else {
+    W = x[r][(m + 2) % 3];
+  }
+  if (m == 2) {
+    const float t = shfl_down(x[r][0].x, 1);
+    E = make_float2(x[r][0].y, zr ? 0.f : t);
+  } else {
+    E = x[r][(m + 1) % 3];
+  }
+  const float2 S = (r > 0) ? x[rs][m] : below[m * 32 + lane];
+  const float2 N = (r < kR1) ? x[rn][m] : above[m * 32 + lane];
+  float2 v = fma2(nax, add2(W, E), bs[r * 96 + m * 32 + lane]);
+  v = fma2(nay, add2(S, N), v);
+  if (DIAG) {
+    // (1,1) neighbours: the row above shifted east; (-1,-1): the row below shifted west
+    float2 NE, SW;
+    if (r < kR1) {
+      if (m == 2) {
+        const float t = shfl_down(x[rn][0].x, 1);
+        NE = make_float2(x[rn][0].y, zr ? 0.f : t);
+      } else {
+        NE = x[rn][(m + 1) % 3];
+      }
+    } else {
+      if (m == 2) {
+        const float t = above[lane + 1].x;  // lane 31 reads the next pair's slot: unused (zr or halo)
+        NE = make_float2(above[lane].y, zr ? 0.f : t);
+      } else {
+        NE = above[((m + 1) % 3) * 32 + lane];
+      }
+    }
+    if (r > 0) {
+      if (m == 0) {
+        const float t = shfl_up(x[rs][2].y, 1);
+        SW = make_float2(zl ? 0.f : t, x[rs][2].x);
+      } else {
+        SW = x[rs][(m + 2) % 3];
+      }
+    } else {
+      if (m == 0) {
+        const float t = below[64 + lane - 1].y;  // lane 0 reads the previous pair's slot: unused (zl or halo)
+        SW = make_float2(zl ? 0.f : t, below[64 + lane].x);
+      } else {
+        SW = below[((m + 2) % 3) * 32 + lane];
+      }
+    }
+    v = fma2(ndg, add2(NE, SW), v);
+  }
+  return v;
+}
+
 // One colour step on a warp's R rows.  P is the active element of the warp's first row (row r:
-// m(r) = (P - r) mod 3).  bs: b' of the warp's rows, bs[r * 96 + k * 32 + lane] = the pair k of
-// the lane in row r.  below / above: the edge rows of the warps underneath and on top, in the
-// same pair layout (zeros past the region).  zl / zr: the lane's west / east neighbour across
-// the region's edge is the grid boundary (a zero).
+// m(r) = (P - r) mod 3); the step overwrites the active pair of every row with its update value.
 template <int R, bool DIAG, int P>
 __device__ __forceinline__ void wide_step(float2 (&x)[R][3], const float2* __restrict__ bs,
                                           const float2* __restrict__ below, const float2* __restrict__ above,
                                           int lane, bool zl, bool zr, float2 nax, float2 nay, float2 ndg) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    constexpr int kR1 = R - 1;
     const int m = ((P - (r % 3)) + 3) % 3;  // a constant once the loop is unrolled
-    const int rs = r > 0 ? r - 1 : 0;
-    const int rn = r < kR1 ? r + 1 : kR1;
-    // west and east pairs (columns 6 l + m -+ 1 and 6 l + m + 3 -+ 1)
-    float2 W, E;
-    if (m == 0) {
-      const float t = shfl_up(x[r][2].y, 1);
-      W = make_float2(zl ? 0.f : t, x[r][2].x);
-    } else {
-      W = x[r][(m + 2) % 3];
+    x[r][m] = pair_update<R, DIAG>(x, r, m, bs, below, above, lane, zl, zr, nax, nay, ndg);
+  }
+}
+
+// The scaled residual r' = b' - C' x (C' = D^-1 C: the update value minus the point's own value)
+// of every point of a warp's rows, written over b' in shared memory (pair layout; b' of a row is
+// read only for that row's residual, and before its slot is overwritten).
+template <int R, bool DIAG>
+__device__ __forceinline__ void wide_residual(const float2 (&x)[R][3], float2* __restrict__ bs,
+                                              const float2* __restrict__ below, const float2* __restrict__ above,
+                                              int lane, bool zl, bool zr, float2 nax, float2 nay, float2 ndg) {
+  const float2 mone = make_float2(-1.f, -1.f);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 v = pair_update<R, DIAG>(x, r, k, bs, below, above, lane, zl, zr, nax, nay, ndg);
+      bs[r * 96 + k * 32 + lane] = fma2(x[r][k], mone, v);  // v - x, rounded once
     }
-    if (m == 2) {
-      const float t = shfl_down(x[r][0].x, 1);
-      E = make_float2(x[r][0].y, zr ? 0.f : t);
-    } else {
-      E = x[r][(m + 1) % 3];
+  }
+}
+
+// The restriction of the scaled residual to the coarse points whose fine centre lies in the
+// block's tile: D_c^-1 P^T D r' = rho r'(centre) + (rho / 2) ((r'_W + r'_E) + (r'_S + r'_N) +
+// (r'_NE + r'_SW)), rho = c / c_coarse (nested P1: the six fine neighbours along the coarse
+// edges carry weight 1/2).  A warp takes the centres in its own rows: rows r = PY, PY + 2, ...
+// (odd grid rows), and in a lane's columns the elements PA, PA + 2, PA + 4 (odd grid columns), so
+// every shared-memory offset is a constant.  rs: the residuals of the region in pair layout
+// (float index 2 ((e mod 3) 32 + lane) + e / 3 of element e of a lane in a row of 192 floats).
+template <typename G, int R, int NWARP, int PA, int PY>
+__device__ __forceinline__ void wide_restrict(const float* __restrict__ rs, G* __restrict__ bcs, int nc, int warp,
+                                              int lane, int gyw, int gx_lane, int tx0, int tx1, int ty0, int ty1,
+                                              float rho, float hrho) {
+  auto at = [&](int row, int e) -> float {  // residual at row `row` of the region, element e of this lane
+    row = row < 0 ? 0 : (row >= NWARP * R ? NWARP * R - 1 : row);  // clamped: only for centres outside the tile
+    const int ln = e < 0 ? lane - 1 : (e > 5 ? lane + 1 : lane);
+    const int ee = e < 0 ? 5 : (e > 5 ? 0 : e);
+    return rs[row * 192 + 2 * ((ee % 3) * 32 + ln) + ee / 3];
+  };
+  const int ry0 = warp * R;
+#pragma unroll
+  for (int r = PY; r < R; r += 2) {
+    const int gy = gyw + r;
+    if (gy < ty0 || gy >= ty1) continue;  // warp-uniform
+    const int cy = (gy - 1) >> 1;
+#pragma unroll
+    for (int e = PA; e < 6; e += 2) {
+      const int gx = gx_lane + e;
+      const int row = ry0 + r;
+      const float c = at(row, e);
+      const float sum = ((at(row, e - 1) + at(row, e + 1)) + (at(row - 1, e) + at(row + 1, e))) +
+                        (at(row + 1, e + 1) + at(row - 1, e - 1));
+      if (gx >= tx0 && gx < tx1) bcs[(int64_t)cy * nc + ((gx - 1) >> 1)] = G(__fmaf_rn(rho, c, hrho * sum));
     }
-    const float2 S = (r > 0) ? x[rs][m] : below[m * 32 + lane];
-    const float2 N = (r < kR1) ? x[rn][m] : above[m * 32 + lane];
-    float2 v = fma2(nax, add2(W, E), bs[r * 96 + m * 32 + lane]);
-    v = fma2(nay, add2(S, N), v);
-    if (DIAG) {
-      // (1,1) neighbours: the row above shifted east; (-1,-1): the row below shifted west
-      float2 NE, SW;
-      if (r < kR1) {
-        if (m == 2) {
-          const float t = shfl_down(x[rn][0].x, 1);
-          NE = make_float2(x[rn][0].y, zr ? 0.f : t);
-        } else {
-          NE = x[rn][(m + 1) % 3];
-        }
-      } else {
-        if (m == 2) {
-          const float t = above[lane + 1].x;  // lane 31 reads the next pair's slot: unused (zr or halo)
-          NE = make_float2(above[lane].y, zr ? 0.f : t);
-        } else {
-          NE = above[((m + 1) % 3) * 32 + lane];
-        }
-      }
-      if (r > 0) {
-        if (m == 0) {
-          const float t = shfl_up(x[rs][2].y, 1);
-          SW = make_float2(zl ? 0.f : t, x[rs][2].x);
-        } else {
-          SW = x[rs][(m + 2) % 3];
-        }
-      } else {
-        if (m == 0) {
-          const float t = below[64 + lane - 1].y;  // lane 0 reads the previous pair's slot: unused (zl or halo)
-          SW = make_float2(zl ? 0.f : t, below[64 + lane].x);
-        } else {
-          SW = below[((m + 2) % 3) * 32 + lane];
-        }
-      }
-      v = fma2(ndg, add2(NE, SW), v);
-    }
-    x[r][m] = v;
   }
 }
 
@@ -195,6 +259,23 @@ __device__ __forceinline__ void wide_step_first(float2 (&x)[R][3], const float2*
   }
 }
 
+// Tiles along one axis of n grid points (n >= W): regions of W points, tiles of W - 2 M points
+// inside the grid, but the first and the last tile W - M wide (a region that ends at the grid's
+// boundary needs no margin there; the last one ends at n and is at most W - M wide).  Tile b is
+// [t, e), its region starts at o = clamp(t - M, 0, n - W): the tile lies at least M inside every
+// side of its region that is not the grid's boundary.
+__host__ __device__ inline int wide_ntiles(int n, int W, int M) {
+  const int w0 = W - M, ti = W - 2 * M;
+  const int rest = n - 2 * w0;
+  return 2 + (rest > 0 ? (rest + ti - 1) / ti : 0);
+}
+__device__ __forceinline__ void wide_tile(int b, int nb, int n, int W, int M, int& t, int& e, int& o) {
+  const int w0 = W - M, ti = W - 2 * M;
+  t = b == 0 ? 0 : w0 + (b - 1) * ti;
+  e = b == nb - 1 ? n : w0 + b * ti;
+  o = min(max(t - M, 0), n - W);
+}
+
 // dynamic shared memory of one block: b' (RH rows x 96 pairs), the edge rows (2 parities x NWARP
 // warps x 2 rows x 96 pairs; also the coarse values of the prolongation before the first step),
 // and a zero row of 96 pairs
@@ -206,16 +287,20 @@ constexpr size_t wide_smem() {
 // The kernel body for one parity class of block regions: PA = (x0 + 1) mod 2, PY = (y0 + 1) mod 2
 // fix the coarse offsets of the prolongation (PROL); every class is its own code path, so the
 // registers of one do not add to another's.
-template <typename G, int NSW, int R, int NWARP, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, int PA, int PY>
+template <typename G, int NSW, int R, int NWARP, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, bool RESTR, int PA,
+          int PY>
 __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __restrict__ x_in, const G* __restrict__ b,
-                                          const G* __restrict__ xc, int n, const Coef<float>* __restrict__ coef,
-                                          int coef_class, int J, int K, int level, int reverse, int zero_init) {
+                                          const G* __restrict__ xc, G* __restrict__ bc, int n,
+                                          const Coef<float>* __restrict__ coef, int coef_class, int J, int K,
+                                          int level, int reverse, int zero_init) {
   constexpr int H = 3 * NSW;
   constexpr int RH = NWARP * R;  // region rows
   // binary32 storage: b' may come by asynchronous copies, which frees the registers the direct
   // prolongation needs; bfloat16 storage stages the coarse values in shared memory
   constexpr bool kF32 = std::is_same<G, float>::value;
-  constexpr int TX = kWW - 2 * H, TY = RH - 2 * H;
+  // tile margin: H, and 2 more when the launch also restricts the residual (the residual at the
+  // fine neighbours of the tile's coarse centres needs the iterate one point further out)
+  constexpr int M = H + (RESTR ? 2 : 0);
   constexpr int CW = kWW / 2 + 2, CH = RH / 2 + 2;  // coarse values under the region (PROL)
   static_assert(CW * CH <= 2 * NWARP * 2 * 96 * 2, "coarse values fit in the edge-row space");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -228,8 +313,9 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
   const int slice = blockIdx.z;
   const int64_t off = (int64_t)slice * n * n;
   // the block's tile and its region, clamped into the grid
-  const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
-  const int x0 = min(max(tx0 - H, 0), n - kWW), y0 = min(max(ty0 - H, 0), n - RH);
+  int tx0, tx1, x0, ty0, ty1, y0;
+  wide_tile(blockIdx.x, gridDim.x, n, kWW, M, tx0, tx1, x0);
+  wide_tile(blockIdx.y, gridDim.y, n, RH, M, ty0, ty1, y0);
   const int ry0 = warp * R;
   const int gyw = y0 + ry0;       // grid row of the warp's first row
   const int cb = x0 + 6 * lane;   // grid column of the lane's element 0
@@ -320,8 +406,36 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
     }
   }
 
-  // store the tile: grid rows ty0 .. ty0 + TY - 1, columns tx0 .. tx0 + TX - 1 (inside the grid)
-  const int ty1 = min(ty0 + TY, n), tx1 = min(tx0 + TX, n);
+  if (RESTR) {
+    // the residual of the smoothed iterate over the region (exact on the tile widened by one
+    // point), then its restriction to the coarse points of the tile: the coarse level's scaled
+    // right-hand side, with no pass of its own over x and b'
+    // the residual is that of the iterate as stored: round it to the storage type first (a
+    // no-op for binary32; bfloat16 storage keeps 8 bits)
+    if constexpr (!kF32) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[r][k] = make_float2(float(G(x[r][k].x)), float(G(x[r][k].y)));
+    }
+    constexpr int t = 3 * NSW;  // the next step parity's edge buffer
+    float2* ed = edge + ((t & 1) * NWARP + warp) * 192;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ed[k * 32 + lane] = x[0][k];
+      ed[96 + k * 32 + lane] = x[R - 1][k];
+    }
+    __syncthreads();
+    const float2* below = warp > 0 ? edge + ((t & 1) * NWARP + warp - 1) * 192 + 96 : zrow;
+    const float2* above = warp < NWARP - 1 ? edge + ((t & 1) * NWARP + warp + 1) * 192 : zrow;
+    wide_residual<R, DIAG>(x, bsh + ry0 * 96, below, above, lane, zl, zr, nax, nay, ndg);
+    __syncthreads();
+    const int nc = (n - 1) / 2;
+    wide_restrict<G, R, NWARP, PA, PY>(reinterpret_cast<const float*>(bsh), bc + (int64_t)slice * nc * nc, nc, warp,
+                                       lane, gyw, cb, tx0, tx1, ty0, ty1, cf.rho, 0.5f * cf.rho);
+  }
+
+  // store the tile (inside the grid)
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int gy = gyw + r;
@@ -336,34 +450,35 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
   }
 }
 
-template <typename G, int NSW, int R, int NWARP, int MINB, bool ASYNCB, bool PDIR, bool DIAG, bool PROL>
+template <typename G, int NSW, int R, int NWARP, int MINB, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, bool RESTR>
 __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_out, const G* __restrict__ x_in,
                                                             const G* __restrict__ b, const G* __restrict__ xc,
-                                                            int n, const Coef<float>* __restrict__ coef,
-                                                            int coef_class, int J, int K, int level, int reverse,
-                                                            int zero_init) {
-  if (!PROL) {
-    wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, 0, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
-                                                   zero_init);
+                                                            G* __restrict__ bc, int n,
+                                                            const Coef<float>* __restrict__ coef, int coef_class,
+                                                            int J, int K, int level, int reverse, int zero_init) {
+  static_assert(!(PROL && RESTR), "the prolongation starts post-smoothing, the restriction ends pre-smoothing");
+#define ST_WIDE_BODY(PA, PY)                                                                                    \
+  wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, RESTR, PA, PY>(x_out, x_in, b, xc, bc, n, coef, coef_class, \
+                                                                       J, K, level, reverse, zero_init)
+  if (!PROL && !RESTR) {
+    ST_WIDE_BODY(0, 0);
     return;
   }
-  // the region origin as in wide_body: block-uniform parities
-  constexpr int H = 3 * NSW, RH = NWARP * R;
-  const int x0 = min(max((int)blockIdx.x * (kWW - 2 * H) - H, 0), n - kWW);
-  const int y0 = min(max((int)blockIdx.y * (RH - 2 * H) - H, 0), n - RH);
+  // the region origin as in wide_body: block-uniform parities, one code path per class
+  constexpr int M = 3 * NSW + (RESTR ? 2 : 0);
+  int t, e, x0, y0;
+  wide_tile(blockIdx.x, gridDim.x, n, kWW, M, t, e, x0);
+  wide_tile(blockIdx.y, gridDim.y, n, NWARP * R, M, t, e, y0);
   const int pa = (x0 + 1) & 1, py = (y0 + 1) & 1;
   if (pa == 0 && py == 0)
-    wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, 0, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
-                                                   zero_init);
+    ST_WIDE_BODY(0, 0);
   else if (pa == 0)
-    wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, 0, 1>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
-                                                   zero_init);
+    ST_WIDE_BODY(0, 1);
   else if (py == 0)
-    wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, 1, 0>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
-                                                   zero_init);
+    ST_WIDE_BODY(1, 0);
   else
-    wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, 1, 1>(x_out, x_in, b, xc, n, coef, coef_class, J, K, level, reverse,
-                                                   zero_init);
+    ST_WIDE_BODY(1, 1);
+#undef ST_WIDE_BODY
 }
 
 // Block shapes (rows per warp, warps, minimum resident blocks per SM)
@@ -382,24 +497,26 @@ struct WideShape<1> {
   static constexpr bool PDIRECT = false;  // coarse values staged in shared memory
 };
 
-template <typename G, int NSW, int SHAPE, bool DIAG, bool PROL>
+template <typename G, int NSW, int SHAPE, bool DIAG, bool PROL, bool RESTR>
 cudaError_t wide_launch_shape(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in,
-                              const G* b, const G* xc, bool reverse, bool zero_init) {
+                              const G* b, const G* xc, G* bc, bool reverse, bool zero_init) {
   using S = WideShape<SHAPE>;
-  constexpr int H = 3 * NSW, RH = S::R * S::NWARP;
+  constexpr int M = 3 * NSW + (RESTR ? 2 : 0), RH = S::R * S::NWARP;
   const int n = (1 << k) - 1;
-  const int TX = kWW - 2 * H, TY = RH - 2 * H;
-  dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, nslices);
+  dim3 grid(wide_ntiles(n, kWW, M), wide_ntiles(n, RH, M), nslices);
   constexpr size_t smem = wide_smem<S::R, S::NWARP>();
   const bool prof = (k == h->K) && prof_start(h);
-  k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL><<<grid, 32 * S::NWARP, smem, h->stream>>>(
-      x_out, x_in, b, xc, n, coef_table<float>(h), cls, h->J, h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0);
+  k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR>
+      <<<grid, 32 * S::NWARP, smem, h->stream>>>(x_out, x_in, b, xc, bc, n, coef_table<float>(h), cls, h->J, h->K, k,
+                                                 reverse ? 1 : 0, zero_init ? 1 : 0);
   count_launch(h);
   if (prof) {
+    // bytes: read x (not from x = 0) and b', write x; the coarse iterate read by the
+    // prolongation, or the coarse right-hand side written by the restriction
     const double pts = (double)n * n * nslices;
     const double nc = (double)((n - 1) / 2);
     prof_stop(h, (DIAG ? 1 : 0) + 2, pts * NSW * (DIAG ? 6.0 : 4.0),
-              sizeof(G) * (pts * (zero_init ? 2.0 : 3.0) + (PROL ? nc * nc * nslices : 0.0)));
+              sizeof(G) * (pts * (zero_init ? 2.0 : 3.0) + ((PROL || RESTR) ? nc * nc * nslices : 0.0)));
   }
   return cudaGetLastError();
 }
@@ -410,17 +527,22 @@ cudaError_t wide_attr_shape() {
   const int smem = (int)wide_smem<S::R, S::NWARP>();
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaSuccess;
-#define ST_WIDE_ATTR(NSW, DIAG, PROL)                                                                         \
-  if (e == cudaSuccess)                                                                                       \
-    e = cudaFuncSetAttribute(k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL>, attr, smem);
-  ST_WIDE_ATTR(1, false, false)
-  ST_WIDE_ATTR(1, false, true)
-  ST_WIDE_ATTR(1, true, false)
-  ST_WIDE_ATTR(1, true, true)
-  ST_WIDE_ATTR(3, false, false)
-  ST_WIDE_ATTR(3, false, true)
-  ST_WIDE_ATTR(3, true, false)
-  ST_WIDE_ATTR(3, true, true)
+#define ST_WIDE_ATTR(NSW, DIAG, PROL, RESTR)                                                                   \
+  if (e == cudaSuccess)                                                                                        \
+    e = cudaFuncSetAttribute(k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR>, \
+                             attr, smem);
+  ST_WIDE_ATTR(1, false, false, false)
+  ST_WIDE_ATTR(1, false, true, false)
+  ST_WIDE_ATTR(1, false, false, true)
+  ST_WIDE_ATTR(1, true, false, false)
+  ST_WIDE_ATTR(1, true, true, false)
+  ST_WIDE_ATTR(1, true, false, true)
+  ST_WIDE_ATTR(3, false, false, false)
+  ST_WIDE_ATTR(3, false, true, false)
+  ST_WIDE_ATTR(3, false, false, true)
+  ST_WIDE_ATTR(3, true, false, false)
+  ST_WIDE_ATTR(3, true, true, false)
+  ST_WIDE_ATTR(3, true, false, true)
 #undef ST_WIDE_ATTR
   return e;
 }
@@ -437,8 +559,20 @@ template <typename G, int NSW, bool DIAG, bool PROL>
 cudaError_t wide_launch(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out, const G* x_in,
                         const G* b, const G* xc, bool reverse, bool zero_init) {
   if (shape == 1)
-    return wide_launch_shape<G, NSW, 1, DIAG, PROL>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
-  return wide_launch_shape<G, NSW, 0, DIAG, PROL>(h, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+    return wide_launch_shape<G, NSW, 1, DIAG, PROL, false>(h, k, nslices, cls, x_out, x_in, b, xc, nullptr, reverse,
+                                                           zero_init);
+  return wide_launch_shape<G, NSW, 0, DIAG, PROL, false>(h, k, nslices, cls, x_out, x_in, b, xc, nullptr, reverse,
+                                                         zero_init);
+}
+
+template <typename G, int NSW, bool DIAG>
+cudaError_t wide_launch_restrict(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out,
+                                 const G* x_in, const G* b, G* bc, bool zero_init) {
+  if (shape == 1)
+    return wide_launch_shape<G, NSW, 1, DIAG, false, true>(h, k, nslices, cls, x_out, x_in, b, nullptr, bc, false,
+                                                           zero_init);
+  return wide_launch_shape<G, NSW, 0, DIAG, false, true>(h, k, nslices, cls, x_out, x_in, b, nullptr, bc, false,
+                                                         zero_init);
 }
 
 cudaError_t wide_set_attributes() {
@@ -457,7 +591,11 @@ cudaError_t wide_set_attributes() {
   template cudaError_t wide_launch<G, NSW, true, false>(const st_handle_s*, int, int, int, int, G*, const G*,  \
                                                         const G*, const G*, bool, bool);                       \
   template cudaError_t wide_launch<G, NSW, true, true>(const st_handle_s*, int, int, int, int, G*, const G*,   \
-                                                       const G*, const G*, bool, bool);
+                                                       const G*, const G*, bool, bool);                        \
+  template cudaError_t wide_launch_restrict<G, NSW, false>(const st_handle_s*, int, int, int, int, G*,         \
+                                                           const G*, const G*, G*, bool);                      \
+  template cudaError_t wide_launch_restrict<G, NSW, true>(const st_handle_s*, int, int, int, int, G*,          \
+                                                          const G*, const G*, G*, bool);
 ST_WIDE(float, 1)
 ST_WIDE(float, 3)
 ST_WIDE(__nv_bfloat16, 1)

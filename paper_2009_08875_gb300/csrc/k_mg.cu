@@ -466,6 +466,12 @@ constexpr int kRCX = 32, kRCY = 16;
 constexpr int kRFX = 2 * kRCX + 1, kRFY = 2 * kRCY + 1;  // residual points
 constexpr int kRXX = kRFX + 2, kRXY = kRFY + 2;          // x points (one-point halo)
 
+// a b + c: one fused multiply-add in binary32 and binary64, the two double-float operations in
+// double-float
+__device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ df64 mad(df64 a, df64 b, df64 c) { return a * b + c; }
+
 template <typename T, typename G, bool DIAG>
 __global__ void __launch_bounds__(256) k_residual_restrict(G* __restrict__ bc, const G* __restrict__ x,
                                                            const G* __restrict__ b, int n,
@@ -543,8 +549,9 @@ __global__ void __launch_bounds__(256) k_residual_restrict(G* __restrict__ bc, c
     }
     const int i = (2 * ty + 1) * kRFX + (2 * tx + 1);
     T e = (rs[i - 1] + rs[i + 1]) + (rs[i - kRFX] + rs[i + kRFX]) + (rs[i + kRFX + 1] + rs[i - kRFX - 1]);
-    // coarse scaled rhs: D_c^-1 P^T D r' = (c / c_coarse) P^T r'
-    bc[(int64_t)slice * nc * nc + (int64_t)cy * nc + cx] = G(cf.rho * rs[i] + (T(0.5) * cf.rho) * e);
+    // coarse scaled rhs: D_c^-1 P^T D r' = (c / c_coarse) P^T r', as one fma onto the rounded
+    // edge term (the order the fused restriction of the wide Gauss-Seidel kernel uses)
+    bc[(int64_t)slice * nc * nc + (int64_t)cy * nc + cx] = G(mad(cf.rho, rs[i], (T(0.5) * cf.rho) * e));
   }
 }
 
@@ -660,10 +667,28 @@ int gs_kind(const st_handle_s* h, bool diag, int k) {
   return h->gs_kind[type_slot<T>()][diag ? 1 : 0][k];
 }
 
+// Whether pre-smoothing on level k runs the wide binary32 kernel, whose last launch can also form
+// and restrict the residual (wide_launch_restrict)
+template <typename T>
+bool wide_restricts(const st_handle_s* h, bool diag, int k) {
+  if (!std::is_same<T, float>::value) return false;
+  const int kind = gs_kind<T>(h, diag, k);
+  return kind >= 5 && wide_fits(h, kind - 5, k);
+}
+
+// bc != nullptr (only where wide_restricts): the launch also writes the coarse right-hand side
 template <typename T, typename G, bool DIAG>
 cudaError_t gs_sweeps(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in, const G* b,
-                      const G* xc, bool reverse, bool zero_init, int nsw) {
+                      const G* xc, bool reverse, bool zero_init, int nsw, G* bc = nullptr) {
   constexpr int F = SweepShape<T>::kFusedNSW;
+  if constexpr (std::is_same<T, float>::value) {
+    if (bc) {
+      const int sh = gs_kind<T>(h, DIAG, k) - 5;
+      return (F > 1 && nsw == F)
+                 ? wide_launch_restrict<G, F, DIAG>(h, sh, k, nslices, cls, x_out, x_in, b, bc, zero_init)
+                 : wide_launch_restrict<G, 1, DIAG>(h, sh, k, nslices, cls, x_out, x_in, b, bc, zero_init);
+    }
+  }
   {
     const int kind = gs_kind<T>(h, DIAG, k);
     if (kind >= 2) {  // register tiles, block shape kind - 2
@@ -709,10 +734,14 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, G* const x
     count_launch(h);
     return cudaGetLastError();
   }
+  G* bc = reinterpret_cast<G*>(L.bc[k - 1]);
+  // the wide binary32 kernel forms and restricts the residual in its last pre-smoothing launch
+  const bool fused = h->cfg.n_pre > 0 && wide_restricts<T>(h, DIAG, k);
   for (int s = 0; s < h->cfg.n_pre;) {
     const int nsw = (h->cfg.n_pre - s >= SweepShape<T>::kFusedNSW) ? SweepShape<T>::kFusedNSW : 1;
+    G* bco = (fused && s + nsw == h->cfg.n_pre) ? bc : nullptr;
     if ((e = gs_sweeps<T, G, DIAG>(h, k, nslices, cls, xb[*cur ^ 1], xb[*cur], b, nullptr, false,
-                                x_is_zero && s == 0, nsw)) != cudaSuccess)
+                                x_is_zero && s == 0, nsw, bco)) != cudaSuccess)
       return e;
     *cur ^= 1;
     s += nsw;
@@ -722,13 +751,14 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, G* const x
     if ((e = cudaMemsetAsync(xb[*cur], 0, sizeof(G) * (size_t)N * nslices, h->stream)) != cudaSuccess) return e;
   }
   G* x = xb[*cur];
-  G* bc = reinterpret_cast<G*>(L.bc[k - 1]);
-  const int nc = (1 << (k - 1)) - 1;
-  dim3 gr((nc + kRCX - 1) / kRCX, (nc + kRCY - 1) / kRCY, nslices);
-  k_residual_restrict<T, G, DIAG><<<gr, 256, 0, h->stream>>>(bc, x, b, n, coef_table<T>(h), cls, h->J, h->K, k,
-                                                             h->domain);
-  count_launch(h);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!fused) {
+    const int nc = (1 << (k - 1)) - 1;
+    dim3 gr((nc + kRCX - 1) / kRCX, (nc + kRCY - 1) / kRCY, nslices);
+    k_residual_restrict<T, G, DIAG><<<gr, 256, 0, h->stream>>>(bc, x, b, n, coef_table<T>(h), cls, h->J, h->K, k,
+                                                               h->domain);
+    count_launch(h);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   G* const xcb[2] = {reinterpret_cast<G*>(L.xc[k - 1]), reinterpret_cast<G*>(L.xc2[k - 1])};
   int ccur = 0;
   if ((e = vcycle<T, G, DIAG>(h, k - 1, nslices, cls, xcb, &ccur, bc, true)) != cudaSuccess) return e;

@@ -280,6 +280,12 @@ bool wide_fits(const st_handle_s* h, int shape, int k);
 template <typename G, int NSW, bool DIAG, bool PROL>
 cudaError_t wide_launch(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out, const G* x_in,
                         const G* b, const G* xc, bool reverse, bool zero_init);
+// the same for the last pre-smoothing launch of a V-cycle, which also forms the residual of the
+// smoothed iterate and restricts it: bc receives the next coarser level's scaled right-hand side
+// (what k_residual_restrict would write)
+template <typename G, int NSW, bool DIAG>
+cudaError_t wide_launch_restrict(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out,
+                                 const G* x_in, const G* b, G* bc, bool zero_init);
 // dynamic shared-memory limits of the wide kernels (once per device)
 cudaError_t wide_set_attributes();
 
