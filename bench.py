@@ -51,6 +51,16 @@ NCU_TRAFFIC = {
         ("Kl", "wavefront"): (154.963e6 + 41.567e6) * 513 / 33,
     },
 }
+# DRAM traffic (bytes) per finest-level binary32 K_x launch of the wide register kernel
+# (k_gs_wide.cuh) from one ncu capture at K = 9, J = 6 (130 slices), scaled by slices to the 1026
+# slices of the full launch; keyed by the SHA-256 of the header's text (null once it changes):
+# profiles/k_gs_wide_f32_Kx_K9_J6.md
+NCU_TRAFFIC_WIDE = {
+    "2851b3e5abd564abc3b8e30b3f3c37305296bd797f5db645c10392478ad1d161": {
+        "K_x_post_smoothing_with_prolongation": (305.531648e6 + 105.769216e6) * 1026 / 130,
+        "K_x_pre_smoothing_with_restriction": (271.856384e6 + 129.012480e6) * 1026 / 130,
+    },
+}
 KERNEL_OF = {"tiles": ("k_gs_sweep", "k_mg.cu"), "wavefront": ("k_gs_wave", "k_mg.cu"),
              "registers": ("k_gs_reg", "k_gs_reg.cu")}
 
@@ -88,7 +98,7 @@ def parse():
                     help="requests per point of the offered-load sweep (25/50/90%% of capacity)")
     ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--smoother", choices=["auto", "tiles", "wavefront", "registers", "registers_8x12", "registers_6x16",
-                             "registers_wide", "registers_wide_8x12"],
+                             "registers_wide"],
                     default="auto",
                     help="Gauss-Seidel kernel: autotuned per level (default) or one kernel on every level")
     ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_precond", "mixed_bf16", "fp64_df"], default="fp64",
@@ -443,7 +453,18 @@ def f32_sweep_roof(prof, step_ms, hbm_peak, hbm_src):
             "K_x_only": {"launches": n - nd,
                          "achieved": ((nbytes - bd) / ((ms_sum - msd) / 1e3) / 1e9) if ms_sum > msd else None,
                          "avg_launch_ms": (ms_sum - msd) / (n - nd) if n > nd else None},
-            "traffic": None}
+            "traffic": wide_traffic()}
+
+
+def wide_traffic():
+    """ncu DRAM bytes per full-size K_x launch of the wide binary32 kernel, if its source is the
+    captured one: the mean of the two captured launch kinds, and each."""
+    with open(os.path.join(ROOT, "paper_2009_08875_gb300", "csrc", "k_gs_wide.cuh"), "rb") as fh:
+        t = NCU_TRAFFIC_WIDE.get(hashlib.sha256(fh.read()).hexdigest())
+    if not t:
+        return None
+    return {"bytes_per_K_x_launch": sum(t.values()) / len(t), "by_launch": t,
+            "source": "ncu at K=9, J=6 (130 slices) scaled by slices to 1026: profiles/k_gs_wide_f32_Kx_K9_J6.md"}
 
 
 def gpu_local_cpus(device_index):

@@ -386,10 +386,11 @@ st_status st_sharded_solve(st_handle h, const st_comm* comm, int rank, int nrank
  * shared-memory tiles (the default), a register wavefront, whose strips of 90 columns are cut into
  * row segments walked by separate warps, and register tiles, whose 96-column regions sit in the
  * registers of a block's warps (binary32: 12 rows x 8 warps, 8 x 12 or 6 x 16, the autotuner
- * trying each; binary64 and double-float: 6 rows x 8 warps).  Binary32 has two more register
- * block shapes on the unit square: 192-column regions (12 rows x 8 warps or 8 x 12) placed
- * inside the grid, whose lanes update two points of one colour with one paired binary32
- * instruction, on the levels with 2^k - 1 >= 192 (elsewhere they run as the first shape).
+ * trying each; binary64 and double-float: 6 rows x 8 warps).  Binary32 has one more register
+ * block shape on the unit square: 192-column regions of 12 rows x 8 warps placed inside the
+ * grid, whose lanes update two points of one colour with one paired binary32 instruction, and
+ * whose last pre-smoothing launch of a V-cycle also forms and restricts the residual, on the
+ * levels with 2^k - 1 >= 192 (elsewhere it runs as the first shape).
  * For every multigrid level
  * above the coarsest, for binary64 and binary32 and for K_x (no mass couplings, 2 B N_t slices)
  * and K_l (mass couplings, B N_t slices), this times one pre-smoothing launch of each kernel (the
@@ -405,10 +406,10 @@ st_status st_autotune(st_handle h, float* times_ms);
 
 /* Forces one Gauss-Seidel kernel on every level of this handle: kind 0 shared-memory tiles (the
  * state after set-up), 1 register wavefront, 2, 3, 4 register tiles of block shape 0, 1, 2 (in
- * binary32 12 rows x 8 warps, 8 x 12, 6 x 16; binary64 and double-float always 6 x 8), 5, 6 the
- * binary32 192-column regions with paired arithmetic of 12 rows x 8 warps and 8 x 12 (unit square,
- * levels with 2^k - 1 >= 192; shape 0 elsewhere and in binary64 and double-float).  All give
- * bitwise the same sweeps.  Returns ST_ERR_ARG for any other kind. */
+ * binary32 12 rows x 8 warps, 8 x 12, 6 x 16; binary64 and double-float always 6 x 8), 5 the
+ * binary32 192-column regions with paired arithmetic (unit square, levels with 2^k - 1 >= 192;
+ * shape 0 elsewhere and in binary64 and double-float).  All give bitwise the same sweeps and
+ * coarse right-hand sides.  Returns ST_ERR_ARG for any other kind. */
 st_status st_set_smoother(st_handle h, int kind);
 
 /* Forces the register wavefront's rows per segment on every level of this handle (rows >= 1;

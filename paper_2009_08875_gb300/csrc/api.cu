@@ -1216,8 +1216,8 @@ st_status st_set_wave_rows(st_handle h, int rows) {
 st_status st_set_smoother(st_handle h, int kind) {
   ST_CHECK(check_handle(h));
   if (kind < 0 || kind > 1 + kRegShapes) {
-    set_error("st_set_smoother: kind must be 0 (shared-memory tiles), 1 (wavefront) or 2..6 (register tiles of "
-              "block shape 0..4)");
+    set_error("st_set_smoother: kind must be 0 (shared-memory tiles), 1 (wavefront) or 2..5 (register tiles of "
+              "block shape 0..3)");
     return ST_ERR_ARG;
   }
   std::memset(h->gs_kind, kind, sizeof(h->gs_kind));

@@ -272,12 +272,12 @@ cudaError_t reg_launch_shape(const st_handle_s* h, int k, int nslices, int cls, 
 template <typename T, typename G, int NSW, bool DIAG, bool PROL>
 cudaError_t reg_launch(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out, const G* x_in,
                        const G* b, const G* xc, bool reverse, bool zero_init) {
-  // shapes 3 and 4: binary32 wide regions with paired arithmetic (k_gs_wide.cu) on the levels
-  // whose grid holds a region; shape 0 elsewhere
+  // shape 3: binary32 wide regions with paired arithmetic (k_gs_wide.cuh) on the levels whose
+  // grid holds a region; shape 0 elsewhere
   if constexpr (std::is_same<T, float>::value) {
-    if (shape >= 3) {
-      if (wide_fits(h, shape - 3, k))
-        return wide_launch<G, NSW, DIAG, PROL>(h, shape - 3, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
+    if (shape == 3) {
+      if (wide_fits(h, 0, k))
+        return wide_launch<G, NSW, DIAG, PROL>(h, 0, k, nslices, cls, x_out, x_in, b, xc, reverse, zero_init);
       shape = 0;
     }
   }

@@ -1,7 +1,9 @@
 // Gauss-Seidel sweeps of the time-slice-batched binary32 multigrid (k_mg.cu) in wide register
 // tiles with paired arithmetic: the same three-colour sweeps as k_gs_sweep and k_gs_reg, two
 // points of one colour per lane and row updated by one packed binary32 instruction (Blackwell's
-// add / fma on float pairs).
+// add / fma on float pairs).  The kernels are instantiated in k_gs_wide_*.cu, one translation
+// unit per storage type and sweep count, so that they compile in parallel.
+#pragma once
 #include <cuda_bf16.h>
 
 #include <type_traits>
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_
 #undef ST_WIDE_BODY
 }
 
-// Block shapes (rows per warp, warps, minimum resident blocks per SM)
+// Block shape (rows per warp, warps, minimum resident blocks per SM)
 template <int SHAPE>
 struct WideShape;
 template <>
@@ -489,12 +491,6 @@ struct WideShape<0> {
   static constexpr int R = 12, NWARP = 8, MINB = 2;
   static constexpr bool ASYNCB = ST_WIDE_ASYNC_B0;  // b' through registers
   static constexpr bool PDIRECT = kProlDirect;      // coarse values straight into registers
-};
-template <>
-struct WideShape<1> {
-  static constexpr int R = 8, NWARP = 12, MINB = 2;
-  static constexpr bool ASYNCB = true;  // b' by asynchronous copies (registers: 80 a thread)
-  static constexpr bool PDIRECT = false;  // coarse values staged in shared memory
 };
 
 template <typename G, int NSW, int SHAPE, bool DIAG, bool PROL, bool RESTR>
@@ -521,69 +517,45 @@ cudaError_t wide_launch_shape(const st_handle_s* h, int k, int nslices, int cls,
   return cudaGetLastError();
 }
 
-template <typename G, int SHAPE>
-cudaError_t wide_attr_shape() {
-  using S = WideShape<SHAPE>;
+// dynamic shared-memory limits of the kernels of one storage type and sweep count
+template <typename G, int NSW>
+cudaError_t wide_attr() {
+  using S = WideShape<0>;
   const int smem = (int)wide_smem<S::R, S::NWARP>();
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaSuccess;
-#define ST_WIDE_ATTR(NSW, DIAG, PROL, RESTR)                                                                   \
+#define ST_WIDE_ATTR(DIAG, PROL, RESTR)                                                                        \
   if (e == cudaSuccess)                                                                                        \
     e = cudaFuncSetAttribute(k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR>, \
                              attr, smem);
-  ST_WIDE_ATTR(1, false, false, false)
-  ST_WIDE_ATTR(1, false, true, false)
-  ST_WIDE_ATTR(1, false, false, true)
-  ST_WIDE_ATTR(1, true, false, false)
-  ST_WIDE_ATTR(1, true, true, false)
-  ST_WIDE_ATTR(1, true, false, true)
-  ST_WIDE_ATTR(3, false, false, false)
-  ST_WIDE_ATTR(3, false, true, false)
-  ST_WIDE_ATTR(3, false, false, true)
-  ST_WIDE_ATTR(3, true, false, false)
-  ST_WIDE_ATTR(3, true, true, false)
-  ST_WIDE_ATTR(3, true, false, true)
+  ST_WIDE_ATTR(false, false, false)
+  ST_WIDE_ATTR(false, true, false)
+  ST_WIDE_ATTR(false, false, true)
+  ST_WIDE_ATTR(true, false, false)
+  ST_WIDE_ATTR(true, true, false)
+  ST_WIDE_ATTR(true, false, true)
 #undef ST_WIDE_ATTR
   return e;
 }
 
 }  // namespace
 
-bool wide_fits(const st_handle_s* h, int shape, int k) {
-  const int n = (1 << k) - 1;
-  const int rh = shape == 0 ? WideShape<0>::R * WideShape<0>::NWARP : WideShape<1>::R * WideShape<1>::NWARP;
-  return h->domain == 0 && n >= kWW && n >= rh;
-}
-
 template <typename G, int NSW, bool DIAG, bool PROL>
-cudaError_t wide_launch(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out, const G* x_in,
+cudaError_t wide_launch(const st_handle_s* h, int /*shape*/, int k, int nslices, int cls, G* x_out, const G* x_in,
                         const G* b, const G* xc, bool reverse, bool zero_init) {
-  if (shape == 1)
-    return wide_launch_shape<G, NSW, 1, DIAG, PROL, false>(h, k, nslices, cls, x_out, x_in, b, xc, nullptr, reverse,
-                                                           zero_init);
   return wide_launch_shape<G, NSW, 0, DIAG, PROL, false>(h, k, nslices, cls, x_out, x_in, b, xc, nullptr, reverse,
                                                          zero_init);
 }
 
 template <typename G, int NSW, bool DIAG>
-cudaError_t wide_launch_restrict(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out,
+cudaError_t wide_launch_restrict(const st_handle_s* h, int /*shape*/, int k, int nslices, int cls, G* x_out,
                                  const G* x_in, const G* b, G* bc, bool zero_init) {
-  if (shape == 1)
-    return wide_launch_shape<G, NSW, 1, DIAG, false, true>(h, k, nslices, cls, x_out, x_in, b, nullptr, bc, false,
-                                                           zero_init);
   return wide_launch_shape<G, NSW, 0, DIAG, false, true>(h, k, nslices, cls, x_out, x_in, b, nullptr, bc, false,
                                                          zero_init);
 }
 
-cudaError_t wide_set_attributes() {
-  cudaError_t e = wide_attr_shape<float, 0>();
-  if (e == cudaSuccess) e = wide_attr_shape<float, 1>();
-  if (e == cudaSuccess) e = wide_attr_shape<__nv_bfloat16, 0>();
-  if (e == cudaSuccess) e = wide_attr_shape<__nv_bfloat16, 1>();
-  return e;
-}
-
-#define ST_WIDE(G, NSW)                                                                                       \
+// the launchers of one storage type G and sweep count NSW, and that pair's attribute setter
+#define ST_WIDE_INSTANTIATE(G, NSW, SETTER)                                                                   \
   template cudaError_t wide_launch<G, NSW, false, false>(const st_handle_s*, int, int, int, int, G*, const G*, \
                                                          const G*, const G*, bool, bool);                      \
   template cudaError_t wide_launch<G, NSW, false, true>(const st_handle_s*, int, int, int, int, G*, const G*,  \
@@ -595,11 +567,13 @@ cudaError_t wide_set_attributes() {
   template cudaError_t wide_launch_restrict<G, NSW, false>(const st_handle_s*, int, int, int, int, G*,         \
                                                            const G*, const G*, G*, bool);                      \
   template cudaError_t wide_launch_restrict<G, NSW, true>(const st_handle_s*, int, int, int, int, G*,          \
-                                                          const G*, const G*, G*, bool);
-ST_WIDE(float, 1)
-ST_WIDE(float, 3)
-ST_WIDE(__nv_bfloat16, 1)
-ST_WIDE(__nv_bfloat16, 3)
-#undef ST_WIDE
+                                                          const G*, const G*, G*, bool);                       \
+  cudaError_t SETTER() { return wide_attr<G, NSW>(); }
+
+// attribute setters of the four translation units
+cudaError_t wide_attr_f32_nsw1();
+cudaError_t wide_attr_f32_nsw3();
+cudaError_t wide_attr_bf16_nsw1();
+cudaError_t wide_attr_bf16_nsw3();
 
 }  // namespace st

@@ -1,0 +1,22 @@
+// Wide binary32 Gauss-Seidel sweeps (k_gs_wide.cuh): binary32 storage, three fused sweeps; the
+// level test and the attribute setter of all four instantiation units.
+#include "k_gs_wide.cuh"
+
+namespace st {
+
+ST_WIDE_INSTANTIATE(float, 3, wide_attr_f32_nsw3)
+
+bool wide_fits(const st_handle_s* h, int /*shape*/, int k) {
+  const int n = (1 << k) - 1;
+  return h->domain == 0 && n >= kWW && n >= WideShape<0>::R * WideShape<0>::NWARP;
+}
+
+cudaError_t wide_set_attributes() {
+  cudaError_t e = wide_attr_f32_nsw3();
+  if (e == cudaSuccess) e = wide_attr_f32_nsw1();
+  if (e == cudaSuccess) e = wide_attr_bf16_nsw3();
+  if (e == cudaSuccess) e = wide_attr_bf16_nsw1();
+  return e;
+}
+
+}  // namespace st

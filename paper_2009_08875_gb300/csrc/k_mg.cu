@@ -673,7 +673,7 @@ template <typename T>
 bool wide_restricts(const st_handle_s* h, bool diag, int k) {
   if (!std::is_same<T, float>::value) return false;
   const int kind = gs_kind<T>(h, diag, k);
-  return kind >= 5 && wide_fits(h, kind - 5, k);
+  return kind == 5 && wide_fits(h, 0, k);
 }
 
 // bc != nullptr (only where wide_restricts): the launch also writes the coarse right-hand side
@@ -683,10 +683,9 @@ cudaError_t gs_sweeps(const st_handle_s* h, int k, int nslices, int cls, G* x_ou
   constexpr int F = SweepShape<T>::kFusedNSW;
   if constexpr (std::is_same<T, float>::value) {
     if (bc) {
-      const int sh = gs_kind<T>(h, DIAG, k) - 5;
       return (F > 1 && nsw == F)
-                 ? wide_launch_restrict<G, F, DIAG>(h, sh, k, nslices, cls, x_out, x_in, b, bc, zero_init)
-                 : wide_launch_restrict<G, 1, DIAG>(h, sh, k, nslices, cls, x_out, x_in, b, bc, zero_init);
+                 ? wide_launch_restrict<G, F, DIAG>(h, 0, k, nslices, cls, x_out, x_in, b, bc, zero_init)
+                 : wide_launch_restrict<G, 1, DIAG>(h, 0, k, nslices, cls, x_out, x_in, b, bc, zero_init);
     }
   }
   {

@@ -265,17 +265,16 @@ inline const Coef<df64>* coef_table<df64>(const st_handle_s* h) {
 // Gauss-Seidel sweeps in register tiles (k_gs_reg.cu): nsw = NSW consecutive sweeps of one colour
 // order from x_in (+ P xc if xc != nullptr) into x_out, block shape `shape` (0: 12 rows x 8 warps
 // in binary32, 6 rows x 8 warps in binary64 and double-float; binary32 only: 1: 8 rows x 12
-// warps; 2: 6 rows x 16 warps; 3 and 4: the wide regions of k_gs_wide.cu, 12 rows x 8 warps and
-// 8 rows x 12 warps, on the levels where they fit, else shape 0; binary64 and double-float have
-// shape 0 only)
+// warps; 2: 6 rows x 16 warps; 3: the wide regions of k_gs_wide.cuh, 12 rows x 8 warps, on the
+// levels where they fit, else shape 0; binary64 and double-float have shape 0 only)
 template <typename T, typename G, int NSW, bool DIAG, bool PROL>
 cudaError_t reg_launch(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out, const G* x_in,
                        const G* b, const G* xc, bool reverse, bool zero_init);
-constexpr int kRegShapes = 5;
-// Binary32 Gauss-Seidel sweeps in wide register regions (k_gs_wide.cu): 192 columns, two points
-// of one colour per lane and row in packed binary32 arithmetic, regions clamped into the grid.
-// wide_fits: the unit square and a level whose n = 2^k - 1 holds a region of block shape `shape`
-// (0: 12 rows x 8 warps, 1: 8 rows x 12 warps).
+constexpr int kRegShapes = 4;
+// Binary32 Gauss-Seidel sweeps in wide register regions (k_gs_wide.cuh): 192 columns x 96 rows,
+// two points of one colour per lane and row in packed binary32 arithmetic, regions clamped into
+// the grid.  wide_fits: the unit square and a level whose n = 2^k - 1 holds a region (one block
+// shape: `shape` is 0).
 bool wide_fits(const st_handle_s* h, int shape, int k);
 template <typename G, int NSW, bool DIAG, bool PROL>
 cudaError_t wide_launch(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out, const G* x_in,

@@ -173,13 +173,13 @@ class Solver:
                 for k in range(2, self.K + 1) if any(t[12 * k + i] for i in range(12))}
 
     SMOOTHERS = {"tiles": 0, "wavefront": 1, "registers": 2, "registers_8x12": 3, "registers_6x16": 4,
-                 "registers_wide": 5, "registers_wide_8x12": 6}
+                 "registers_wide": 5}
 
     def set_smoother(self, kind):
         """Force the Gauss-Seidel kernel on every level (st_set_smoother): 'tiles', 'wavefront',
         'registers' (12 rows x 8 warps in binary32), 'registers_8x12', 'registers_6x16', or the
-        binary32 192-column regions with paired arithmetic 'registers_wide' (12 rows x 8 warps) and
-        'registers_wide_8x12' (where a level holds no such region: 'registers')."""
+        binary32 192-column regions with paired arithmetic 'registers_wide' (where a level holds no
+        such region: 'registers')."""
         _lib.check(_lib.load().st_set_smoother(self._h, self.SMOOTHERS[kind]))
 
     def set_wave_rows(self, rows):

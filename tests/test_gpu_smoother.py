@@ -39,7 +39,7 @@ def run_ops(s, x):
     return out
 
 
-REGISTER_KINDS = ("registers", "registers_8x12", "registers_6x16", "registers_wide", "registers_wide_8x12")
+REGISTER_KINDS = ("registers", "registers_8x12", "registers_6x16", "registers_wide")
 
 
 # K = 3 (one tile / strip), K = 6 and K = 8 (several strips and vertical segments, ragged edges);
@@ -91,7 +91,7 @@ def test_register_tiles_with_unfused_sweeps(K, J, domain, pre, post):
 def test_set_smoother_rejects_unknown_kind():
     from paper_2009_08875_gb300 import _lib
     with Solver(3, 2) as s:
-        assert _lib.load().st_set_smoother(s._h, 7) == 1  # ST_ERR_ARG
+        assert _lib.load().st_set_smoother(s._h, 6) == 1  # ST_ERR_ARG
         assert _lib.load().st_set_smoother(s._h, -1) == 1
         assert _lib.load().st_set_wave_rows(s._h, -1) == 1
         assert _lib.load().st_set_wave_rows(s._h, 65536) == 1
