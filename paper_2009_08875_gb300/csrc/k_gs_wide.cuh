@@ -137,7 +137,9 @@ __device__ __forceinline__ void wide_step(float2 (&x)[R][3], const float2* __res
 
 // The scaled residual r' = b' - C' x (C' = D^-1 C: the update value minus the point's own value)
 // of every point of a warp's rows, written over b' in shared memory (pair layout; b' of a row is
-// read only for that row's residual, and before its slot is overwritten).
+// read only for that row's residual, and before its slot is overwritten).  (The points of the
+// last colour step have residual exactly 0, but skipping them in these unrolled rows measured
+// slower than forming them.)
 template <int R, bool DIAG>
 __device__ __forceinline__ void wide_residual(const float2 (&x)[R][3], float2* __restrict__ bs,
                                               const float2* __restrict__ below, const float2* __restrict__ above,
@@ -289,10 +291,11 @@ constexpr size_t wide_smem() {
 // The kernel body for one parity class of block regions: PA = (x0 + 1) mod 2, PY = (y0 + 1) mod 2
 // fix the coarse offsets of the prolongation (PROL); every class is its own code path, so the
 // registers of one do not add to another's.
-template <typename G, int NSW, int R, int NWARP, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, bool RESTR, int PA,
-          int PY>
+template <typename G, int NSW, int R, int NWARP, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, bool RESTR,
+          bool SCALE, int PA, int PY>
 __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __restrict__ x_in, const G* __restrict__ b,
-                                          const G* __restrict__ xc, G* __restrict__ bc, int n,
+                                          const G* __restrict__ xc, G* __restrict__ bc,
+                                          const float* __restrict__ braw, G* __restrict__ bsc, int n,
                                           const Coef<float>* __restrict__ coef, int coef_class, int J, int K,
                                           int level, int reverse, int zero_init) {
   constexpr int H = 3 * NSW;
@@ -343,6 +346,18 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
           const unsigned dx = (unsigned)__cvta_generic_to_shared(&d->x);
           asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dx), "l"(bg + (int64_t)r * n + k));
           asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dx + 4u), "l"(bg + (int64_t)r * n + k + 3));
+        } else if constexpr (SCALE) {
+          // the finest level's b' = b / c formed here (what k_scale_rhs writes), and written for
+          // the tile's points for the launches that follow
+          const float* br = braw + off + (int64_t)(gyw + r) * n + cb;
+          const G v0 = G(br[k] * cf.inv_c), v1 = G(br[k + 3] * cf.inv_c);
+          *d = make_float2(float(v0), float(v1));
+          const int gy = gyw + r;
+          if (gy >= ty0 && gy < ty1) {
+            G* bw = bsc + off + (int64_t)gy * n + cb;
+            if (cb + k >= tx0 && cb + k < tx1) bw[k] = v0;
+            if (cb + k + 3 >= tx0 && cb + k + 3 < tx1) bw[k + 3] = v1;
+          }
         } else {
           *d = make_float2(float(bg[(int64_t)r * n + k]), float(bg[(int64_t)r * n + k + 3]));
         }
@@ -452,15 +467,19 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
   }
 }
 
-template <typename G, int NSW, int R, int NWARP, int MINB, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, bool RESTR>
+template <typename G, int NSW, int R, int NWARP, int MINB, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, bool RESTR,
+          bool SCALE>
 __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_out, const G* __restrict__ x_in,
                                                             const G* __restrict__ b, const G* __restrict__ xc,
-                                                            G* __restrict__ bc, int n,
+                                                            G* __restrict__ bc, const float* __restrict__ braw,
+                                                            G* __restrict__ bsc, int n,
                                                             const Coef<float>* __restrict__ coef, int coef_class,
                                                             int J, int K, int level, int reverse, int zero_init) {
   static_assert(!(PROL && RESTR), "the prolongation starts post-smoothing, the restriction ends pre-smoothing");
+  static_assert(!SCALE || RESTR, "the scaling is fused into the one pre-smoothing launch, which also restricts");
 #define ST_WIDE_BODY(PA, PY)                                                                                    \
-  wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, RESTR, PA, PY>(x_out, x_in, b, xc, bc, n, coef, coef_class, \
+  wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, RESTR, SCALE, PA, PY>(x_out, x_in, b, xc, bc, braw, bsc, n,   \
+                                                                              coef, coef_class,                   \
                                                                        J, K, level, reverse, zero_init)
   if (!PROL && !RESTR) {
     ST_WIDE_BODY(0, 0);
@@ -493,26 +512,28 @@ struct WideShape<0> {
   static constexpr bool PDIRECT = kProlDirect;      // coarse values straight into registers
 };
 
-template <typename G, int NSW, int SHAPE, bool DIAG, bool PROL, bool RESTR>
+template <typename G, int NSW, int SHAPE, bool DIAG, bool PROL, bool RESTR, bool SCALE = false>
 cudaError_t wide_launch_shape(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in,
-                              const G* b, const G* xc, G* bc, bool reverse, bool zero_init) {
+                              const G* b, const G* xc, G* bc, bool reverse, bool zero_init,
+                              const float* braw = nullptr, G* bsc = nullptr) {
   using S = WideShape<SHAPE>;
   constexpr int M = 3 * NSW + (RESTR ? 2 : 0), RH = S::R * S::NWARP;
   const int n = (1 << k) - 1;
   dim3 grid(wide_ntiles(n, kWW, M), wide_ntiles(n, RH, M), nslices);
   constexpr size_t smem = wide_smem<S::R, S::NWARP>();
   const bool prof = (k == h->K) && prof_start(h);
-  k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR>
-      <<<grid, 32 * S::NWARP, smem, h->stream>>>(x_out, x_in, b, xc, bc, n, coef_table<float>(h), cls, h->J, h->K, k,
-                                                 reverse ? 1 : 0, zero_init ? 1 : 0);
+  k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR, SCALE>
+      <<<grid, 32 * S::NWARP, smem, h->stream>>>(x_out, x_in, b, xc, bc, braw, bsc, n, coef_table<float>(h), cls, h->J,
+                                                 h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0);
   count_launch(h);
   if (prof) {
-    // bytes: read x (not from x = 0) and b', write x; the coarse iterate read by the
-    // prolongation, or the coarse right-hand side written by the restriction
+    // bytes: read x (not from x = 0) and b' (with SCALE: b, and write b'), write x; the coarse
+    // iterate read by the prolongation, or the coarse right-hand side written by the restriction
     const double pts = (double)n * n * nslices;
     const double nc = (double)((n - 1) / 2);
     prof_stop(h, (DIAG ? 1 : 0) + 2, pts * NSW * (DIAG ? 6.0 : 4.0),
-              sizeof(G) * (pts * (zero_init ? 2.0 : 3.0) + ((PROL || RESTR) ? nc * nc * nslices : 0.0)));
+              sizeof(G) * (pts * ((zero_init ? 2.0 : 3.0) + (SCALE ? 1.0 : 0.0)) +
+                           ((PROL || RESTR) ? nc * nc * nslices : 0.0)));
   }
   return cudaGetLastError();
 }
@@ -524,16 +545,20 @@ cudaError_t wide_attr() {
   const int smem = (int)wide_smem<S::R, S::NWARP>();
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaSuccess;
-#define ST_WIDE_ATTR(DIAG, PROL, RESTR)                                                                        \
+#define ST_WIDE_ATTR(DIAG, PROL, RESTR, SCALE)                                                                 \
   if (e == cudaSuccess)                                                                                        \
-    e = cudaFuncSetAttribute(k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR>, \
-                             attr, smem);
-  ST_WIDE_ATTR(false, false, false)
-  ST_WIDE_ATTR(false, true, false)
-  ST_WIDE_ATTR(false, false, true)
-  ST_WIDE_ATTR(true, false, false)
-  ST_WIDE_ATTR(true, true, false)
-  ST_WIDE_ATTR(true, false, true)
+    e = cudaFuncSetAttribute(                                                                                  \
+        k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR, SCALE>, attr, smem);
+  ST_WIDE_ATTR(false, false, false, false)
+  ST_WIDE_ATTR(false, true, false, false)
+  ST_WIDE_ATTR(false, false, true, false)
+  ST_WIDE_ATTR(true, false, false, false)
+  ST_WIDE_ATTR(true, true, false, false)
+  ST_WIDE_ATTR(true, false, true, false)
+  if constexpr (std::is_same<G, float>::value && NSW == 3) {
+    ST_WIDE_ATTR(false, false, true, true)
+    ST_WIDE_ATTR(true, false, true, true)
+  }
 #undef ST_WIDE_ATTR
   return e;
 }
@@ -552,6 +577,16 @@ cudaError_t wide_launch_restrict(const st_handle_s* h, int /*shape*/, int k, int
                                  const G* x_in, const G* b, G* bc, bool zero_init) {
   return wide_launch_shape<G, NSW, 0, DIAG, false, true>(h, k, nslices, cls, x_out, x_in, b, nullptr, bc, false,
                                                          zero_init);
+}
+
+// the finest level's only pre-smoothing launch of the first V-cycle (x = 0): b' = b / c formed from
+// the input b and written to bsc, three sweeps, and the residual restricted to bc (binary32
+// storage, three fused sweeps)
+template <bool DIAG>
+cudaError_t wide_launch_scale_restrict(const st_handle_s* h, int k, int nslices, int cls, float* x_out,
+                                       const float* braw, float* bsc, float* bc) {
+  return wide_launch_shape<float, 3, 0, DIAG, false, true, true>(h, k, nslices, cls, x_out, nullptr, bsc, nullptr, bc,
+                                                                 false, true, braw, bsc);
 }
 
 // the launchers of one storage type G and sweep count NSW, and that pair's attribute setter

@@ -5,6 +5,10 @@
 namespace st {
 
 ST_WIDE_INSTANTIATE(float, 3, wide_attr_f32_nsw3)
+template cudaError_t wide_launch_scale_restrict<false>(const st_handle_s*, int, int, int, float*, const float*, float*,
+                                                       float*);
+template cudaError_t wide_launch_scale_restrict<true>(const st_handle_s*, int, int, int, float*, const float*, float*,
+                                                      float*);
 
 bool wide_fits(const st_handle_s* h, int /*shape*/, int k) {
   const int n = (1 << k) - 1;

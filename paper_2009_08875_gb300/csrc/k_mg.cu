@@ -465,6 +465,7 @@ __global__ void k_prolong_add(G* __restrict__ x, const G* __restrict__ xc, int n
 constexpr int kRCX = 32, kRCY = 16;
 constexpr int kRFX = 2 * kRCX + 1, kRFY = 2 * kRCY + 1;  // residual points
 constexpr int kRXX = kRFX + 2, kRXY = kRFY + 2;          // x points (one-point halo)
+constexpr int kRZ = (kRFX + 2) / 3;                      // groups of three columns of a residual row
 
 // a b + c: one fused multiply-add in binary32 and binary64, the two double-float operations in
 // double-float
@@ -476,7 +477,7 @@ template <typename T, typename G, bool DIAG>
 __global__ void __launch_bounds__(256) k_residual_restrict(G* __restrict__ bc, const G* __restrict__ x,
                                                            const G* __restrict__ b, int n,
                                                            const Coef<T>* __restrict__ coef, int coef_class, int J,
-                                                           int K, int level, int lshape) {
+                                                           int K, int level, int lshape, int zc) {
   __shared__ T xs[kRXY * kRXX];
   __shared__ T rs[kRFY * kRFX];
   const int nc = (n - 1) / 2;
@@ -533,9 +534,26 @@ __global__ void __launch_bounds__(256) k_residual_restrict(G* __restrict__ bc, c
       xs[idx] = in ? T(xsl[(int64_t)gy * n + gx]) : T(0);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < kRFY * kRFX; idx += blockDim.x) {
-      const int ry = idx / kRFX, rx = idx - ry * kRFX;
-      rs[idx] = residual_at(rx, ry, fy0 + ry);
+    if (zc >= 0) {
+      // the residual of colour zc is exactly 0: the binary64 pipe forms only the other two
+      for (int idx = threadIdx.x; idx < kRFY * 2 * kRZ; idx += blockDim.x) {
+        const int ry = idx / (2 * kRZ), q = idx - ry * (2 * kRZ);
+        int ph = (zc - fx0 - (fy0 + ry) - 2) % 3;
+        ph += (ph < 0) ? 3 : 0;
+        const int rx = 3 * (q >> 1) + (ph + 1 + (q & 1)) % 3;
+        if (rx < kRFX) rs[ry * kRFX + rx] = residual_at(rx, ry, fy0 + ry);
+      }
+      for (int idx = threadIdx.x; idx < kRFY * kRZ; idx += blockDim.x) {
+        const int ry = idx / kRZ, j = idx - ry * kRZ;
+        int ph = (zc - fx0 - (fy0 + ry) - 2) % 3;
+        ph += (ph < 0) ? 3 : 0;
+        if (3 * j + ph < kRFX) rs[ry * kRFX + 3 * j + ph] = T(0);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < kRFY * kRFX; idx += blockDim.x) {
+        const int ry = idx / kRFX, rx = idx - ry * kRFX;
+        rs[idx] = residual_at(rx, ry, fy0 + ry);
+      }
     }
   }
   __syncthreads();
@@ -716,10 +734,12 @@ cudaError_t gs_sweeps(const st_handle_s* h, int k, int nslices, int cls, G* x_ou
 }
 
 // One V-cycle on level k.  xb[0], xb[1] are the level's two iterate buffers and *cur the one
-// holding the iterate; every sweep moves it to the other buffer.
+// holding the iterate; every sweep moves it to the other buffer.  braw != nullptr (binary32, the
+// finest level's first V-cycle, one pre-smoothing launch that also restricts): b' = b / c is not
+// there yet; that launch forms it from braw and writes it to bsc (= b).
 template <typename T, typename G, bool DIAG>
 cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, G* const xb[2], int* cur, const G* b,
-                   bool x_is_zero) {
+                   bool x_is_zero, const T* braw = nullptr, G* bsc = nullptr) {
   const st::MGLevels& L = h->mg;
   const int n = (1 << k) - 1;
   const int N = n * n;
@@ -738,6 +758,15 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, G* const x
   const bool fused = h->cfg.n_pre > 0 && wide_restricts<T>(h, DIAG, k);
   for (int s = 0; s < h->cfg.n_pre;) {
     const int nsw = (h->cfg.n_pre - s >= SweepShape<T>::kFusedNSW) ? SweepShape<T>::kFusedNSW : 1;
+    if constexpr (std::is_same<T, float>::value && std::is_same<G, float>::value) {
+      if (braw) {  // the caller checked: one launch of all n_pre sweeps, fused restriction
+        if ((e = wide_launch_scale_restrict<DIAG>(h, k, nslices, cls, xb[*cur ^ 1], braw, bsc, bc)) != cudaSuccess)
+          return e;
+        *cur ^= 1;
+        s += nsw;
+        continue;
+      }
+    }
     G* bco = (fused && s + nsw == h->cfg.n_pre) ? bc : nullptr;
     if ((e = gs_sweeps<T, G, DIAG>(h, k, nslices, cls, xb[*cur ^ 1], xb[*cur], b, nullptr, false,
                                 x_is_zero && s == 0, nsw, bco)) != cudaSuccess)
@@ -753,8 +782,14 @@ cudaError_t vcycle(const st_handle_s* h, int k, int nslices, int cls, G* const x
   if (!fused) {
     const int nc = (1 << (k - 1)) - 1;
     dim3 gr((nc + kRCX - 1) / kRCX, (nc + kRCY - 1) / kRCY, nslices);
+    // pre-smoothing ends with a colour-2 step, which set those points from the same operations
+    // the residual uses, on neighbours that have not changed since: their residual is exactly 0
+    // (not so after no pre-smoothing, or for an iterate stored narrower than it is computed).
+    // Only binary64 and double-float, bound by their arithmetic, gain from not forming them
+    // (measured: binary32 issue-bound lanes lose more to the uneven enumeration than they save).
+    const int zc = (h->cfg.n_pre > 0 && std::is_same<T, G>::value && sizeof(T) != 4) ? 2 : -1;
     k_residual_restrict<T, G, DIAG><<<gr, 256, 0, h->stream>>>(bc, x, b, n, coef_table<T>(h), cls, h->J, h->K, k,
-                                                               h->domain);
+                                                               h->domain, zc);
     count_launch(h);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -854,14 +889,21 @@ cudaError_t mg_run(const st_handle_s* h, int nslices, int coef_class, const T* b
   int cur = 0;
   G* bs = reinterpret_cast<G*>(h->Bs);
   const int n = h->n;
-  dim3 gs((n * n + 255) / 256, nslices);
-  k_scale_rhs<T, G><<<gs, 256, 0, h->stream>>>(bs, b, n, coef_table<T>(h), coef_class, h->J, h->K);
-  count_launch(h);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  // binary32 on the wide regions with one pre-smoothing launch: the scaling b' = b / c is formed
+  // by that launch of the first V-cycle
+  const bool fuse_scale = std::is_same<T, float>::value && std::is_same<G, float>::value && h->cfg.n_vcycles > 0 &&
+                          h->cfg.n_pre == SweepShape<T>::kFusedNSW && wide_restricts<T>(h, diag, h->K);
+  cudaError_t e = cudaSuccess;
+  if (!fuse_scale) {
+    dim3 gs((n * n + 255) / 256, nslices);
+    k_scale_rhs<T, G><<<gs, 256, 0, h->stream>>>(bs, b, n, coef_table<T>(h), coef_class, h->J, h->K);
+    count_launch(h);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   for (int c = 0; c < h->cfg.n_vcycles; ++c) {
-    e = diag ? vcycle<T, G, true>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0)
-             : vcycle<T, G, false>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0);
+    const T* braw = (fuse_scale && c == 0) ? b : nullptr;
+    e = diag ? vcycle<T, G, true>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0, braw, bs)
+             : vcycle<T, G, false>(h, h->K, nslices, coef_class, xb, &cur, bs, c == 0, braw, bs);
     if (e != cudaSuccess) return e;
   }
   if (h->cfg.n_vcycles == 0) return cudaMemsetAsync(x, 0, sizeof(T) * npts, h->stream);

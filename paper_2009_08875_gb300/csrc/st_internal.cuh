@@ -285,6 +285,12 @@ cudaError_t wide_launch(const st_handle_s* h, int shape, int k, int nslices, int
 template <typename G, int NSW, bool DIAG>
 cudaError_t wide_launch_restrict(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out,
                                  const G* x_in, const G* b, G* bc, bool zero_init);
+// the finest level's first pre-smoothing launch when it is also the last one (three sweeps from
+// x = 0, binary32 storage): forms b' = b / c from the input b (written to bsc, what k_scale_rhs
+// would write), smooths, and restricts the residual to bc
+template <bool DIAG>
+cudaError_t wide_launch_scale_restrict(const st_handle_s* h, int k, int nslices, int cls, float* x_out,
+                                       const float* braw, float* bsc, float* bc);
 // dynamic shared-memory limits of the wide kernels (once per device)
 cudaError_t wide_set_attributes();
 
