@@ -347,17 +347,10 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
           asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dx), "l"(bg + (int64_t)r * n + k));
           asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dx + 4u), "l"(bg + (int64_t)r * n + k + 3));
         } else if constexpr (SCALE) {
-          // the finest level's b' = b / c formed here (what k_scale_rhs writes), and written for
-          // the tile's points for the launches that follow
+          // the finest level's b' = b / c formed here (what k_scale_rhs writes); the tile's part
+          // is written out after the colour steps
           const float* br = braw + off + (int64_t)(gyw + r) * n + cb;
-          const G v0 = G(br[k] * cf.inv_c), v1 = G(br[k + 3] * cf.inv_c);
-          *d = make_float2(float(v0), float(v1));
-          const int gy = gyw + r;
-          if (gy >= ty0 && gy < ty1) {
-            G* bw = bsc + off + (int64_t)gy * n + cb;
-            if (cb + k >= tx0 && cb + k < tx1) bw[k] = v0;
-            if (cb + k + 3 >= tx0 && cb + k + 3 < tx1) bw[k + 3] = v1;
-          }
+          *d = make_float2(float(G(br[k] * cf.inv_c)), float(G(br[k + 3] * cf.inv_c)));
         } else {
           *d = make_float2(float(bg[(int64_t)r * n + k]), float(bg[(int64_t)r * n + k + 3]));
         }
@@ -423,6 +416,24 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
     }
   }
 
+  if (SCALE) {
+    // b' of the tile's points for the launches that follow, one warp row at a time with lane l
+    // at the columns l + 32 j (coalesced), read from the pair layout in shared memory before the
+    // residual overwrites it
+    const float* bf = reinterpret_cast<const float*>(bsh);
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+      const int gy = gyw + r;
+      if (gy < ty0 || gy >= ty1) continue;  // warp-uniform
+      G* row = bsc + off + (int64_t)gy * n;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int c = lane + 32 * j, e = c % 6;
+        const int gx = x0 + c;
+        if (gx >= tx0 && gx < tx1) row[gx] = G(bf[(ry0 + r) * 192 + 2 * ((e % 3) * 32 + c / 6) + e / 3]);
+      }
+    }
+  }
   if (RESTR) {
     // the residual of the smoothed iterate over the region (exact on the tile widened by one
     // point), then its restriction to the coarse points of the tile: the coarse level's scaled

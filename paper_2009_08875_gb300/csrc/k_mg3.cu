@@ -77,8 +77,10 @@ __global__ void __launch_bounds__(256) k_gs3(T* __restrict__ x, const T* __restr
   const int q = (n + 3) >> 2;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)q * n * n) return;
-  const int row = (int)(t / q), m = (int)(t - (int64_t)row * q);
-  const int iz = row / n, iy = row - iz * n;
+  // 32-bit unsigned division (t < q n^2 < 2^31 for the cube's levels): a fraction of 64-bit's cost
+  const unsigned row = (unsigned)t / (unsigned)q;
+  const int m = (int)((unsigned)t - row * (unsigned)q);
+  const int iz = (int)(row / (unsigned)n), iy = (int)row - iz * n;
   // colour of (ix, iy, iz) is (ix + iy + iz + 3) mod 4
   int ix0 = (colour - 3 - iy - iz) % 4;
   ix0 += ix0 < 0 ? 4 : 0;
@@ -105,7 +107,8 @@ __global__ void __launch_bounds__(256) k_residual3(T* __restrict__ r, const T* _
   const int64_t N3 = (int64_t)n * n * n;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= N3) return;
-  const int ix = (int)(p % n), iy = (int)((p / n) % n), iz = (int)(p / ((int64_t)n * n));
+  const unsigned pq = (unsigned)p, un = (unsigned)n, rq = pq / un;  // p < n^3 < 2^31
+  const int ix = (int)(pq - rq * un), iy = (int)(rq % un), iz = (int)(rq / un);
   const int slice = blockIdx.y;
   const int64_t off = (int64_t)slice * N3;
   const Coef<T> cf = coef_of(coef, cls, slice, J, K, level);
@@ -128,7 +131,8 @@ __global__ void __launch_bounds__(256) k_restrict3(T* __restrict__ bc, const T* 
   const int64_t Nc = (int64_t)nc * nc * nc;
   const int64_t pc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (pc >= Nc) return;
-  const int cx = (int)(pc % nc), cy = (int)((pc / nc) % nc), cz = (int)(pc / ((int64_t)nc * nc));
+  const unsigned pq = (unsigned)pc, un = (unsigned)nc, rq = pq / un;  // pc < nc^3 < 2^31
+  const int cx = (int)(pq - rq * un), cy = (int)(rq % un), cz = (int)(rq / un);
   const int slice = blockIdx.y;
   const Coef<T> cf = coef_of(coef, cls, slice, J, K, level);
   const int64_t nn = (int64_t)nf * nf;
@@ -147,7 +151,8 @@ __global__ void __launch_bounds__(256) k_prolong_add3(T* __restrict__ x, const T
   const int64_t N3 = (int64_t)nf * nf * nf;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= N3) return;
-  const int ix = (int)(p % nf), iy = (int)((p / nf) % nf), iz = (int)(p / ((int64_t)nf * nf));
+  const unsigned pq = (unsigned)p, un = (unsigned)nf, rq = pq / un;  // p < nf^3 < 2^31
+  const int ix = (int)(pq - rq * un), iy = (int)(rq % un), iz = (int)(rq / un);
   const int nc = (nf - 1) / 2;
   const int slice = blockIdx.y;
   x[(int64_t)slice * N3 + p] += prolong_value3<T>(xc + (int64_t)slice * nc * nc * nc, nc, ix + 1, iy + 1, iz + 1);

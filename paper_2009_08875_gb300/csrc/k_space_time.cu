@@ -58,18 +58,20 @@ __device__ __forceinline__ T mass_of(const Sums<T>& v, const Stencil7<T>& sm) {
   return stiff_of(v, sm);
 }
 
-// grid coordinates of interior index p
+// grid coordinates of interior index p (p < n^DIM < 2^31: 32-bit unsigned division, a fraction of
+// the cost of 64-bit division)
 template <int DIM>
 __device__ __forceinline__ void coords_of(int64_t p, int n, int& ix, int& iy, int& iz) {
+  const unsigned q = (unsigned)p, un = (unsigned)n;
   if (DIM == 2) {
-    iy = (int)(p / n);
-    ix = (int)(p - (int64_t)iy * n);
+    iy = (int)(q / un);
+    ix = (int)(q - (unsigned)iy * un);
     iz = 0;
   } else {
-    const int64_t r = p / n;
-    ix = (int)(p - r * n);
-    iz = (int)(r / n);
-    iy = (int)(r - (int64_t)iz * n);
+    const unsigned r = q / un;
+    ix = (int)(q - r * un);
+    iz = (int)(r / un);
+    iy = (int)(r - (unsigned)iz * un);
   }
 }
 
