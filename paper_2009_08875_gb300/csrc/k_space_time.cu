@@ -229,6 +229,168 @@ __global__ void __launch_bounds__(256) k_apply_A(const T* __restrict__ X, T* __r
 }
 
 // ---------------------------------------------------------------------------------------
+// The same stencils on the square (and the L-shape) with each thread computing QB consecutive
+// points of one grid row: the three grid rows it needs are read once for all QB points (16 loads
+// per input for 4 points instead of 28), and the grid coordinates come from the block indices.
+// Same neighbour sums in the same order as load_nbr.
+// ---------------------------------------------------------------------------------------
+constexpr int QB = 4;     // points per thread
+constexpr int kBT = 128;  // threads per block: 512 columns of one grid row
+
+template <typename T>
+struct RowBlock {  // the neighbour sums of the QB points (ix0 .. ix0 + QB - 1, iy)
+  Sums<T> v[QB];
+};
+
+template <typename T>
+__device__ __forceinline__ RowBlock<T> load_rows(const T* __restrict__ u, int ix0, int iy, int n) {
+  // rows iy - 1 (columns ix0 - 1 .. ix0 + QB - 1), iy (ix0 - 1 .. ix0 + QB), iy + 1 (ix0 .. ix0 + QB)
+  T lo[QB + 1], mid[QB + 2], hi[QB + 1];
+  const bool ym = iy > 0, yp = iy < n - 1;
+  const T* r0 = u + (int64_t)iy * n;
+#pragma unroll
+  for (int q = 0; q < QB + 2; ++q) {
+    const int c = ix0 - 1 + q;
+    const bool cin = c >= 0 && c < n;
+    mid[q] = cin ? r0[c] : T(0);
+    if (q < QB + 1) lo[q] = (cin && ym) ? r0[c - n] : T(0);
+    if (q >= 1) hi[q - 1] = (cin && yp) ? r0[c + n] : T(0);
+  }
+  RowBlock<T> b;
+#pragma unroll
+  for (int q = 0; q < QB; ++q) {
+    // point ix0 + q: west mid[q], centre mid[q + 1], east mid[q + 2]; south lo[q + 1], north
+    // hi[q]; (1,1) hi[q + 1]; (-1,-1) lo[q]
+    b.v[q].c = mid[q + 1];
+    b.v[q].s1 = mid[q] + mid[q + 2];
+    b.v[q].s2 = lo[q + 1] + hi[q];
+    b.v[q].s3 = hi[q + 1] + lo[q];
+  }
+  return b;
+}
+
+// Z_i = M X1_i + A X2_i (+ M row0 on row 0), as k_epilogue (DIM 2); grid (columns / 512, n, slices
+// of all problems)
+template <typename T>
+__global__ void __launch_bounds__(kBT) k_epilogue_rows2(const T* __restrict__ X1, const T* __restrict__ X2,
+                                                        const T* __restrict__ row0, int64_t row0_stride,
+                                                        T* __restrict__ Z, int n, int Nt, Stencil7<T> sm,
+                                                        Stencil7<T> sa, int lshape) {
+  const int ix0 = QB * (blockIdx.x * kBT + threadIdx.x);
+  if (ix0 >= n) return;
+  const int iy = blockIdx.y;
+  const int slice = blockIdx.z;  // problem slice / Nt, time row slice % Nt
+  const int64_t off = (int64_t)slice * n * n;
+  const RowBlock<T> a = load_rows(X1 + off, ix0, iy, n);
+  const RowBlock<T> c = load_rows(X2 + off, ix0, iy, n);
+  T z[QB];
+#pragma unroll
+  for (int q = 0; q < QB; ++q) z[q] = mass_of<T, 2>(a.v[q], sm) + stiff_of(c.v[q], sa);
+  if (slice % Nt == 0 && row0 != nullptr) {
+    const RowBlock<T> r = load_rows(row0 + (slice / Nt) * row0_stride, ix0, iy, n);
+#pragma unroll
+    for (int q = 0; q < QB; ++q) z[q] += mass_of<T, 2>(r.v[q], sm);
+  }
+  T* zr = Z + off + (int64_t)iy * n;
+#pragma unroll
+  for (int q = 0; q < QB; ++q) {
+    const int ix = ix0 + q;
+    if (ix < n) zr[ix] = outside_domain(ix, iy, n, lshape) ? T(0) : z[q];
+  }
+}
+
+// The time mix of k_timemix (DIM 2; problem blockIdx.z / nchunk, rows of chunk blockIdx.z % nchunk)
+// with QB points per thread; the stencil results of rows i - 1, i, i + 1 roll in registers.
+template <typename T>
+__global__ void __launch_bounds__(kBT) k_timemix_rows2(const T* __restrict__ U, T* __restrict__ Y1, T* __restrict__ Y2,
+                                                       int n, int Nt, int chunk, int nchunk, Stencil7<T> sm,
+                                                       Stencil7<T> sa, TimeConsts<T> tk, int mode, int lshape) {
+  const int ix0 = QB * (blockIdx.x * kBT + threadIdx.x);
+  if (ix0 >= n) return;
+  const int iy = blockIdx.y;
+  const int prob = blockIdx.z / nchunk;
+  const int i0 = (blockIdx.z - prob * nchunk) * chunk;
+  const int i1 = min(Nt, i0 + chunk);
+  const int64_t N = (int64_t)n * n;
+  const int64_t poff = (int64_t)prob * Nt * N;
+  U += poff;
+  Y1 += poff;
+  Y2 += poff;
+  T um_m[QB], ua_m[QB], um_c[QB], ua_c[QB], um_p[QB], ua_p[QB];
+#pragma unroll
+  for (int q = 0; q < QB; ++q) um_m[q] = ua_m[q] = um_p[q] = ua_p[q] = T(0);
+  if (i0 > 0) {
+    const RowBlock<T> v = load_rows(U + (int64_t)(i0 - 1) * N, ix0, iy, n);
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      um_m[q] = mass_of<T, 2>(v.v[q], sm);
+      ua_m[q] = stiff_of(v.v[q], sa);
+    }
+  }
+  {
+    const RowBlock<T> v = load_rows(U + (int64_t)i0 * N, ix0, iy, n);
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      um_c[q] = mass_of<T, 2>(v.v[q], sm);
+      ua_c[q] = stiff_of(v.v[q], sa);
+    }
+  }
+  for (int i = i0; i < i1; ++i) {
+    if (i + 1 < Nt) {
+      const RowBlock<T> v = load_rows(U + (int64_t)(i + 1) * N, ix0, iy, n);
+#pragma unroll
+      for (int q = 0; q < QB; ++q) {
+        um_p[q] = mass_of<T, 2>(v.v[q], sm);
+        ua_p[q] = mode == 0 ? stiff_of(v.v[q], sa) : T(0);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < QB; ++q) um_p[q] = ua_p[q] = T(0);
+    }
+    T* y1 = Y1 + (int64_t)i * N + (int64_t)iy * n;
+    T* y2 = Y2 + (int64_t)i * N + (int64_t)iy * n;
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      T a, c;
+      if (mode == 0) {
+        a = tri_dot(tri_At(i, Nt, tk), um_m[q], um_c[q], um_p[q]) + tri_dot(tri_LT<T>(i, Nt), ua_m[q], ua_c[q], ua_p[q]);
+        c = tri_dot(tri_L<T>(i, Nt), um_m[q], um_c[q], um_p[q]) + tri_dot(tri_Mt(i, Nt, tk), ua_m[q], ua_c[q], ua_p[q]);
+      } else {
+        a = tri_dot(tri_LT<T>(i, Nt), um_m[q], um_c[q], um_p[q]);
+        c = tri_dot(tri_Mt(i, Nt, tk), um_m[q], um_c[q], um_p[q]);
+      }
+      const int ix = ix0 + q;
+      if (ix < n) {
+        const bool out = outside_domain(ix, iy, n, lshape);  // nodes outside the domain stay zero
+        y1[ix] = out ? T(0) : a;
+        y2[ix] = out ? T(0) : c;
+      }
+      um_m[q] = um_c[q];
+      ua_m[q] = ua_c[q];
+      um_c[q] = um_p[q];
+      ua_c[q] = ua_p[q];
+    }
+  }
+}
+
+// Y = A_x X on each slice, as k_apply_A (DIM 2)
+template <typename T>
+__global__ void __launch_bounds__(kBT) k_apply_A_rows2(const T* __restrict__ X, T* __restrict__ Y, int n,
+                                                       Stencil7<T> sa, int lshape) {
+  const int ix0 = QB * (blockIdx.x * kBT + threadIdx.x);
+  if (ix0 >= n) return;
+  const int iy = blockIdx.y;
+  const int64_t off = (int64_t)blockIdx.z * n * n;
+  const RowBlock<T> a = load_rows(X + off, ix0, iy, n);
+  T* yr = Y + off + (int64_t)iy * n;
+#pragma unroll
+  for (int q = 0; q < QB; ++q) {
+    const int ix = ix0 + q;
+    if (ix < n) yr[ix] = outside_domain(ix, iy, n, lshape) ? T(0) : stiff_of(a.v[q], sa);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // three-point wavelet lifting along time, in-place row order (level-j nodes at rows that are
 // multiples of 2^(J-j)).  Stage j maps level j (2^j + 1 nodes, coefficients c) plus the
 // level-(j+1) wavelet coefficients d (2^j of them) to level j+1, M_j = [P_j | Q_j]:
@@ -328,7 +490,12 @@ cudaError_t launch_timemix(const st_handle_s* h, int nb, int mode, const T* U, T
     k_timemix<T, 3><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, 0, (int)h->Nt, 0,
                                                  chunk, fine_M<T>(h),
                                                  fine_A<T>(h), time_consts<T>(h->J), mode, 0);
-  else
+  else if (sizeof(T) == 4) {  // binary32: row blocks (binary64 is bound by its arithmetic either way)
+    const int nchunk = (int)((h->Nt + chunk - 1) / chunk);
+    k_timemix_rows2<T><<<dim3((n + QB * kBT - 1) / (QB * kBT), n, (unsigned)(nchunk * nb)), kBT, 0, h->stream>>>(
+        U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, chunk, nchunk, fine_M<T>(h), fine_A<T>(h),
+        time_consts<T>(h->J), mode, h->domain);
+  } else
     k_timemix<T, 2><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, 0, (int)h->Nt, 0,
                                                  chunk, fine_M<T>(h),
                                                  fine_A<T>(h), time_consts<T>(h->J), mode, h->domain);
@@ -344,6 +511,9 @@ cudaError_t launch_epilogue(const st_handle_s* h, int nb, const T* X, const T* r
   if (h->domain == 2)
     k_epilogue<T, 3><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt, 0,
                                                   fine_M<T>(h), fine_A<T>(h), 0);
+  else if (sizeof(T) == 4)  // binary32: row blocks (binary64 is bound by its arithmetic either way)
+    k_epilogue_rows2<T><<<dim3((n + QB * kBT - 1) / (QB * kBT), n, (unsigned)(nb * h->Nt)), kBT, 0, h->stream>>>(
+        X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt, fine_M<T>(h), fine_A<T>(h), h->domain);
   else
     k_epilogue<T, 2><<<grid, 256, 0, h->stream>>>(X, X + nb * h->Nt * h->Nx, row0, row0_stride, Z, n, (int)h->Nt, 0,
                                                   fine_M<T>(h), fine_A<T>(h), h->domain);
@@ -358,6 +528,9 @@ cudaError_t launch_apply_A(const st_handle_s* h, int nrows, const T* X, T* Y) {
   dim3 grid((unsigned)((N + 255) / 256), nrows);
   if (h->domain == 2)
     k_apply_A<T, 3><<<grid, 256, 0, h->stream>>>(X, Y, n, fine_A<T>(h), 0);
+  else if (sizeof(T) == 4)
+    k_apply_A_rows2<T><<<dim3((n + QB * kBT - 1) / (QB * kBT), n, (unsigned)nrows), kBT, 0, h->stream>>>(
+        X, Y, n, fine_A<T>(h), h->domain);
   else
     k_apply_A<T, 2><<<grid, 256, 0, h->stream>>>(X, Y, n, fine_A<T>(h), h->domain);
   count_launch(h);
