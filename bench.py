@@ -56,9 +56,10 @@ NCU_TRAFFIC = {
 # slices of the full launch; keyed by the SHA-256 of the header's text (null once it changes):
 # profiles/k_gs_wide_f32_Kx_K9_J6.md
 NCU_TRAFFIC_WIDE = {
-    "2851b3e5abd564abc3b8e30b3f3c37305296bd797f5db645c10392478ad1d161": {
-        "K_x_post_smoothing_with_prolongation": (305.531648e6 + 105.769216e6) * 1026 / 130,
-        "K_x_pre_smoothing_with_restriction": (271.856384e6 + 129.012480e6) * 1026 / 130,
+    "e6085d72eb970998c9c6e508f9c85ee2f0e30b5f66660ee524d9ef5efaf761df": {
+        "K_x_pre_smoothing_with_scaling_and_restriction": (136.079616e6 + 244.735744e6) * 1026 / 130,
+        "K_x_post_smoothing_with_prolongation": (305.527552e6 + 105.818368e6) * 1026 / 130,
+        "K_x_pre_smoothing_with_restriction": (271.841792e6 + 128.954112e6) * 1026 / 130,
     },
 }
 KERNEL_OF = {"tiles": ("k_gs_sweep", "k_mg.cu"), "wavefront": ("k_gs_wave", "k_mg.cu"),

@@ -420,18 +420,25 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
     // b' of the tile's points for the launches that follow, one warp row at a time with lane l
     // at the columns l + 32 j (coalesced), read from the pair layout in shared memory before the
     // residual overwrites it
-    const float* bf = reinterpret_cast<const float*>(bsh);
+    const float* bf = reinterpret_cast<const float*>(bsh) + ry0 * 192;
+    // column lane + 32 j of a row is element e = c mod 6 of lane c / 6: its float index in the
+    // pair layout, a lane constant
+    int sp[6];
+    bool in[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int c = lane + 32 * j, e = c % 6;
+      sp[j] = 2 * ((e % 3) * 32 + c / 6) + e / 3;
+      in[j] = x0 + c >= tx0 && x0 + c < tx1;
+    }
 #pragma unroll 1
     for (int r = 0; r < R; ++r) {
       const int gy = gyw + r;
       if (gy < ty0 || gy >= ty1) continue;  // warp-uniform
-      G* row = bsc + off + (int64_t)gy * n;
+      G* row = bsc + off + (int64_t)gy * n + x0 + lane;
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const int c = lane + 32 * j, e = c % 6;
-        const int gx = x0 + c;
-        if (gx >= tx0 && gx < tx1) row[gx] = G(bf[(ry0 + r) * 192 + 2 * ((e % 3) * 32 + c / 6) + e / 3]);
-      }
+      for (int j = 0; j < 6; ++j)
+        if (in[j]) row[32 * j] = G(bf[r * 192 + sp[j]]);
     }
   }
   if (RESTR) {

@@ -299,80 +299,6 @@ __global__ void __launch_bounds__(kBT) k_epilogue_rows2(const T* __restrict__ X1
   }
 }
 
-// The time mix of k_timemix (DIM 2; problem blockIdx.z / nchunk, rows of chunk blockIdx.z % nchunk)
-// with QB points per thread; the stencil results of rows i - 1, i, i + 1 roll in registers.
-template <typename T>
-__global__ void __launch_bounds__(kBT) k_timemix_rows2(const T* __restrict__ U, T* __restrict__ Y1, T* __restrict__ Y2,
-                                                       int n, int Nt, int chunk, int nchunk, Stencil7<T> sm,
-                                                       Stencil7<T> sa, TimeConsts<T> tk, int mode, int lshape) {
-  const int ix0 = QB * (blockIdx.x * kBT + threadIdx.x);
-  if (ix0 >= n) return;
-  const int iy = blockIdx.y;
-  const int prob = blockIdx.z / nchunk;
-  const int i0 = (blockIdx.z - prob * nchunk) * chunk;
-  const int i1 = min(Nt, i0 + chunk);
-  const int64_t N = (int64_t)n * n;
-  const int64_t poff = (int64_t)prob * Nt * N;
-  U += poff;
-  Y1 += poff;
-  Y2 += poff;
-  T um_m[QB], ua_m[QB], um_c[QB], ua_c[QB], um_p[QB], ua_p[QB];
-#pragma unroll
-  for (int q = 0; q < QB; ++q) um_m[q] = ua_m[q] = um_p[q] = ua_p[q] = T(0);
-  if (i0 > 0) {
-    const RowBlock<T> v = load_rows(U + (int64_t)(i0 - 1) * N, ix0, iy, n);
-#pragma unroll
-    for (int q = 0; q < QB; ++q) {
-      um_m[q] = mass_of<T, 2>(v.v[q], sm);
-      ua_m[q] = stiff_of(v.v[q], sa);
-    }
-  }
-  {
-    const RowBlock<T> v = load_rows(U + (int64_t)i0 * N, ix0, iy, n);
-#pragma unroll
-    for (int q = 0; q < QB; ++q) {
-      um_c[q] = mass_of<T, 2>(v.v[q], sm);
-      ua_c[q] = stiff_of(v.v[q], sa);
-    }
-  }
-  for (int i = i0; i < i1; ++i) {
-    if (i + 1 < Nt) {
-      const RowBlock<T> v = load_rows(U + (int64_t)(i + 1) * N, ix0, iy, n);
-#pragma unroll
-      for (int q = 0; q < QB; ++q) {
-        um_p[q] = mass_of<T, 2>(v.v[q], sm);
-        ua_p[q] = mode == 0 ? stiff_of(v.v[q], sa) : T(0);
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < QB; ++q) um_p[q] = ua_p[q] = T(0);
-    }
-    T* y1 = Y1 + (int64_t)i * N + (int64_t)iy * n;
-    T* y2 = Y2 + (int64_t)i * N + (int64_t)iy * n;
-#pragma unroll
-    for (int q = 0; q < QB; ++q) {
-      T a, c;
-      if (mode == 0) {
-        a = tri_dot(tri_At(i, Nt, tk), um_m[q], um_c[q], um_p[q]) + tri_dot(tri_LT<T>(i, Nt), ua_m[q], ua_c[q], ua_p[q]);
-        c = tri_dot(tri_L<T>(i, Nt), um_m[q], um_c[q], um_p[q]) + tri_dot(tri_Mt(i, Nt, tk), ua_m[q], ua_c[q], ua_p[q]);
-      } else {
-        a = tri_dot(tri_LT<T>(i, Nt), um_m[q], um_c[q], um_p[q]);
-        c = tri_dot(tri_Mt(i, Nt, tk), um_m[q], um_c[q], um_p[q]);
-      }
-      const int ix = ix0 + q;
-      if (ix < n) {
-        const bool out = outside_domain(ix, iy, n, lshape);  // nodes outside the domain stay zero
-        y1[ix] = out ? T(0) : a;
-        y2[ix] = out ? T(0) : c;
-      }
-      um_m[q] = um_c[q];
-      ua_m[q] = ua_c[q];
-      um_c[q] = um_p[q];
-      ua_c[q] = ua_p[q];
-    }
-  }
-}
-
 // Y = A_x X on each slice, as k_apply_A (DIM 2)
 template <typename T>
 __global__ void __launch_bounds__(kBT) k_apply_A_rows2(const T* __restrict__ X, T* __restrict__ Y, int n,
@@ -490,12 +416,8 @@ cudaError_t launch_timemix(const st_handle_s* h, int nb, int mode, const T* U, T
     k_timemix<T, 3><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, 0, (int)h->Nt, 0,
                                                  chunk, fine_M<T>(h),
                                                  fine_A<T>(h), time_consts<T>(h->J), mode, 0);
-  else if (sizeof(T) == 4) {  // binary32: row blocks (binary64 is bound by its arithmetic either way)
-    const int nchunk = (int)((h->Nt + chunk - 1) / chunk);
-    k_timemix_rows2<T><<<dim3((n + QB * kBT - 1) / (QB * kBT), n, (unsigned)(nchunk * nb)), kBT, 0, h->stream>>>(
-        U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, chunk, nchunk, fine_M<T>(h), fine_A<T>(h),
-        time_consts<T>(h->J), mode, h->domain);
-  } else
+  else  // (a row-blocked binary32 variant, four points a thread, measured slower: fewer threads,
+        // each walking its chunk of time rows)
     k_timemix<T, 2><<<grid, 256, 0, h->stream>>>(U, Y, Y + nb * h->Nt * h->Nx, n, (int)h->Nt, 0, (int)h->Nt, 0,
                                                  chunk, fine_M<T>(h),
                                                  fine_A<T>(h), time_consts<T>(h->J), mode, h->domain);
