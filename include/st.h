@@ -387,10 +387,11 @@ st_status st_sharded_solve(st_handle h, const st_comm* comm, int rank, int nrank
  * row segments walked by separate warps, and register tiles, whose 96-column regions sit in the
  * registers of a block's warps (binary32: 12 rows x 8 warps, 8 x 12 or 6 x 16, the autotuner
  * trying each; binary64 and double-float: 6 rows x 8 warps).  Binary32 has one more register
- * block shape on the unit square: 192-column regions of 12 rows x 8 warps placed inside the
- * grid, whose lanes update two points of one colour with one paired binary32 instruction, and
- * whose last pre-smoothing launch of a V-cycle also forms and restricts the residual, on the
- * levels with 2^k - 1 >= 192 (elsewhere it runs as the first shape).
+ * block shape on the unit square: regions placed inside the grid, 192 columns x 96 rows of
+ * whole warps on the levels with 2^k - 1 >= 192 and 96 x 96 of half-warps on those with
+ * 2^k - 1 >= 96, whose lanes update two points of one colour with one paired binary32
+ * instruction, and whose last pre-smoothing launch of a V-cycle also forms and restricts the
+ * residual (on smaller levels it runs as the first shape).
  * For every multigrid level
  * above the coarsest, for binary64 and binary32 and for K_x (no mass couplings, 2 B N_t slices)
  * and K_l (mass couplings, B N_t slices), this times one pre-smoothing launch of each kernel (the
@@ -407,8 +408,8 @@ st_status st_autotune(st_handle h, float* times_ms);
 /* Forces one Gauss-Seidel kernel on every level of this handle: kind 0 shared-memory tiles (the
  * state after set-up), 1 register wavefront, 2, 3, 4 register tiles of block shape 0, 1, 2 (in
  * binary32 12 rows x 8 warps, 8 x 12, 6 x 16; binary64 and double-float always 6 x 8), 5 the
- * binary32 192-column regions with paired arithmetic (unit square, levels with 2^k - 1 >= 192;
- * shape 0 elsewhere and in binary64 and double-float).  All give bitwise the same sweeps and
+ * binary32 regions with paired arithmetic (unit square, levels with 2^k - 1 >= 96; shape 0
+ * elsewhere and in binary64 and double-float).  All give bitwise the same sweeps and
  * coarse right-hand sides.  Returns ST_ERR_ARG for any other kind. */
 st_status st_set_smoother(st_handle h, int kind);
 

@@ -59,7 +59,7 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // pair layout (zeros past the region).  zl / zr: the lane's west / east neighbour across the
 // region's edge is the grid boundary (a zero).  r and m are constants once inlined in an
 // unrolled loop.
-template <int R, bool DIAG>
+template <int NL, int R, bool DIAG>
 __device__ __forceinline__ float2 pair_update(const float2 (&x)[R][3], int r, int m, const float2* __restrict__ bs,
                                               const float2* __restrict__ below, const float2* __restrict__ above,
                                               int lane, bool zl, bool zr, float2 nax, float2 nay, float2 ndg) {
@@ -69,52 +69,52 @@ __device__ __forceinline__ float2 pair_update(const float2 (&x)[R][3], int r, in
   // west and east pairs (columns 6 l + m -+ 1 and 6 l + m + 3 -+ 1)
   float2 W, E;
   if (m == 0) {
-    const float t = shfl_up(x[r][2].y, 1);
+    const float t = __shfl_up_sync(0xffffffffu, x[r][2].y, 1, NL);
     W = make_float2(zl ? 0.f : t, x[r][2].x);
   } else {
     W = x[r][(m + 2) % 3];
   }
   if (m == 2) {
-    const float t = shfl_down(x[r][0].x, 1);
+    const float t = __shfl_down_sync(0xffffffffu, x[r][0].x, 1, NL);
     E = make_float2(x[r][0].y, zr ? 0.f : t);
   } else {
     E = x[r][(m + 1) % 3];
   }
-  const float2 S = (r > 0) ? x[rs][m] : below[m * 32 + lane];
-  const float2 N = (r < kR1) ? x[rn][m] : above[m * 32 + lane];
-  float2 v = fma2(nax, add2(W, E), bs[r * 96 + m * 32 + lane]);
+  const float2 S = (r > 0) ? x[rs][m] : below[m * NL + lane];
+  const float2 N = (r < kR1) ? x[rn][m] : above[m * NL + lane];
+  float2 v = fma2(nax, add2(W, E), bs[r * 3 * NL + m * NL + lane]);
   v = fma2(nay, add2(S, N), v);
   if (DIAG) {
     // (1,1) neighbours: the row above shifted east; (-1,-1): the row below shifted west
     float2 NE, SW;
     if (r < kR1) {
       if (m == 2) {
-        const float t = shfl_down(x[rn][0].x, 1);
+        const float t = __shfl_down_sync(0xffffffffu, x[rn][0].x, 1, NL);
         NE = make_float2(x[rn][0].y, zr ? 0.f : t);
       } else {
         NE = x[rn][(m + 1) % 3];
       }
     } else {
       if (m == 2) {
-        const float t = above[lane + 1].x;  // lane 31 reads the next pair's slot: unused (zr or halo)
+        const float t = above[lane + 1].x;  // the last lane reads the next pair's slot: unused (zr or halo)
         NE = make_float2(above[lane].y, zr ? 0.f : t);
       } else {
-        NE = above[((m + 1) % 3) * 32 + lane];
+        NE = above[((m + 1) % 3) * NL + lane];
       }
     }
     if (r > 0) {
       if (m == 0) {
-        const float t = shfl_up(x[rs][2].y, 1);
+        const float t = __shfl_up_sync(0xffffffffu, x[rs][2].y, 1, NL);
         SW = make_float2(zl ? 0.f : t, x[rs][2].x);
       } else {
         SW = x[rs][(m + 2) % 3];
       }
     } else {
       if (m == 0) {
-        const float t = below[64 + lane - 1].y;  // lane 0 reads the previous pair's slot: unused (zl or halo)
-        SW = make_float2(zl ? 0.f : t, below[64 + lane].x);
+        const float t = below[2 * NL + lane - 1].y;  // lane 0 reads the previous pair's slot: unused (zl or halo)
+        SW = make_float2(zl ? 0.f : t, below[2 * NL + lane].x);
       } else {
-        SW = below[((m + 2) % 3) * 32 + lane];
+        SW = below[((m + 2) % 3) * NL + lane];
       }
     }
     v = fma2(ndg, add2(NE, SW), v);
@@ -124,14 +124,14 @@ __device__ __forceinline__ float2 pair_update(const float2 (&x)[R][3], int r, in
 
 // One colour step on a warp's R rows.  P is the active element of the warp's first row (row r:
 // m(r) = (P - r) mod 3); the step overwrites the active pair of every row with its update value.
-template <int R, bool DIAG, int P>
+template <int NL, int R, bool DIAG, int P>
 __device__ __forceinline__ void wide_step(float2 (&x)[R][3], const float2* __restrict__ bs,
                                           const float2* __restrict__ below, const float2* __restrict__ above,
                                           int lane, bool zl, bool zr, float2 nax, float2 nay, float2 ndg) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int m = ((P - (r % 3)) + 3) % 3;  // a constant once the loop is unrolled
-    x[r][m] = pair_update<R, DIAG>(x, r, m, bs, below, above, lane, zl, zr, nax, nay, ndg);
+    x[r][m] = pair_update<NL, R, DIAG>(x, r, m, bs, below, above, lane, zl, zr, nax, nay, ndg);
   }
 }
 
@@ -140,7 +140,7 @@ __device__ __forceinline__ void wide_step(float2 (&x)[R][3], const float2* __res
 // read only for that row's residual, and before its slot is overwritten).  (The points of the
 // last colour step have residual exactly 0, but skipping them in these unrolled rows measured
 // slower than forming them.)
-template <int R, bool DIAG>
+template <int NL, int R, bool DIAG>
 __device__ __forceinline__ void wide_residual(const float2 (&x)[R][3], float2* __restrict__ bs,
                                               const float2* __restrict__ below, const float2* __restrict__ above,
                                               int lane, bool zl, bool zr, float2 nax, float2 nay, float2 ndg) {
@@ -149,8 +149,8 @@ __device__ __forceinline__ void wide_residual(const float2 (&x)[R][3], float2* _
   for (int r = 0; r < R; ++r) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const float2 v = pair_update<R, DIAG>(x, r, k, bs, below, above, lane, zl, zr, nax, nay, ndg);
-      bs[r * 96 + k * 32 + lane] = fma2(x[r][k], mone, v);  // v - x, rounded once
+      const float2 v = pair_update<NL, R, DIAG>(x, r, k, bs, below, above, lane, zl, zr, nax, nay, ndg);
+      bs[r * 3 * NL + k * NL + lane] = fma2(x[r][k], mone, v);  // v - x, rounded once
     }
   }
 }
@@ -162,21 +162,21 @@ __device__ __forceinline__ void wide_residual(const float2 (&x)[R][3], float2* _
 // (odd grid rows), and in a lane's columns the elements PA, PA + 2, PA + 4 (odd grid columns), so
 // every shared-memory offset is a constant.  rs: the residuals of the region in pair layout
 // (float index 2 ((e mod 3) 32 + lane) + e / 3 of element e of a lane in a row of 192 floats).
-template <typename G, int R, int NWARP, int PA, int PY>
+template <typename G, int NL, int R, int RH, int PA, int PY>
 __device__ __forceinline__ void wide_restrict(const float* __restrict__ rs, G* __restrict__ bcs, int nc, int warp,
                                               int lane, int gyw, int gx_lane, int tx0, int tx1, int ty0, int ty1,
                                               float rho, float hrho) {
   auto at = [&](int row, int e) -> float {  // residual at row `row` of the region, element e of this lane
-    row = row < 0 ? 0 : (row >= NWARP * R ? NWARP * R - 1 : row);  // clamped: only for centres outside the tile
+    row = row < 0 ? 0 : (row >= RH ? RH - 1 : row);  // clamped: only for centres outside the tile
     const int ln = e < 0 ? lane - 1 : (e > 5 ? lane + 1 : lane);
     const int ee = e < 0 ? 5 : (e > 5 ? 0 : e);
-    return rs[row * 192 + 2 * ((ee % 3) * 32 + ln) + ee / 3];
+    return rs[row * 6 * NL + 2 * ((ee % 3) * NL + ln) + ee / 3];
   };
   const int ry0 = warp * R;
 #pragma unroll
   for (int r = PY; r < R; r += 2) {
     const int gy = gyw + r;
-    if (gy < ty0 || gy >= ty1) continue;  // warp-uniform
+    if (gy < ty0 || gy >= ty1) continue;  // uniform in the row group
     const int cy = (gy - 1) >> 1;
 #pragma unroll
     for (int e = PA; e < 6; e += 2) {
@@ -254,12 +254,12 @@ __device__ __forceinline__ void wide_add_prol_direct(float2 (&x)[R][3], const G*
 }
 
 // The first colour step of a sweep from x = 0: every neighbour is zero, so x = b'.
-template <int R, int P>
+template <int NL, int R, int P>
 __device__ __forceinline__ void wide_step_first(float2 (&x)[R][3], const float2* __restrict__ bs, int lane) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int m = ((P - (r % 3)) + 3) % 3;
-    x[r][m] = bs[r * 96 + m * 32 + lane];
+    x[r][m] = bs[r * 3 * NL + m * NL + lane];
   }
 }
 
@@ -280,18 +280,20 @@ __device__ __forceinline__ void wide_tile(int b, int nb, int n, int W, int M, in
   o = min(max(t - M, 0), n - W);
 }
 
-// dynamic shared memory of one block: b' (RH rows x 96 pairs), the edge rows (2 parities x NWARP
-// warps x 2 rows x 96 pairs; also the coarse values of the prolongation before the first step),
-// and a zero row of 96 pairs
-template <int R, int NWARP>
+// dynamic shared memory of one block of NWARP warps in row groups of NL lanes (NVW = 32 NWARP /
+// NL groups of R rows, RH = NVW R region rows): b' (RH rows x 3 NL pairs), the edge rows (2
+// parities x NVW groups x 2 rows x 3 NL pairs; also the coarse values of the prolongation before
+// the first step), and a zero row of 3 NL pairs
+template <int NL, int R, int NWARP>
 constexpr size_t wide_smem() {
-  return sizeof(float2) * (size_t)(NWARP * R * 96 + 2 * NWARP * 2 * 96 + 96);
+  constexpr int NVW = 32 * NWARP / NL;
+  return sizeof(float2) * (size_t)(NVW * R * 3 * NL + 2 * NVW * 2 * 3 * NL + 3 * NL);
 }
 
 // The kernel body for one parity class of block regions: PA = (x0 + 1) mod 2, PY = (y0 + 1) mod 2
 // fix the coarse offsets of the prolongation (PROL); every class is its own code path, so the
 // registers of one do not add to another's.
-template <typename G, int NSW, int R, int NWARP, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, bool RESTR,
+template <typename G, int NL, int NSW, int R, int NWARP, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, bool RESTR,
           bool SCALE, int PA, int PY>
 __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __restrict__ x_in, const G* __restrict__ b,
                                           const G* __restrict__ xc, G* __restrict__ bc,
@@ -299,37 +301,40 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
                                           const Coef<float>* __restrict__ coef, int coef_class, int J, int K,
                                           int level, int reverse, int zero_init) {
   constexpr int H = 3 * NSW;
-  constexpr int RH = NWARP * R;  // region rows
+  // row groups of NL lanes (a warp, or half a warp): NVW groups of R rows; regions of W columns
+  constexpr int NVW = 32 * NWARP / NL, RH = NVW * R, W = 6 * NL, P3 = 3 * NL;
+  static_assert(NL == 32 || R % 3 == 0, "half-warp groups must share their colour-step branch: R % 3 == 0");
   // binary32 storage: b' may come by asynchronous copies, which frees the registers the direct
   // prolongation needs; bfloat16 storage stages the coarse values in shared memory
   constexpr bool kF32 = std::is_same<G, float>::value;
   // tile margin: H, and 2 more when the launch also restricts the residual (the residual at the
   // fine neighbours of the tile's coarse centres needs the iterate one point further out)
   constexpr int M = H + (RESTR ? 2 : 0);
-  constexpr int CW = kWW / 2 + 2, CH = RH / 2 + 2;  // coarse values under the region (PROL)
-  static_assert(CW * CH <= 2 * NWARP * 2 * 96 * 2, "coarse values fit in the edge-row space");
+  constexpr int CW = W / 2 + 2, CH = RH / 2 + 2;  // coarse values under the region (PROL)
+  static_assert(CW * CH <= 2 * NVW * 2 * P3 * 2, "coarse values fit in the edge-row space");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* bsh = reinterpret_cast<float2*>(smem_raw);  // [RH][3][32]
-  float2* edge = bsh + RH * 96;                        // [2][NWARP][2][3][32]
-  float2* zrow = edge + 2 * NWARP * 2 * 96;            // [3][32]
+  float2* bsh = reinterpret_cast<float2*>(smem_raw);  // [RH][3][NL]
+  float2* edge = bsh + RH * P3;                        // [2][NVW][2][3][NL]
+  float2* zrow = edge + 2 * NVW * 2 * P3;              // [3][NL]
   float* ct = reinterpret_cast<float*>(edge);          // [CH][CW] before the first step
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // lane within the row group, and the group ("warp" below)
+  const int lane = threadIdx.x % NL, warp = threadIdx.x / NL;
   const int slice = blockIdx.z;
   const int64_t off = (int64_t)slice * n * n;
   // the block's tile and its region, clamped into the grid
   int tx0, tx1, x0, ty0, ty1, y0;
-  wide_tile(blockIdx.x, gridDim.x, n, kWW, M, tx0, tx1, x0);
+  wide_tile(blockIdx.x, gridDim.x, n, W, M, tx0, tx1, x0);
   wide_tile(blockIdx.y, gridDim.y, n, RH, M, ty0, ty1, y0);
   const int ry0 = warp * R;
   const int gyw = y0 + ry0;       // grid row of the warp's first row
   const int cb = x0 + 6 * lane;   // grid column of the lane's element 0
   const bool zl = lane == 0 && x0 == 0;
-  const bool zr = lane == 31 && x0 + kWW == n;
+  const bool zr = lane == NL - 1 && x0 + W == n;
   const Coef<float> cf = slice_coef(coef, coef_class, slice, J, K, level);
   const float2 nax = make_float2(-cf.axs, -cf.axs), nay = make_float2(-cf.ays, -cf.ays);
   const float2 ndg = make_float2(-cf.dgs, -cf.dgs);
-  for (int i = threadIdx.x; i < 96; i += blockDim.x) zrow[i] = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < P3; i += blockDim.x) zrow[i] = make_float2(0.f, 0.f);
 
   // load: x into registers (0 from x = 0) and b' into shared memory, in the pair layout
   float2 x[R][3];
@@ -340,7 +345,7 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
     for (int r = 0; r < R; ++r) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        float2* d = &bsh[(ry0 + r) * 96 + k * 32 + lane];
+        float2* d = &bsh[(ry0 + r) * P3 + k * NL + lane];
         if constexpr ((ASYNCB || (PROL && PDIR)) && kF32) {
           // binary32: asynchronous 4-byte copies straight into the pair slots (no registers held)
           const unsigned dx = (unsigned)__cvta_generic_to_shared(&d->x);
@@ -371,11 +376,11 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
     const int nc = (n - 1) / 2;
     const int Ib = (x0 + 1) >> 1, Jb = (y0 + 1) >> 1;
     const G* xcs = xc + (int64_t)slice * nc * nc;
-    for (int jj = warp; jj < CH; jj += NWARP) {
+    for (int jj = warp; jj < CH; jj += NVW) {
       const int Jc = Jb + jj;
       const bool rowok = Jc >= 1 && Jc <= nc;
       const G* src = xcs + (int64_t)(Jc - 1) * nc - 1;  // indexed by the 1-based I
-      for (int ii = lane; ii < CW; ii += 32) {
+      for (int ii = lane; ii < CW; ii += NL) {
         const int I = Ib + ii;
         ct[jj * CW + ii] = (rowok && I >= 1 && I <= nc) ? float(src[I]) : 0.f;
       }
@@ -385,60 +390,60 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
     __syncthreads();  // ct (the edge-row space) is read before the first step writes it
   }
 
-  const float2* bw = bsh + ry0 * 96;
+  const float2* bw = bsh + ry0 * P3;
 #pragma unroll 1
   for (int t = 0; t < 3 * NSW; ++t) {
     const int colour = reverse ? 2 - t % 3 : t % 3;
-    float2* ed = edge + ((t & 1) * NWARP + warp) * 192;
+    float2* ed = edge + ((t & 1) * NVW + warp) * 2 * P3;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      ed[k * 32 + lane] = x[0][k];
-      ed[96 + k * 32 + lane] = x[R - 1][k];
+      ed[k * NL + lane] = x[0][k];
+      ed[P3 + k * NL + lane] = x[R - 1][k];
     }
     __syncthreads();
-    const float2* below = warp > 0 ? edge + ((t & 1) * NWARP + warp - 1) * 192 + 96 : zrow;
-    const float2* above = warp < NWARP - 1 ? edge + ((t & 1) * NWARP + warp + 1) * 192 : zrow;
+    const float2* below = warp > 0 ? edge + ((t & 1) * NVW + warp - 1) * 2 * P3 + P3 : zrow;
+    const float2* above = warp < NVW - 1 ? edge + ((t & 1) * NVW + warp + 1) * 2 * P3 : zrow;
     int P = (colour - 2 - gyw - x0) % 3;  // active element in the warp's first row
     P += (P < 0) ? 3 : 0;
     if (!PROL && zero_init && t == 0) {
       if (P == 0)
-        wide_step_first<R, 0>(x, bw, lane);
+        wide_step_first<NL, R, 0>(x, bw, lane);
       else if (P == 1)
-        wide_step_first<R, 1>(x, bw, lane);
+        wide_step_first<NL, R, 1>(x, bw, lane);
       else
-        wide_step_first<R, 2>(x, bw, lane);
+        wide_step_first<NL, R, 2>(x, bw, lane);
     } else if (P == 0) {
-      wide_step<R, DIAG, 0>(x, bw, below, above, lane, zl, zr, nax, nay, ndg);
+      wide_step<NL, R, DIAG, 0>(x, bw, below, above, lane, zl, zr, nax, nay, ndg);
     } else if (P == 1) {
-      wide_step<R, DIAG, 1>(x, bw, below, above, lane, zl, zr, nax, nay, ndg);
+      wide_step<NL, R, DIAG, 1>(x, bw, below, above, lane, zl, zr, nax, nay, ndg);
     } else {
-      wide_step<R, DIAG, 2>(x, bw, below, above, lane, zl, zr, nax, nay, ndg);
+      wide_step<NL, R, DIAG, 2>(x, bw, below, above, lane, zl, zr, nax, nay, ndg);
     }
   }
 
   if (SCALE) {
-    // b' of the tile's points for the launches that follow, one warp row at a time with lane l
-    // at the columns l + 32 j (coalesced), read from the pair layout in shared memory before the
+    // b' of the tile's points for the launches that follow, one group row at a time with lane l
+    // at the columns l + NL j (coalesced), read from the pair layout in shared memory before the
     // residual overwrites it
-    const float* bf = reinterpret_cast<const float*>(bsh) + ry0 * 192;
-    // column lane + 32 j of a row is element e = c mod 6 of lane c / 6: its float index in the
-    // pair layout, a lane constant
+    const float* bf = reinterpret_cast<const float*>(bsh) + ry0 * 2 * P3;
+    // column c = lane + NL j of a row is element e = c mod 6 of lane c / 6: its float index in
+    // the pair layout, a lane constant
     int sp[6];
     bool in[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      const int c = lane + 32 * j, e = c % 6;
-      sp[j] = 2 * ((e % 3) * 32 + c / 6) + e / 3;
+      const int c = lane + NL * j, e = c % 6;
+      sp[j] = 2 * ((e % 3) * NL + c / 6) + e / 3;
       in[j] = x0 + c >= tx0 && x0 + c < tx1;
     }
 #pragma unroll 1
     for (int r = 0; r < R; ++r) {
       const int gy = gyw + r;
-      if (gy < ty0 || gy >= ty1) continue;  // warp-uniform
+      if (gy < ty0 || gy >= ty1) continue;  // uniform in the row group
       G* row = bsc + off + (int64_t)gy * n + x0 + lane;
 #pragma unroll
       for (int j = 0; j < 6; ++j)
-        if (in[j]) row[32 * j] = G(bf[r * 192 + sp[j]]);
+        if (in[j]) row[NL * j] = G(bf[r * 2 * P3 + sp[j]]);
     }
   }
   if (RESTR) {
@@ -454,20 +459,20 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
         for (int k = 0; k < 3; ++k) x[r][k] = make_float2(float(G(x[r][k].x)), float(G(x[r][k].y)));
     }
     constexpr int t = 3 * NSW;  // the next step parity's edge buffer
-    float2* ed = edge + ((t & 1) * NWARP + warp) * 192;
+    float2* ed = edge + ((t & 1) * NVW + warp) * 2 * P3;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      ed[k * 32 + lane] = x[0][k];
-      ed[96 + k * 32 + lane] = x[R - 1][k];
+      ed[k * NL + lane] = x[0][k];
+      ed[P3 + k * NL + lane] = x[R - 1][k];
     }
     __syncthreads();
-    const float2* below = warp > 0 ? edge + ((t & 1) * NWARP + warp - 1) * 192 + 96 : zrow;
-    const float2* above = warp < NWARP - 1 ? edge + ((t & 1) * NWARP + warp + 1) * 192 : zrow;
-    wide_residual<R, DIAG>(x, bsh + ry0 * 96, below, above, lane, zl, zr, nax, nay, ndg);
+    const float2* below = warp > 0 ? edge + ((t & 1) * NVW + warp - 1) * 2 * P3 + P3 : zrow;
+    const float2* above = warp < NVW - 1 ? edge + ((t & 1) * NVW + warp + 1) * 2 * P3 : zrow;
+    wide_residual<NL, R, DIAG>(x, bsh + ry0 * P3, below, above, lane, zl, zr, nax, nay, ndg);
     __syncthreads();
     const int nc = (n - 1) / 2;
-    wide_restrict<G, R, NWARP, PA, PY>(reinterpret_cast<const float*>(bsh), bc + (int64_t)slice * nc * nc, nc, warp,
-                                       lane, gyw, cb, tx0, tx1, ty0, ty1, cf.rho, 0.5f * cf.rho);
+    wide_restrict<G, NL, R, RH, PA, PY>(reinterpret_cast<const float*>(bsh), bc + (int64_t)slice * nc * nc, nc,
+                                        warp, lane, gyw, cb, tx0, tx1, ty0, ty1, cf.rho, 0.5f * cf.rho);
   }
 
   // store the tile (inside the grid)
@@ -485,8 +490,8 @@ __device__ __forceinline__ void wide_body(G* __restrict__ x_out, const G* __rest
   }
 }
 
-template <typename G, int NSW, int R, int NWARP, int MINB, bool ASYNCB, bool PDIR, bool DIAG, bool PROL, bool RESTR,
-          bool SCALE>
+template <typename G, int NL, int NSW, int R, int NWARP, int MINB, bool ASYNCB, bool PDIR, bool DIAG, bool PROL,
+          bool RESTR, bool SCALE>
 __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_out, const G* __restrict__ x_in,
                                                             const G* __restrict__ b, const G* __restrict__ xc,
                                                             G* __restrict__ bc, const float* __restrict__ braw,
@@ -496,7 +501,8 @@ __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_
   static_assert(!(PROL && RESTR), "the prolongation starts post-smoothing, the restriction ends pre-smoothing");
   static_assert(!SCALE || RESTR, "the scaling is fused into the one pre-smoothing launch, which also restricts");
 #define ST_WIDE_BODY(PA, PY)                                                                                    \
-  wide_body<G, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, RESTR, SCALE, PA, PY>(x_out, x_in, b, xc, bc, braw, bsc, n,   \
+  wide_body<G, NL, NSW, R, NWARP, ASYNCB, PDIR, DIAG, PROL, RESTR, SCALE, PA, PY>(x_out, x_in, b, xc, bc, braw, bsc, \
+                                                                                  n,                               \
                                                                               coef, coef_class,                   \
                                                                        J, K, level, reverse, zero_init)
   if (!PROL && !RESTR) {
@@ -506,8 +512,8 @@ __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_
   // the region origin as in wide_body: block-uniform parities, one code path per class
   constexpr int M = 3 * NSW + (RESTR ? 2 : 0);
   int t, e, x0, y0;
-  wide_tile(blockIdx.x, gridDim.x, n, kWW, M, t, e, x0);
-  wide_tile(blockIdx.y, gridDim.y, n, NWARP * R, M, t, e, y0);
+  wide_tile(blockIdx.x, gridDim.x, n, 6 * NL, M, t, e, x0);
+  wide_tile(blockIdx.y, gridDim.y, n, (32 * NWARP / NL) * R, M, t, e, y0);
   const int pa = (x0 + 1) & 1, py = (y0 + 1) & 1;
   if (pa == 0 && py == 0)
     ST_WIDE_BODY(0, 0);
@@ -520,27 +526,38 @@ __global__ void __launch_bounds__(32 * NWARP, MINB) k_gs_wide(G* __restrict__ x_
 #undef ST_WIDE_BODY
 }
 
-// Block shape (rows per warp, warps, minimum resident blocks per SM)
+// Block shapes (lanes per row group, rows per group, warps, minimum resident blocks per SM): 0 the
+// 192 x 96 regions of whole warps (levels with n >= 192), 1 the 96 x 96 regions of half-warps
+// (96 <= n < 192; 6 rows a group, a multiple of 3, so both halves of a warp take the same
+// colour-step branch)
 template <int SHAPE>
 struct WideShape;
 template <>
 struct WideShape<0> {
-  static constexpr int R = 12, NWARP = 8, MINB = 2;
+  static constexpr int NL = 32, R = 12, NWARP = 8, MINB = 2;
   static constexpr bool ASYNCB = ST_WIDE_ASYNC_B0;  // b' through registers
   static constexpr bool PDIRECT = kProlDirect;      // coarse values straight into registers
 };
+template <>
+struct WideShape<1> {
+  static constexpr int NL = 16, R = 6, NWARP = 8, MINB = 3;
+  static constexpr bool ASYNCB = ST_WIDE_ASYNC_B0;
+  static constexpr bool PDIRECT = kProlDirect;
+};
+// the shape for level k (n = 2^k - 1 >= 96; wide_fits)
+inline int wide_shape_for(int k) { return ((1 << k) - 1) >= 192 ? 0 : 1; }
 
 template <typename G, int NSW, int SHAPE, bool DIAG, bool PROL, bool RESTR, bool SCALE = false>
 cudaError_t wide_launch_shape(const st_handle_s* h, int k, int nslices, int cls, G* x_out, const G* x_in,
                               const G* b, const G* xc, G* bc, bool reverse, bool zero_init,
                               const float* braw = nullptr, G* bsc = nullptr) {
   using S = WideShape<SHAPE>;
-  constexpr int M = 3 * NSW + (RESTR ? 2 : 0), RH = S::R * S::NWARP;
+  constexpr int M = 3 * NSW + (RESTR ? 2 : 0), RH = (32 * S::NWARP / S::NL) * S::R;
   const int n = (1 << k) - 1;
-  dim3 grid(wide_ntiles(n, kWW, M), wide_ntiles(n, RH, M), nslices);
-  constexpr size_t smem = wide_smem<S::R, S::NWARP>();
+  dim3 grid(wide_ntiles(n, 6 * S::NL, M), wide_ntiles(n, RH, M), nslices);
+  constexpr size_t smem = wide_smem<S::NL, S::R, S::NWARP>();
   const bool prof = (k == h->K) && prof_start(h);
-  k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR, SCALE>
+  k_gs_wide<G, S::NL, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR, SCALE>
       <<<grid, 32 * S::NWARP, smem, h->stream>>>(x_out, x_in, b, xc, bc, braw, bsc, n, coef_table<float>(h), cls, h->J,
                                                  h->K, k, reverse ? 1 : 0, zero_init ? 1 : 0);
   count_launch(h);
@@ -556,17 +573,18 @@ cudaError_t wide_launch_shape(const st_handle_s* h, int k, int nslices, int cls,
   return cudaGetLastError();
 }
 
-// dynamic shared-memory limits of the kernels of one storage type and sweep count
-template <typename G, int NSW>
-cudaError_t wide_attr() {
-  using S = WideShape<0>;
-  const int smem = (int)wide_smem<S::R, S::NWARP>();
+// dynamic shared-memory limits of the kernels of one storage type, sweep count and block shape
+template <typename G, int NSW, int SHAPE>
+cudaError_t wide_attr_shape() {
+  using S = WideShape<SHAPE>;
+  const int smem = (int)wide_smem<S::NL, S::R, S::NWARP>();
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaSuccess;
 #define ST_WIDE_ATTR(DIAG, PROL, RESTR, SCALE)                                                                 \
   if (e == cudaSuccess)                                                                                        \
     e = cudaFuncSetAttribute(                                                                                  \
-        k_gs_wide<G, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR, SCALE>, attr, smem);
+        k_gs_wide<G, S::NL, NSW, S::R, S::NWARP, S::MINB, S::ASYNCB, S::PDIRECT, DIAG, PROL, RESTR, SCALE>, attr, \
+        smem);
   ST_WIDE_ATTR(false, false, false, false)
   ST_WIDE_ATTR(false, true, false, false)
   ST_WIDE_ATTR(false, false, true, false)
@@ -581,11 +599,21 @@ cudaError_t wide_attr() {
   return e;
 }
 
+template <typename G, int NSW>
+cudaError_t wide_attr() {
+  cudaError_t e = wide_attr_shape<G, NSW, 0>();
+  if (e == cudaSuccess) e = wide_attr_shape<G, NSW, 1>();
+  return e;
+}
+
 }  // namespace
 
 template <typename G, int NSW, bool DIAG, bool PROL>
 cudaError_t wide_launch(const st_handle_s* h, int /*shape*/, int k, int nslices, int cls, G* x_out, const G* x_in,
                         const G* b, const G* xc, bool reverse, bool zero_init) {
+  if (wide_shape_for(k) == 1)
+    return wide_launch_shape<G, NSW, 1, DIAG, PROL, false>(h, k, nslices, cls, x_out, x_in, b, xc, nullptr, reverse,
+                                                           zero_init);
   return wide_launch_shape<G, NSW, 0, DIAG, PROL, false>(h, k, nslices, cls, x_out, x_in, b, xc, nullptr, reverse,
                                                          zero_init);
 }
@@ -593,6 +621,9 @@ cudaError_t wide_launch(const st_handle_s* h, int /*shape*/, int k, int nslices,
 template <typename G, int NSW, bool DIAG>
 cudaError_t wide_launch_restrict(const st_handle_s* h, int /*shape*/, int k, int nslices, int cls, G* x_out,
                                  const G* x_in, const G* b, G* bc, bool zero_init) {
+  if (wide_shape_for(k) == 1)
+    return wide_launch_shape<G, NSW, 1, DIAG, false, true>(h, k, nslices, cls, x_out, x_in, b, nullptr, bc, false,
+                                                           zero_init);
   return wide_launch_shape<G, NSW, 0, DIAG, false, true>(h, k, nslices, cls, x_out, x_in, b, nullptr, bc, false,
                                                          zero_init);
 }
@@ -603,6 +634,9 @@ cudaError_t wide_launch_restrict(const st_handle_s* h, int /*shape*/, int k, int
 template <bool DIAG>
 cudaError_t wide_launch_scale_restrict(const st_handle_s* h, int k, int nslices, int cls, float* x_out,
                                        const float* braw, float* bsc, float* bc) {
+  if (wide_shape_for(k) == 1)
+    return wide_launch_shape<float, 3, 1, DIAG, false, true, true>(h, k, nslices, cls, x_out, nullptr, bsc, nullptr,
+                                                                   bc, false, true, braw, bsc);
   return wide_launch_shape<float, 3, 0, DIAG, false, true, true>(h, k, nslices, cls, x_out, nullptr, bsc, nullptr, bc,
                                                                  false, true, braw, bsc);
 }

@@ -11,8 +11,9 @@ template cudaError_t wide_launch_scale_restrict<true>(const st_handle_s*, int, i
                                                       float*);
 
 bool wide_fits(const st_handle_s* h, int /*shape*/, int k) {
+  // the half-warp regions (96 x 96) below 192 columns, the whole-warp ones (192 x 96) above
   const int n = (1 << k) - 1;
-  return h->domain == 0 && n >= kWW && n >= WideShape<0>::R * WideShape<0>::NWARP;
+  return h->domain == 0 && n >= 6 * WideShape<1>::NL && n >= (32 * WideShape<1>::NWARP / WideShape<1>::NL) * WideShape<1>::R;
 }
 
 cudaError_t wide_set_attributes() {

@@ -271,10 +271,10 @@ template <typename T, typename G, int NSW, bool DIAG, bool PROL>
 cudaError_t reg_launch(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out, const G* x_in,
                        const G* b, const G* xc, bool reverse, bool zero_init);
 constexpr int kRegShapes = 4;
-// Binary32 Gauss-Seidel sweeps in wide register regions (k_gs_wide.cuh): 192 columns x 96 rows,
-// two points of one colour per lane and row in packed binary32 arithmetic, regions clamped into
-// the grid.  wide_fits: the unit square and a level whose n = 2^k - 1 holds a region (one block
-// shape: `shape` is 0).
+// Binary32 Gauss-Seidel sweeps in wide register regions (k_gs_wide.cuh): 192 columns x 96 rows
+// of whole warps where n = 2^k - 1 >= 192, else 96 x 96 of half-warps, two points of one colour
+// per lane and row in packed binary32 arithmetic, regions clamped into the grid.  wide_fits: the
+// unit square and a level with n >= 96 (`shape` is 0; the region shape follows from the level).
 bool wide_fits(const st_handle_s* h, int shape, int k);
 template <typename G, int NSW, bool DIAG, bool PROL>
 cudaError_t wide_launch(const st_handle_s* h, int shape, int k, int nslices, int cls, G* x_out, const G* x_in,

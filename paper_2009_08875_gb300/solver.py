@@ -178,8 +178,8 @@ class Solver:
     def set_smoother(self, kind):
         """Force the Gauss-Seidel kernel on every level (st_set_smoother): 'tiles', 'wavefront',
         'registers' (12 rows x 8 warps in binary32), 'registers_8x12', 'registers_6x16', or the
-        binary32 192-column regions with paired arithmetic 'registers_wide' (where a level holds no
-        such region: 'registers')."""
+        binary32 regions with paired arithmetic 'registers_wide' (192 or 96 columns; where a level
+        holds no such region: 'registers')."""
         _lib.check(_lib.load().st_set_smoother(self._h, self.SMOOTHERS[kind]))
 
     def set_wave_rows(self, rows):

@@ -43,10 +43,12 @@ REGISTER_KINDS = ("registers", "registers_8x12", "registers_6x16", "registers_wi
 
 
 # K = 3 (one tile / strip), K = 6 and K = 8 (several strips and vertical segments, ragged edges);
-# K = 8 and 9 on the square also run the wide binary32 regions on their finest one or two levels
-# (two and three regions per row, the last clamped against the grid's edge)
+# K = 7, 8 and 9 on the square also run the wide binary32 regions on their levels with n >= 96
+# (half-warp 96-column regions at n = 127, whole-warp 192-column regions above: two and three
+# regions per row, the last clamped against the grid's edge)
 @pytest.mark.parametrize("K,J,domain,B", [(3, 3, 0, 1), (6, 4, 0, 1), (8, 2, 0, 1), (6, 3, 1, 1), (5, 3, 0, 3),
-                                          (7, 2, 1, 2), (9, 1, 0, 1), (8, 1, 0, 2), (8, 2, 1, 1)])
+                                          (7, 2, 1, 2), (9, 1, 0, 1), (8, 1, 0, 2), (8, 2, 1, 1), (7, 3, 0, 1),
+                                          (7, 2, 0, 2)])
 def test_tiles_and_wavefront_bitwise_equal(K, J, domain, B):
     with Solver(K, J, domain=domain, batch=B) as s:
         rng = np.random.default_rng(K * 100 + J)
