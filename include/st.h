@@ -406,7 +406,8 @@ st_status st_sharded_solve(st_handle h, const st_comm* comm, int rank, int nrank
 st_status st_autotune(st_handle h, float* times_ms);
 
 /* Forces one Gauss-Seidel kernel on every level of this handle: kind 0 shared-memory tiles (the
- * state after set-up), 1 register wavefront, 2, 3, 4 register tiles of block shape 0, 1, 2 (in
+ * state after set-up, except binary32 on the unit square's levels with 2^k - 1 >= 96, which
+ * start with kind 5), 1 register wavefront, 2, 3, 4 register tiles of block shape 0, 1, 2 (in
  * binary32 12 rows x 8 warps, 8 x 12, 6 x 16; binary64 and double-float always 6 x 8), 5 the
  * binary32 regions with paired arithmetic (unit square, levels with 2^k - 1 >= 96; shape 0
  * elsewhere and in binary64 and double-float).  All give bitwise the same sweeps and

@@ -1048,6 +1048,11 @@ st_status st_setup_batch(st_handle* out, int domain, int space_level, int time_l
     delete h;
     return s;
   }
+  // default Gauss-Seidel kernels: binary32 on the levels that hold a wide register region (the
+  // autotuner's usual choice there), the shared-memory tiles everywhere else; all give the same
+  // bits, so this only sets the speed of handles that are not autotuned (batches, the server)
+  for (int k = 1; k <= h->K && k < 16; ++k)
+    if (wide_fits(h, 0, k)) h->gs_kind[1][0][k] = h->gs_kind[1][1][k] = (unsigned char)(2 + 3);
   *out = h;
   return ST_OK;
 }
