@@ -16,8 +16,10 @@ namespace st {
 namespace {
 
 // ---------------------------------------------------------------------------------------
-// A block of NWARP warps holds a region of 192 columns x NWARP * R rows of one slice: warp w
-// owns the region rows w R .. w R + R - 1, lane l the columns 6 l .. 6 l + 5 of them.  Columns
+// A block's threads form row groups of NL lanes (whole warps, NL = 32, or half-warps, NL = 16):
+// the block holds a region of 6 NL columns x (groups x R) rows of one slice, group w owning the
+// region rows w R .. w R + R - 1 and its lane l the columns 6 l .. 6 l + 5 of them ("warp" and
+// "lane" below mean the group and the lane in it; shuffles run within the group).  Columns
 // 6 l + e and 6 l + e + 3 have the same colour ((i + j) mod 3), so in every row the two points
 // of the active colour sit in one register pair x[r][m] = (column 6 l + m, column 6 l + m + 3),
 // m = the active element, and every neighbour sum of the update is a pair as well: the update
@@ -28,7 +30,7 @@ namespace {
 // (shared memory, double-buffered by step parity, one barrier per colour step).  The scaled
 // right-hand side b' sits in shared memory (read once per point and colour step).
 //
-// Placement: the region lies inside the grid (n >= 192 and n >= NWARP R), clamped against the
+// Placement: the region lies inside the grid (n at least its width and height), clamped against the
 // grid's edges, so no point of it is outside the grid and no update is masked.  On a side where
 // the region ends at the grid's boundary the missing neighbours are the Dirichlet zeros, which
 // is exact; on a side inside the grid the region carries a halo of H = 3 NSW points whose
